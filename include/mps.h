@@ -1,0 +1,155 @@
+/*
+ * mps.h -- C ABI of the GB300-native Multiway Powersort library (libmps.so).
+ *
+ * The library sorts device arrays with Multiway Powersort (Cawley Gelling,
+ * Nebel, Smith, Wild, arXiv 2209.06909): it detects the input's natural runs
+ * (maximal weakly increasing or strictly decreasing segments, the latter
+ * reversed; Sec. 2), computes every run boundary's k-way power (Def. 3.1),
+ * builds the merge tree those powers define (Alg. 1) and executes it level by
+ * level as stable k-way merges (Sec. 2.2, Sec. 4).  Every step runs in CUDA
+ * kernels written for sm_103a; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are device pointers owned by the caller; the library
+ *     never allocates or frees device memory on these paths.  Host pointers
+ *     are named h_*.
+ *   - Calls are enqueued on the given CUDA stream.  mps_sort_keys,
+ *     mps_sort_pairs and mps_merge_tree synchronise the stream twice to size
+ *     their level loop (the number of runs and the per-level node counts are
+ *     data dependent); outputs are complete when the call returns MPS_OK.
+ *   - Key types: MPS_U32 (uint32_t) or MPS_U64 (uint64_t), compared as
+ *     unsigned integers; every value, including the type's maximum, is a
+ *     legal key (no sentinel is reserved; cf. Sec. 4 "Sentinel values").
+ *   - Fan-in k must be 2, 4 or 8.  n must be below 2^31.
+ *   - Output arrays must not overlap input arrays.
+ *   - Errors are returned as mps_status; a device-side invariant violation
+ *     (which would indicate a library bug) is reported as MPS_ERR_DEVICE_CHECK.
+ */
+#ifndef MPS_H
+#define MPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MPS_OK = 0,
+    MPS_ERR_INVALID_ARG = 1,  /* null pointer, overlap, bad key type           */
+    MPS_ERR_UNSUPPORTED = 2,  /* k not in {2,4,8}, n >= 2^31                   */
+    MPS_ERR_WORKSPACE = 3,    /* workspace smaller than mps_workspace_size      */
+    MPS_ERR_CUDA = 4,         /* a CUDA runtime call failed                     */
+    MPS_ERR_TIMEOUT = 5,      /* a bounded wait ran out (queue / device spin)   */
+    MPS_ERR_BUDGET = 6,       /* request larger than the serving budget         */
+    MPS_ERR_DEVICE_CHECK = 7, /* a device-side invariant check failed           */
+    MPS_ERR_NOT_READY = 8,    /* queue: ticket still in flight                  */
+    MPS_ERR_CANCELLED = 9     /* queue: request cancelled by destroy            */
+} mps_status;
+
+typedef enum { MPS_U32 = 0, MPS_U64 = 1 } mps_key_type;
+
+/* One node of the canonical merge-tree encoding (16 bytes).  A node covers
+ * the runs [first_run, end_run); its d-1 run boundaries all carry the power
+ * `power` (Sec. 2.2: each merge-tree node of degree d owns d-1 boundaries).
+ * The table is sorted by (power, first_run); `parent` indexes that table and
+ * is 0xFFFFFFFF at the root. */
+typedef struct {
+    uint32_t first_run;
+    uint32_t end_run;
+    uint8_t power;
+    uint8_t degree;
+    uint16_t pad;
+    uint32_t parent;
+} mps_node;
+
+/* Optional tree outputs (all device pointers, caller-allocated, sized for the
+ * worst case of n runs).  Any member may be NULL to skip it.
+ *   run_starts[n+1] : s_0 = 0 < s_1 < ... < s_r = n (Sec. 2, runs R_0..R_{r-1})
+ *   run_desc[n]     : 1 if run i was strictly decreasing (and got reversed)
+ *   powers[n+1]     : powers[i] = P_i of boundary B_i (1 <= i < r), Def. 3.1;
+ *                     powers[0] = powers[r] = 0
+ *   node_first[n]   : smallest boundary index of the node owning B_i
+ *                     (node_first[0] = 0)
+ *   nodes[n]        : canonical node table (see mps_node)
+ *   leaf_depth[n]   : d_i, the depth of run i in the tree (Sec. 2.2)
+ *   counts[4]       : {r, number of nodes, number of distinct powers,
+ *                      merge cost M = sum_i d_i L_i} (Sec. 2.2)            */
+typedef struct {
+    uint32_t* run_starts;
+    uint8_t* run_desc;
+    uint8_t* powers;
+    uint32_t* node_first;
+    mps_node* nodes;
+    uint8_t* leaf_depth;
+    uint64_t* counts;
+} mps_tree;
+
+/* Bytes of device workspace needed to sort n keys of type kt (with a uint32
+ * payload if has_payload) with fan-in k.  The same size serves
+ * mps_merge_tree.  Returns MPS_ERR_INVALID_ARG if bytes is NULL. */
+mps_status mps_workspace_size(uint64_t n, mps_key_type kt, int has_payload, int k, size_t* bytes);
+
+/* Multiway Powersort of n keys (Alg. 2's merge policy via the tree of Alg. 1).
+ *   d_keys_in  : n keys, read only.
+ *   d_keys_out : n keys, receives the sorted keys.
+ *   d_ws       : workspace of at least mps_workspace_size(n, kt, 0, k) bytes.
+ *   opt_tree   : NULL, or device arrays that receive the run structure,
+ *                powers and canonical tree (slower: builds the full table). */
+mps_status mps_sort_keys(const void* d_keys_in, void* d_keys_out, uint64_t n, mps_key_type kt, int k,
+                         void* d_ws, size_t ws_bytes, const mps_tree* opt_tree, cudaStream_t stream);
+
+/* Stable key-value sort: every uint32 payload moves with its key, and equal
+ * keys keep their input order (runs are weakly increasing or strictly
+ * decreasing, so reversal never reorders equal keys; merges prefer the
+ * leftmost run on ties -- Sec. 2, Sec. 4 "Tournament tree").
+ * Workspace: mps_workspace_size(n, kt, 1, k). */
+mps_status mps_sort_pairs(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out,
+                          uint32_t* d_vals_out, uint64_t n, mps_key_type kt, int k,
+                          void* d_ws, size_t ws_bytes, const mps_tree* opt_tree, cudaStream_t stream);
+
+/* Run structure, powers and canonical merge tree of d_keys without moving
+ * any key (the keys are not modified).  `out` must be non-NULL. */
+mps_status mps_merge_tree(const void* d_keys, uint64_t n, mps_key_type kt, int k, const mps_tree* out,
+                          void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* End-to-end form of mps_sort_keys from host memory: copies h_keys_in to
+ * d_keys_in, sorts into d_keys_out and copies the result to h_keys_out, all on
+ * `stream` (pinned host buffers give asynchronous copies).  Returns after the
+ * result has reached h_keys_out. */
+mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t n, mps_key_type kt, int k,
+                              void* d_keys_in, void* d_keys_out, void* d_ws, size_t ws_bytes,
+                              cudaStream_t stream);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream.
+ * mps_profile_enable(1) clears and starts recording; mps_profile_read fills
+ * up to `cap` entries (kernel name, launches, total milliseconds) after
+ * synchronising the recorded events, and returns the number of entries. */
+typedef struct {
+    char name[48];
+    uint64_t launches;
+    double total_ms;
+    double bytes;      /* algorithmic bytes moved by those launches */
+} mps_profile_entry;
+
+void mps_profile_enable(int on);
+int mps_profile_read(mps_profile_entry* out, int cap);
+
+/* Statistics of the most recent sort on this host thread (host memory). */
+typedef struct {
+    uint64_t n, r, merge_cost, frontier_nodes, hbm_nodes;
+    uint32_t num_levels, hbm_levels;
+    uint64_t bytes_fused, bytes_levels; /* algorithmic bytes of the merge kernels */
+} mps_stats;
+
+mps_status mps_last_stats(mps_stats* out);
+
+const char* mps_status_string(mps_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPS_H */

@@ -1,0 +1,463 @@
+// api.cu -- C ABI of libmps.so: argument checks, workspace layout and the
+// host-side order of the kernels.
+//
+// Order of one sort (every step is a CUDA kernel; see runs.cu, tree.cu,
+// merge.cu):
+//   1. run detection (Sec. 2)                       -> run_starts, run_desc
+//   2. boundary powers (Def. 3.1)                   -> powers
+//   3. min-tree over the powers, depth scans        -> node depths
+//   4. node pass (Alg. 1 unrolled)                  -> level nodes, fused subtrees, M
+//   5. fused merges of all small subtrees           -> their outputs
+//   6. level merges, largest power first            -> root output in keys_out
+// The host reads back the run count after step 1 and the per-level node
+// counts after step 4 to size the launches of steps 2-6.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mps.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace mps {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Byte layout of the workspace for one (n, key bytes, payload, k).
+struct Plan {
+    uint64_t n = 0;
+    int kb = 4;
+    bool vals = false;
+    int k = 4;
+    MergeGeom g{};
+    uint64_t rmax = 0, det_tiles = 0, mask_tiles = 0, windows = 0;
+    uint32_t nodes_cap = 0, unit_cap = 0;
+    uint64_t lv_cap[kMinTreeLevels] = {};
+    int nlv_max = 0;
+    // offsets
+    size_t o_ctr, o_lvloff, o_det_sum, o_det_pref, o_rs, o_rdesc, o_fr_end, o_fr_depth, o_lv[kMinTreeLevels], o_info,
+        o_mt, o_first_run, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_hist, o_ktmp, o_vtmp, total;
+
+    explicit Plan(uint64_t n_, int kb_, bool vals_, int k_) : n(n_), kb(kb_), vals(vals_), k(k_) {
+        g = merge_geom(kb, vals, k);
+        rmax = n / 2 + 2;
+        det_tiles = ceil_div(std::max<uint64_t>(n, 1), kDetTile);
+        mask_tiles = ceil_div(rmax, kMaskTile);
+        windows = ceil_div(std::max<uint64_t>(n, 1), g.tfix) + 1;
+        nodes_cap = (uint32_t)(34 * (n / g.tmax + 1) + 64);
+        unit_cap = (uint32_t)(n / g.ts + n / g.tmax + 64);
+        uint64_t len = rmax + 1;
+        nlv_max = 0;
+        while (true) {
+            lv_cap[nlv_max] = (len + 31) / 32 * 32 + 32;
+            nlv_max++;
+            if (len <= 32 || nlv_max == kMinTreeLevels) break;
+            len = ceil_div(len, 32);
+        }
+        size_t o = 0;
+        auto take = [&](size_t bytes) { size_t at = o; o += align_up(bytes); return at; };
+        o_ctr = take(kCtrWords * 8);
+        o_lvloff = take(kMaxLevels * 4);
+        o_det_sum = take(det_tiles * 16);
+        o_det_pref = take(det_tiles * 8);
+        o_rs = take((rmax + 2) * 4);
+        o_rdesc = take(rmax + 1);
+        o_fr_end = take((rmax + 1) * 4);
+        o_fr_depth = take(rmax + 1);
+        for (int t = 0; t < kMinTreeLevels; t++) o_lv[t] = t < nlv_max ? take(lv_cap[t]) : 0;
+        o_info = take(rmax + 1);
+        o_mt = take(mask_tiles * 8 * 4);
+        o_first_run = take((windows + 1) * 4);
+        o_nodes_raw = take((size_t)nodes_cap * sizeof(LevelNode));
+        o_nodes_lvl = take((size_t)nodes_cap * sizeof(LevelNode));
+        o_unit_node = take((size_t)unit_cap * 4);
+        o_split = take((size_t)(unit_cap + 1) * k * 4);
+        o_hist = take(mask_tiles * kMaxLevels * 4);
+        o_ktmp = take(n * kb);
+        o_vtmp = vals ? take(n * 4) : o;
+        total = o;
+    }
+
+    WsView view(void* base) const {
+        char* b = static_cast<char*>(base);
+        WsView w{};
+        w.counters = reinterpret_cast<uint64_t*>(b + o_ctr);
+        w.det_sum = reinterpret_cast<uint4*>(b + o_det_sum);
+        w.det_pref = reinterpret_cast<uint2*>(b + o_det_pref);
+        w.run_starts = reinterpret_cast<uint32_t*>(b + o_rs);
+        w.run_desc = reinterpret_cast<uint8_t*>(b + o_rdesc);
+        w.fr_end = reinterpret_cast<uint32_t*>(b + o_fr_end);
+        w.fr_depth = reinterpret_cast<uint8_t*>(b + o_fr_depth);
+        for (int t = 0; t < kMinTreeLevels; t++) w.lv[t] = t < nlv_max ? reinterpret_cast<uint8_t*>(b + o_lv[t]) : nullptr;
+        w.powers = w.lv[0];
+        w.node_info = reinterpret_cast<uint8_t*>(b + o_info);
+        unsigned long long* mt = reinterpret_cast<unsigned long long*>(b + o_mt);
+        w.mt_f = mt;
+        w.mt_g = mt + mask_tiles;
+        w.mt_fpre = mt + 2 * mask_tiles;
+        w.mt_gsuf = mt + 3 * mask_tiles;
+        w.first_run = reinterpret_cast<uint32_t*>(b + o_first_run);
+        w.tfix = g.tfix;
+        w.windows = (uint32_t)windows;
+        w.nodes_raw = reinterpret_cast<LevelNode*>(b + o_nodes_raw);
+        w.nodes_lvl = reinterpret_cast<LevelNode*>(b + o_nodes_lvl);
+        w.nodes_cap = nodes_cap;
+        w.unit_node = reinterpret_cast<uint32_t*>(b + o_unit_node);
+        w.split_tab = reinterpret_cast<uint32_t*>(b + o_split);
+        w.unit_cap = unit_cap;
+        w.canon_idx = w.fr_end;  // the tree dump runs after the merges no longer need fr_end
+        w.hist = reinterpret_cast<uint32_t*>(b + o_hist);
+        w.keys_tmp = b + o_ktmp;
+        w.vals_tmp = vals ? reinterpret_cast<uint32_t*>(b + o_vtmp) : nullptr;
+        return w;
+    }
+};
+
+// Sets the min-tree level lengths for the actual run count.
+void set_levels(WsView& w, uint32_t r) {
+    uint64_t len = (uint64_t)r + 1;
+    int nl = 0;
+    while (true) {
+        w.lv_len[nl] = (uint32_t)len;
+        nl++;
+        if (len <= 32 || nl == kMinTreeLevels) break;
+        len = ceil_div(len, 32);
+    }
+    w.nlv = nl;
+}
+
+__global__ void k_level_offsets(const uint64_t* __restrict__ ctr, uint32_t* __restrict__ off) {
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int p = 0; p < kMaxLevels; p++) {
+            off[p] = acc;
+            acc += (uint32_t)ctr[kCtrHbmCount + p];
+        }
+    }
+}
+
+// ------------------------------------------------------------- profiling
+
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+    double bytes;
+};
+
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct ProfScope {
+    bool on;
+    ProfRec rec;
+    cudaStream_t st;
+    ProfScope(const char* name, double bytes, cudaStream_t s) : on(false), st(s) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (!g_prof_on) return;
+        on = true;
+        rec.name = name;
+        rec.bytes = bytes;
+        rec.a = take_event();
+        rec.b = take_event();
+        cudaEventRecord(rec.a, st);
+    }
+    ~ProfScope() {
+        if (!on) return;
+        cudaEventRecord(rec.b, st);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof.push_back(rec);
+    }
+};
+
+thread_local mps_stats g_last{};
+
+bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
+    if (!a || !b || !an || !bn) return false;
+    uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + bn && y < x + an;
+}
+
+#define MPS_CUDA(call)                                 \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return MPS_ERR_CUDA;    \
+    } while (0)
+
+template <typename K, bool V>
+mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, uint64_t n, int k,
+                     void* d_ws, size_t ws_bytes, const mps_tree* tree, bool move_keys, cudaStream_t st) {
+    if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    g_last = mps_stats{};
+    g_last.n = n;
+    if (n == 0) {
+        if (tree && tree->counts) MPS_CUDA(cudaMemsetAsync(tree->counts, 0, 4 * sizeof(uint64_t), st));
+        MPS_CUDA(cudaStreamSynchronize(st));
+        return MPS_OK;
+    }
+    if (!keys_in || !d_ws) return MPS_ERR_INVALID_ARG;
+    if (move_keys && !keys_out) return MPS_ERR_INVALID_ARG;
+    if (V && move_keys && (!vals_in || !vals_out)) return MPS_ERR_INVALID_ARG;
+    if (move_keys && overlaps(keys_in, n * sizeof(K), keys_out, n * sizeof(K))) return MPS_ERR_INVALID_ARG;
+    if (V && move_keys && overlaps(vals_in, n * 4, vals_out, n * 4)) return MPS_ERR_INVALID_ARG;
+    Plan plan(n, sizeof(K), V, k);
+    if (ws_bytes < plan.total) return MPS_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(d_ws) % 16) return MPS_ERR_INVALID_ARG;
+    WsView ws = plan.view(d_ws);
+    const MergeGeom& g = plan.g;
+    const double b = (double)sizeof(K) + (V ? 4.0 : 0.0);
+
+    uint64_t h_ctr[kCtrWords];
+    MPS_CUDA(cudaMemsetAsync(ws.counters, 0, kCtrWords * 8, st));
+    {
+        ProfScope ps("detect_runs", (double)n * sizeof(K) * 2, st);
+        launch_detect<K>(keys_in, n, ws, st);
+    }
+    MPS_CUDA(cudaGetLastError());
+    MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, 8, cudaMemcpyDeviceToHost, st));
+    MPS_CUDA(cudaStreamSynchronize(st));
+    const uint32_t r = (uint32_t)h_ctr[kCtrR];
+    g_last.r = r;
+
+    if (r <= 1) {
+        if (move_keys) {
+            ProfScope ps("copy_single_run", (double)n * b * 2, st);
+            launch_copy_single_run<K, V>(keys_in, vals_in, keys_out, vals_out, n, ws, st);
+        }
+        if (tree) {
+            if (tree->run_starts) MPS_CUDA(cudaMemcpyAsync(tree->run_starts, ws.run_starts, 8, cudaMemcpyDeviceToDevice, st));
+            if (tree->run_desc) MPS_CUDA(cudaMemcpyAsync(tree->run_desc, ws.run_desc, 1, cudaMemcpyDeviceToDevice, st));
+            if (tree->powers) MPS_CUDA(cudaMemsetAsync(tree->powers, 0, 2, st));
+            if (tree->node_first) MPS_CUDA(cudaMemsetAsync(tree->node_first, 0, 4, st));
+            if (tree->leaf_depth) MPS_CUDA(cudaMemsetAsync(tree->leaf_depth, 0, 1, st));
+            if (tree->counts) {
+                uint64_t c[4] = {1, 0, 0, 0};
+                MPS_CUDA(cudaMemcpyAsync(tree->counts, c, sizeof(c), cudaMemcpyHostToDevice, st));
+            }
+        }
+        MPS_CUDA(cudaGetLastError());
+        MPS_CUDA(cudaStreamSynchronize(st));
+        return MPS_OK;
+    }
+
+    set_levels(ws, r);
+    {
+        ProfScope ps("powers", (double)r * 9.0, st);
+        launch_powers(n, r, k, ws, st);
+    }
+    {
+        ProfScope ps("tree_scans", (double)r * 4.0, st);
+        launch_mintree(r, ws, st);
+        launch_masks(r, tree && tree->leaf_depth, tree ? tree->leaf_depth : nullptr, ws, st);
+    }
+    {
+        ProfScope ps("node_pass", (double)r * 2.0, st);
+        launch_node_pass(r, k, g.tmax, ws, st);
+    }
+    MPS_CUDA(cudaGetLastError());
+    MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, sizeof(h_ctr), cudaMemcpyDeviceToHost, st));
+    MPS_CUDA(cudaStreamSynchronize(st));
+    if ((uint32_t)h_ctr[kCtrStatus]) return MPS_ERR_DEVICE_CHECK;
+    const uint64_t hbm_total = h_ctr[kCtrHbmTotal];
+    if (hbm_total > plan.nodes_cap) return MPS_ERR_DEVICE_CHECK;
+    g_last.merge_cost = h_ctr[kCtrM];
+    g_last.frontier_nodes = h_ctr[kCtrFrontier];
+    g_last.hbm_nodes = hbm_total;
+    g_last.num_levels = (uint32_t)__builtin_popcountll(h_ctr[kCtrLevelBits]);
+
+    if (move_keys) {
+        uint32_t* level_off = reinterpret_cast<uint32_t*>(static_cast<char*>(d_ws) + plan.o_lvloff);
+        if (hbm_total) {
+            k_level_offsets<<<1, 32, 0, st>>>(ws.counters, level_off);
+            launch_bucket((uint32_t)hbm_total, level_off, ws, st);
+        }
+        if (h_ctr[kCtrFrontier]) {
+            // algorithmic bytes: each element of a fused subtree is read and written once
+            ProfScope ps("fused_merge", 2.0 * b * (double)h_ctr[kCtrFrontierElems], st);
+            launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, n, g, ws, st);
+        }
+        uint32_t off = 0;
+        std::vector<std::pair<int, uint32_t>> levels;
+        for (int p = 0; p < kMaxLevels; p++) {
+            uint32_t c = (uint32_t)h_ctr[kCtrHbmCount + p];
+            if (c) levels.push_back({p, off});
+            off += c;
+        }
+        g_last.hbm_levels = (uint32_t)levels.size();
+        uint64_t lvl_bytes = 0;
+        for (auto it = levels.rbegin(); it != levels.rend(); ++it) {
+            int p = it->first;
+            uint32_t cnt = (uint32_t)h_ctr[kCtrHbmCount + p];
+            uint64_t elems = h_ctr[kCtrHbmSize + p];
+            lvl_bytes += (uint64_t)(2 * b * elems);
+            ProfScope ps("level_merge", 2.0 * b * (double)elems, st);
+            launch_level<K, V>(it->second, cnt, elems, k, keys_in, vals_in, keys_out, vals_out, g, ws, st);
+        }
+        g_last.bytes_levels = lvl_bytes;
+        MPS_CUDA(cudaGetLastError());
+    }
+    if (tree) {
+        if (tree->run_starts)
+            MPS_CUDA(cudaMemcpyAsync(tree->run_starts, ws.run_starts, ((size_t)r + 1) * 4, cudaMemcpyDeviceToDevice, st));
+        if (tree->run_desc) MPS_CUDA(cudaMemcpyAsync(tree->run_desc, ws.run_desc, r, cudaMemcpyDeviceToDevice, st));
+        if (tree->powers) MPS_CUDA(cudaMemcpyAsync(tree->powers, ws.powers, (size_t)r + 1, cudaMemcpyDeviceToDevice, st));
+        if (tree->node_first || tree->nodes) {
+            uint32_t* nf = tree->node_first;
+            if (!nf) return MPS_ERR_INVALID_ARG;  // the node table needs node_first
+            launch_tree_dump(r, k, ws, nf, tree->nodes, nullptr, st);
+        }
+        if (tree->counts) {
+            uint64_t c[4] = {r, h_ctr[kCtrNodes], (uint64_t)__builtin_popcountll(h_ctr[kCtrLevelBits]), h_ctr[kCtrM]};
+            MPS_CUDA(cudaMemcpyAsync(tree->counts, c, sizeof(c), cudaMemcpyHostToDevice, st));
+        }
+        MPS_CUDA(cudaGetLastError());
+    }
+    uint32_t status = 0;
+    MPS_CUDA(cudaMemcpyAsync(&status, ws.counters + kCtrStatus, 4, cudaMemcpyDeviceToHost, st));
+    MPS_CUDA(cudaStreamSynchronize(st));
+    if (status) return MPS_ERR_DEVICE_CHECK;
+    g_last.bytes_fused = (uint64_t)(2 * b * (double)h_ctr[kCtrFrontierElems]);
+    return MPS_OK;
+}
+
+}  // namespace
+}  // namespace mps
+
+using namespace mps;
+
+extern "C" {
+
+mps_status mps_workspace_size(uint64_t n, mps_key_type kt, int has_payload, int k, size_t* bytes) {
+    if (!bytes) return MPS_ERR_INVALID_ARG;
+    if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
+    if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    Plan p(n, kt == MPS_U32 ? 4 : 8, has_payload != 0, k);
+    *bytes = p.total;
+    return MPS_OK;
+}
+
+mps_status mps_sort_keys(const void* d_keys_in, void* d_keys_out, uint64_t n, mps_key_type kt, int k, void* d_ws,
+                         size_t ws_bytes, const mps_tree* opt_tree, cudaStream_t stream) {
+    if (kt == MPS_U32)
+        return sort_impl<uint32_t, false>((const uint32_t*)d_keys_in, nullptr, (uint32_t*)d_keys_out, nullptr, n, k, d_ws,
+                                          ws_bytes, opt_tree, true, stream);
+    if (kt == MPS_U64)
+        return sort_impl<uint64_t, false>((const uint64_t*)d_keys_in, nullptr, (uint64_t*)d_keys_out, nullptr, n, k, d_ws,
+                                          ws_bytes, opt_tree, true, stream);
+    return MPS_ERR_INVALID_ARG;
+}
+
+mps_status mps_sort_pairs(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out, uint32_t* d_vals_out,
+                          uint64_t n, mps_key_type kt, int k, void* d_ws, size_t ws_bytes, const mps_tree* opt_tree,
+                          cudaStream_t stream) {
+    if (kt == MPS_U32)
+        return sort_impl<uint32_t, true>((const uint32_t*)d_keys_in, d_vals_in, (uint32_t*)d_keys_out, d_vals_out, n, k, d_ws,
+                                         ws_bytes, opt_tree, true, stream);
+    if (kt == MPS_U64)
+        return sort_impl<uint64_t, true>((const uint64_t*)d_keys_in, d_vals_in, (uint64_t*)d_keys_out, d_vals_out, n, k, d_ws,
+                                         ws_bytes, opt_tree, true, stream);
+    return MPS_ERR_INVALID_ARG;
+}
+
+mps_status mps_merge_tree(const void* d_keys, uint64_t n, mps_key_type kt, int k, const mps_tree* out, void* d_ws,
+                          size_t ws_bytes, cudaStream_t stream) {
+    if (!out) return MPS_ERR_INVALID_ARG;
+    if (kt == MPS_U32)
+        return sort_impl<uint32_t, false>((const uint32_t*)d_keys, nullptr, nullptr, nullptr, n, k, d_ws, ws_bytes, out, false,
+                                          stream);
+    if (kt == MPS_U64)
+        return sort_impl<uint64_t, false>((const uint64_t*)d_keys, nullptr, nullptr, nullptr, n, k, d_ws, ws_bytes, out, false,
+                                          stream);
+    return MPS_ERR_INVALID_ARG;
+}
+
+mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t n, mps_key_type kt, int k, void* d_keys_in,
+                              void* d_keys_out, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (n && (!h_keys_in || !h_keys_out || !d_keys_in || !d_keys_out)) return MPS_ERR_INVALID_ARG;
+    size_t bytes = n * (kt == MPS_U32 ? 4 : 8);
+    if (n && cudaMemcpyAsync(d_keys_in, h_keys_in, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) return MPS_ERR_CUDA;
+    mps_status s = mps_sort_keys(d_keys_in, d_keys_out, n, kt, k, d_ws, ws_bytes, nullptr, stream);
+    if (s != MPS_OK) return s;
+    if (n && cudaMemcpyAsync(h_keys_out, d_keys_out, bytes, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return MPS_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return MPS_ERR_CUDA;
+    return MPS_OK;
+}
+
+void mps_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g_prof) {
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    g_prof.clear();
+    g_prof_on = on != 0;
+}
+
+int mps_profile_read(mps_profile_entry* out, int cap) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::vector<mps_profile_entry> agg;
+    for (auto& r : g_prof) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        mps_profile_entry* e = nullptr;
+        for (auto& x : agg)
+            if (!strncmp(x.name, r.name, sizeof(x.name))) e = &x;
+        if (!e) {
+            agg.push_back(mps_profile_entry{});
+            e = &agg.back();
+            strncpy(e->name, r.name, sizeof(e->name) - 1);
+        }
+        e->launches++;
+        e->total_ms += ms;
+        e->bytes += r.bytes;
+    }
+    int m = std::min<int>(cap, (int)agg.size());
+    for (int i = 0; i < m; i++) out[i] = agg[i];
+    return (int)agg.size();
+}
+
+mps_status mps_last_stats(mps_stats* out) {
+    if (!out) return MPS_ERR_INVALID_ARG;
+    *out = g_last;
+    return MPS_OK;
+}
+
+const char* mps_status_string(mps_status s) {
+    switch (s) {
+        case MPS_OK: return "ok";
+        case MPS_ERR_INVALID_ARG: return "invalid argument";
+        case MPS_ERR_UNSUPPORTED: return "unsupported (k not in {2,4,8} or n >= 2^31)";
+        case MPS_ERR_WORKSPACE: return "workspace too small";
+        case MPS_ERR_CUDA: return "CUDA runtime error";
+        case MPS_ERR_TIMEOUT: return "timed out";
+        case MPS_ERR_BUDGET: return "request exceeds the memory budget";
+        case MPS_ERR_DEVICE_CHECK: return "device-side check failed";
+        case MPS_ERR_NOT_READY: return "not ready";
+        case MPS_ERR_CANCELLED: return "cancelled";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// kernels.cuh -- workspace view, device records and launcher declarations
+// shared by the translation units of the CUDA path.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mps {
+
+constexpr int kDetTile = 4096;     // elements per run-detection tile
+constexpr int kMaskTile = 4096;    // boundaries per mask-scan tile
+constexpr int kMaxLevels = 64;     // bound on distinct powers (P <= 32 for n < 2^31)
+constexpr int kMinTreeLevels = 8;  // fan-out 32 min-tree over the powers
+constexpr int kMaxFrontierPerWindow = 512;
+
+// Indices into the 64-bit device counter block.
+enum : int {
+    kCtrR = 0,          // number of runs r
+    kCtrLevelBits = 1,  // bit p set if some boundary has power p
+    kCtrM = 2,          // merge cost (sum of node sizes)
+    kCtrHbmTotal = 3,   // number of nodes executed as level merges
+    kCtrFrontier = 4,   // number of fused subtrees
+    kCtrStatus = 5,     // device error word (low 32 bits)
+    kCtrNodes = 6,      // number of tree nodes
+    kCtrUnits = 7,      // work units of the current level
+    kCtrHbmCount = 8,   // [64] nodes per power (level merges only)
+    kCtrHbmSize = 72,   // [64] elements per power (level merges only)
+    kCtrHbmFill = 136,  // [64] fill counters for bucketing
+    kCtrFrontierElems = 200,  // elements inside fused subtrees
+    kCtrWords = 256
+};
+
+// A node executed by the level-merge kernels (more than T_max elements).
+// Children c = 0..d-1 cover runs [b[c], b[c+1]); b[0] and b[d] are the node's
+// delimiting boundaries (nearest boundaries of smaller power).
+struct __align__(16) LevelNode {
+    uint32_t sL, sR;          // element range of the node
+    uint32_t unit_off;        // first work unit of this node (per level)
+    uint32_t nunits;          // number of work units
+    uint32_t b[9];            // child boundaries (run indices)
+    uint8_t power, depth, degree, pad;
+    uint32_t pad2[2];
+};
+static_assert(sizeof(LevelNode) == 64, "LevelNode layout");
+
+struct WsView {
+    uint64_t* counters;
+    uint4* det_sum;
+    uint2* det_pref;
+    uint32_t* run_starts;
+    uint8_t* run_desc;
+    uint32_t* fr_end;
+    uint8_t* fr_depth;
+    uint8_t* lv[kMinTreeLevels];   // lv[0] = powers[0..r] (+ padding)
+    uint32_t lv_len[kMinTreeLevels];
+    int nlv;
+    uint8_t* powers;               // == lv[0]
+    uint8_t* node_info;            // per boundary: depth | (is_start << 7)
+    unsigned long long* mt_f;      // mask-scan tile aggregates
+    unsigned long long* mt_g;
+    unsigned long long* mt_fpre;
+    unsigned long long* mt_gsuf;
+    uint32_t* first_run;           // window -> first run with start >= window start
+    uint32_t tfix, windows;
+    LevelNode* nodes_raw;
+    LevelNode* nodes_lvl;
+    uint32_t nodes_cap;
+    uint32_t* unit_node;
+    uint32_t* split_tab;
+    uint32_t unit_cap;
+    uint32_t* canon_idx;           // dump: canonical index of each node start
+    uint32_t* hist;                // dump: per-tile power histograms
+    void* keys_tmp;
+    uint32_t* vals_tmp;
+};
+
+// Sizes of the merge stages for one key/payload type.
+struct MergeGeom {
+    uint32_t c_fused;   // elements of shared memory per fused tile
+    uint32_t tfix;      // window of frontier starts per fused tile
+    uint32_t tmax;      // largest fused subtree
+    uint32_t c_level;   // elements per level-merge unit
+    uint32_t ts;        // splitter spacing per child (c_level / k)
+    int k;              // fan-in
+};
+
+MergeGeom merge_geom(int key_bytes, bool vals, int k);
+
+// runs.cu
+template <typename K> void launch_detect(const K* keys, uint64_t n, const WsView& ws, cudaStream_t st);
+void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t st);
+
+// tree.cu
+void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st);
+void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView& ws, cudaStream_t st);
+void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st);
+void launch_bucket(uint32_t total, const uint32_t* level_off, const WsView& ws, cudaStream_t st);
+void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first, void* nodes,
+                      uint64_t* counts_out, cudaStream_t st);
+
+// merge.cu
+template <typename K, bool V>
+void launch_fused(const K* leaf_keys, const uint32_t* leaf_vals, K* out, uint32_t* vout, uint64_t n,
+                  const MergeGeom& g, const WsView& ws, cudaStream_t st);
+template <typename K, bool V>
+void launch_level(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys,
+                  const uint32_t* leaf_vals, K* out, uint32_t* vout, const MergeGeom& g, const WsView& ws,
+                  cudaStream_t st);
+template <typename K, bool V>
+void launch_copy_single_run(const K* in, const uint32_t* vin, K* out, uint32_t* vout, uint64_t n,
+                            const WsView& ws, cudaStream_t st);
+
+}  // namespace mps

@@ -1,0 +1,507 @@
+// tree.cu -- the merge tree of Alg. 1 built from the boundary powers.
+//
+// Alg. 1 (KwayTree_k) splits a range of runs at every boundary of minimum
+// power and recurses.  Unrolled, a node is a maximal group of equal-power
+// boundaries not separated by any boundary of smaller power; it covers the
+// runs between its delimiters L and R, the nearest boundaries of smaller
+// power on either side (the virtual boundaries 0 and r have power 0).  Its
+// parent owns whichever delimiter has the larger power (Alg. 1 recursed into
+// that side last).  The nodes of power p are disjoint and depend only on
+// nodes of larger power, so the tree executes level by level, p = max .. 1.
+//
+// Nearest-smaller queries run on a fan-out-32 min-tree over the u8 powers.
+//
+// Depths come from two scans.  The ancestors of a node are one node per
+// distinct power among the "staircase" boundaries around it: the suffix
+// minima of the powers to its left and the prefix minima to its right.  A
+// segment is summarised by (bit set of its suffix-minimum values, its minimum);
+// the summaries compose associatively:
+//   F(XY) = (F_Y.bits | (F_X.bits & below(min_Y)), min(min_X, min_Y))
+// and symmetrically for prefix minima.  Then
+//   depth(node of B_j) = |(F(P_1..P_{j-1}) | G(P_{j+1}..P_{r-1})) & below(P_j)|,
+//   depth(run i)       = |F(P_1..P_i) | G(P_{i+1}..P_{r-1})|,
+// and B_j starts its node iff P_j is not among the suffix minima to its left.
+// (Sec. 2.2: M = sum_i d_i L_i; Fact 3.2: depth(m(B_j)) <= P_j - 1.)
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace mps {
+
+namespace {
+
+// ------------------------------------------------------------- min-tree
+
+__global__ void __launch_bounds__(1024) k_mintree(const uint8_t* __restrict__ src, uint32_t src_len, uint8_t* __restrict__ dst1,
+                                                  uint8_t* __restrict__ dst2, uint32_t dst2_pad_from, uint32_t dst2_pad_to) {
+    __shared__ uint32_t wmin[32];
+    uint32_t i = blockIdx.x * 1024u + threadIdx.x;
+    uint32_t v = i < src_len ? src[i] : 255u;
+    v = __reduce_min_sync(0xffffffffu, v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        dst1[blockIdx.x * 32u + warp] = (uint8_t)v;
+        wmin[warp] = v;
+    }
+    if (dst2 == nullptr) return;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = __reduce_min_sync(0xffffffffu, wmin[lane]);
+        if (lane == 0) dst2[blockIdx.x] = (uint8_t)w;
+        if (blockIdx.x == 0)
+            for (uint32_t q = dst2_pad_from + lane; q < dst2_pad_to; q += 32) dst2[q] = 255;
+    }
+}
+
+struct MinTree {
+    const uint8_t* lv[kMinTreeLevels];
+    int nl;
+};
+
+// Bit b set iff blk[b] < v (strict) or blk[b] <= v; blk is 32-byte aligned.
+__device__ __forceinline__ uint32_t match32(const uint8_t* blk, uint32_t v, bool strict) {
+    const uint4* p = reinterpret_cast<const uint4*>(blk);
+    uint4 a = p[0], b = p[1];
+    uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t vv = v * 0x01010101u;
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        uint32_t c = strict ? __vcmpltu4(w[q], vv) : __vcmpleu4(w[q], vv);
+        uint32_t nib = ((c >> 7) & 1u) | ((c >> 14) & 2u) | ((c >> 21) & 4u) | ((c >> 28) & 8u);
+        m |= nib << (4 * q);
+    }
+    return m;
+}
+
+// Nearest index l < i with P_l < v (strict) or P_l <= v.
+__device__ uint32_t nsv_left(const MinTree& T, uint32_t i, uint32_t v, bool strict) {
+    uint32_t pos = i;
+    for (int t = 0; t < T.nl; t++) {
+        uint32_t bs = pos & ~31u;
+        uint32_t off = pos - bs;
+        uint32_t m = off ? (match32(T.lv[t] + bs, v, strict) & (0xFFFFFFFFu >> (32 - off))) : 0u;
+        if (m) {
+            uint32_t j = bs + 31 - __clz(m);
+            while (t > 0) {
+                t--;
+                uint32_t cm = match32(T.lv[t] + j * 32u, v, strict);
+                j = j * 32u + 31 - __clz(cm);
+            }
+            return j;
+        }
+        pos = bs >> 5;
+    }
+    return kNone;
+}
+
+// Nearest index l > i with P_l < v (strict) or P_l <= v.
+__device__ uint32_t nsv_right(const MinTree& T, uint32_t i, uint32_t v, bool strict) {
+    uint32_t pos = i;
+    for (int t = 0; t < T.nl; t++) {
+        uint32_t bs = pos & ~31u;
+        uint32_t off = pos - bs;
+        uint32_t m = off < 31 ? (match32(T.lv[t] + bs, v, strict) & (0xFFFFFFFFu << (off + 1))) : 0u;
+        if (m) {
+            uint32_t j = bs + __ffs(m) - 1;
+            while (t > 0) {
+                t--;
+                uint32_t cm = match32(T.lv[t] + j * 32u, v, strict);
+                j = j * 32u + __ffs(cm) - 1;
+            }
+            return j;
+        }
+        pos = bs >> 5;
+    }
+    return kNone;
+}
+
+MinTree make_mintree(const WsView& ws) {
+    MinTree T;
+    for (int t = 0; t < kMinTreeLevels; t++) T.lv[t] = ws.lv[t];
+    T.nl = ws.nlv;
+    return T;
+}
+
+// ------------------------------------------------------------- masks
+
+constexpr uint64_t kBits = (1ull << 56) - 1;
+constexpr uint64_t kMaskIdentity = 255ull << 56;
+
+__device__ __forceinline__ uint64_t below(uint32_t m) { return m >= 56 ? kBits : ((1ull << m) - 1); }
+__device__ __forceinline__ uint32_t mmin(uint64_t x) { return (uint32_t)(x >> 56); }
+__device__ __forceinline__ uint64_t melem(uint32_t p) { return (1ull << p) | ((uint64_t)p << 56); }
+
+// suffix-minima summary, X then Y
+struct OpF {
+    __device__ unsigned long long operator()(unsigned long long X, unsigned long long Y) const {
+        uint32_t mx = mmin(X), my = mmin(Y);
+        uint64_t bits = (Y & kBits) | (X & kBits & below(my));
+        return bits | ((uint64_t)(mx < my ? mx : my) << 56);
+    }
+};
+// prefix-minima summary, X then Y
+struct OpG {
+    __device__ unsigned long long operator()(unsigned long long X, unsigned long long Y) const {
+        uint32_t mx = mmin(X), my = mmin(Y);
+        uint64_t bits = (X & kBits) | (Y & kBits & below(mx));
+        return bits | ((uint64_t)(mx < my ? mx : my) << 56);
+    }
+};
+// the same prefix-minima summary for a reverse-order scan: a follows b in scan order
+struct OpGRev {
+    __device__ unsigned long long operator()(unsigned long long A, unsigned long long B) const { return OpG()(B, A); }
+};
+
+constexpr int kMaskThreads = 256;
+constexpr int kMaskItems = kMaskTile / kMaskThreads;
+
+__global__ void __launch_bounds__(kMaskThreads) k_mask_reduce(const uint8_t* __restrict__ powers, uint32_t r,
+                                                              unsigned long long* __restrict__ tf, unsigned long long* __restrict__ tg) {
+    __shared__ unsigned long long tmp[kMaskThreads / 32 + 1];
+    uint32_t nb = r - 1;
+    uint32_t b0 = blockIdx.x * kMaskTile + threadIdx.x * kMaskItems;
+    unsigned long long f = kMaskIdentity, g = kMaskIdentity;
+#pragma unroll
+    for (int q = 0; q < kMaskItems; q++) {
+        uint32_t b = b0 + q;
+        if (b < nb) {
+            uint64_t e = melem(powers[b + 1]);
+            f = OpF()(f, e);
+            g = OpG()(g, e);
+        }
+    }
+    unsigned long long tot;
+    block_scan_excl<kMaskThreads, false>(f, OpF(), kMaskIdentity, tmp, &tot);
+    if (threadIdx.x == 0) tf[blockIdx.x] = tot;
+    block_scan_excl<kMaskThreads, false>(g, OpG(), kMaskIdentity, tmp, &tot);
+    if (threadIdx.x == 0) tg[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_mask_scan(const unsigned long long* __restrict__ tf, const unsigned long long* __restrict__ tg,
+                                                    uint32_t tiles, unsigned long long* __restrict__ fpre,
+                                                    unsigned long long* __restrict__ gsuf) {
+    __shared__ unsigned long long tmp[1024 / 32 + 1];
+    uint32_t per = (tiles + 1023) / 1024;
+    uint32_t b = threadIdx.x * per, e = min(tiles, b + per);
+    unsigned long long f = kMaskIdentity, g = kMaskIdentity;
+    for (uint32_t t = b; t < e; t++) f = OpF()(f, tf[t]);
+    for (uint32_t t = e; t > b; t--) g = OpG()(tg[t - 1], g);
+    unsigned long long pf = block_scan_excl<1024, false>(f, OpF(), kMaskIdentity, tmp, nullptr);
+    unsigned long long sg = block_scan_excl<1024, true>(g, OpGRev(), kMaskIdentity, tmp, nullptr);
+    for (uint32_t t = b; t < e; t++) {
+        fpre[t] = pf;
+        pf = OpF()(pf, tf[t]);
+    }
+    for (uint32_t t = e; t > b; t--) {
+        gsuf[t - 1] = sg;
+        sg = OpG()(tg[t - 1], sg);
+    }
+}
+
+__global__ void __launch_bounds__(kMaskThreads) k_mask_apply(const uint8_t* __restrict__ powers, uint32_t r,
+                                                             const unsigned long long* __restrict__ fpre,
+                                                             const unsigned long long* __restrict__ gsuf,
+                                                             uint8_t* __restrict__ node_info, uint8_t* __restrict__ leaf_depth) {
+    __shared__ unsigned long long tmp[kMaskThreads / 32 + 1];
+    uint32_t nb = r - 1;
+    uint32_t b0 = blockIdx.x * kMaskTile + threadIdx.x * kMaskItems;
+    uint64_t e[kMaskItems];
+    unsigned long long f = kMaskIdentity, g = kMaskIdentity;
+#pragma unroll
+    for (int q = 0; q < kMaskItems; q++) {
+        uint32_t b = b0 + q;
+        e[q] = b < nb ? melem(powers[b + 1]) : kMaskIdentity;
+        f = OpF()(f, e[q]);
+        g = OpG()(g, e[q]);
+    }
+    unsigned long long pf = block_scan_excl<kMaskThreads, false>(f, OpF(), kMaskIdentity, tmp, nullptr);
+    unsigned long long sg = block_scan_excl<kMaskThreads, true>(g, OpGRev(), kMaskIdentity, tmp, nullptr);
+    pf = OpF()(fpre[blockIdx.x], pf);
+    sg = OpG()(sg, gsuf[blockIdx.x]);
+    // right-side summaries per item, right to left
+    uint64_t gex[kMaskItems];
+#pragma unroll
+    for (int q = kMaskItems - 1; q >= 0; q--) {
+        gex[q] = sg;
+        sg = OpG()(e[q], sg);
+    }
+#pragma unroll
+    for (int q = 0; q < kMaskItems; q++) {
+        uint32_t b = b0 + q;
+        if (b < nb) {
+            uint32_t j = b + 1;
+            uint32_t p = mmin(e[q]);
+            uint64_t left = pf & kBits, right = gex[q] & kBits;
+            uint32_t depth = __popcll((left | right) & below(p));
+            uint32_t start = ((left >> p) & 1ull) ? 0u : 1u;
+            node_info[j] = (uint8_t)(depth | (start << 7));
+            if (leaf_depth) {
+                uint64_t incl = OpF()(pf, e[q]) & kBits;
+                leaf_depth[j] = (uint8_t)__popcll(incl | right);
+                if (j == 1) leaf_depth[0] = (uint8_t)__popcll(OpG()(e[q], gex[q]) & kBits);
+            }
+        }
+        pf = OpF()(pf, e[q]);
+    }
+}
+
+// ------------------------------------------------------------- node pass
+
+struct NodeShape {
+    uint32_t L, R, d;
+    uint32_t b[9];
+};
+
+__device__ __forceinline__ bool node_shape(const MinTree& T, const uint8_t* P, uint32_t j, uint32_t v, int k,
+                                           NodeShape& s) {
+    s.L = nsv_left(T, j, v, true);
+    s.R = nsv_right(T, j, v, true);
+    s.b[0] = s.L;
+    s.b[1] = j;
+    uint32_t cnt = 1, cur = j;
+    bool ok = true;
+    while (true) {
+        uint32_t nx = nsv_right(T, cur, v, false);
+        if (nx >= s.R) break;
+        if ((int)cnt >= k - 1) { ok = false; break; }
+        s.b[++cnt] = nx;
+        cur = nx;
+    }
+    s.d = cnt + 1;
+    s.b[s.d] = s.R;
+    return ok;
+}
+
+__global__ void __launch_bounds__(256) k_node_pass(MinTree T, uint32_t r, int k, uint32_t tmax,
+                                                   const uint32_t* __restrict__ rs, const uint8_t* __restrict__ node_info,
+                                                   uint64_t* __restrict__ ctr, LevelNode* __restrict__ nodes_raw, uint32_t nodes_cap,
+                                                   uint32_t* __restrict__ fr_end, uint8_t* __restrict__ fr_depth) {
+    const uint8_t* P = T.lv[0];
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    unsigned long long msize = 0, nstarts = 0;
+    if (j < r) {
+        uint8_t info = node_info[j];
+        if (info & 0x80) {
+            nstarts = 1;
+            uint32_t v = P[j];
+            uint32_t depth = info & 0x7F;
+            NodeShape s;
+            if (!node_shape(T, P, j, v, k, s)) dev_fail(reinterpret_cast<uint32_t*>(ctr + kCtrStatus), kDevDegree);
+            uint32_t sL = rs[s.L], sR = rs[s.R];
+            uint32_t size = sR - sL;
+            msize = size;
+            if (size > tmax) {
+                uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmTotal), 1ull);
+                if (slot < nodes_cap) {
+                    LevelNode nd;
+                    nd.sL = sL; nd.sR = sR; nd.unit_off = 0; nd.nunits = 0;
+#pragma unroll
+                    for (int q = 0; q < 9; q++) nd.b[q] = q <= (int)s.d ? s.b[q] : 0u;
+                    nd.power = (uint8_t)v; nd.depth = (uint8_t)depth; nd.degree = (uint8_t)s.d; nd.pad = 0;
+                    nd.pad2[0] = nd.pad2[1] = 0;
+                    nodes_raw[slot] = nd;
+                } else {
+                    dev_fail(reinterpret_cast<uint32_t*>(ctr + kCtrStatus), kDevCapacity);
+                }
+                atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmCount + v), 1ull);
+                atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmSize + v), (unsigned long long)size);
+            } else {
+                bool frontier;
+                uint32_t pl = P[s.L], pr = P[s.R];
+                if (pl == 0 && pr == 0) {
+                    frontier = true;
+                } else {
+                    uint32_t q = pl >= pr ? s.L : s.R;
+                    uint32_t pq = P[q];
+                    uint32_t lq = nsv_left(T, q, pq, true), rq = nsv_right(T, q, pq, true);
+                    frontier = (rs[rq] - rs[lq]) > tmax;
+                }
+                if (frontier) {
+                    fr_end[s.L] = s.R;
+                    fr_depth[s.L] = (uint8_t)depth;
+                    atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), (unsigned long long)size);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        msize += __shfl_xor_sync(0xffffffffu, msize, o);
+        nstarts += __shfl_xor_sync(0xffffffffu, nstarts, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (msize) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrM), msize);
+        if (nstarts) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrNodes), nstarts);
+    }
+}
+
+// Copies level-merge nodes into per-power buckets (order within a bucket is
+// irrelevant: nodes of one power are disjoint).
+__global__ void k_bucket(const LevelNode* __restrict__ raw, uint32_t total, const uint32_t* __restrict__ level_off,
+                         uint64_t* __restrict__ ctr, LevelNode* __restrict__ out) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    LevelNode nd = raw[i];
+    uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmFill + nd.power), 1ull);
+    out[level_off[nd.power] + slot] = nd;
+}
+
+// ------------------------------------------------------------- tree dump
+
+// node_first for every boundary; canonical rank is computed by k_dump_rank.
+__global__ void __launch_bounds__(256) k_dump_node_first(MinTree T, uint32_t r, const uint8_t* __restrict__ node_info,
+                                                         uint32_t* __restrict__ node_first) {
+    const uint8_t* P = T.lv[0];
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0) node_first[0] = 0;
+    if (j == 0 || j >= r) return;
+    if (node_info[j] & 0x80) {
+        node_first[j] = j;
+    } else {
+        uint32_t v = P[j];
+        uint32_t L = nsv_left(T, j, v, true);
+        node_first[j] = nsv_right(T, L, v, false);
+    }
+}
+
+// Per-tile histograms of node-start powers (tile = kMaskTile boundaries).
+__global__ void __launch_bounds__(256) k_dump_hist(const uint8_t* __restrict__ P, const uint8_t* __restrict__ node_info, uint32_t r,
+                                                   uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[kMaxLevels];
+    if (threadIdx.x < kMaxLevels) h[threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t base = blockIdx.x * kMaskTile;
+    for (uint32_t q = threadIdx.x; q < kMaskTile; q += blockDim.x) {
+        uint32_t j = base + q + 1;
+        if (j < r && (node_info[j] & 0x80)) atomicAdd(&h[P[j]], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kMaxLevels) hist[(size_t)blockIdx.x * kMaxLevels + threadIdx.x] = h[threadIdx.x];
+}
+
+// Turns the histograms into exclusive offsets in (power, tile) order.  One block.
+__global__ void __launch_bounds__(1024) k_dump_hist_scan(uint32_t* __restrict__ hist, uint32_t tiles) {
+    __shared__ uint32_t tmp[1024 / 32 + 1];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t p = 0; p < (uint32_t)kMaxLevels; p++) {
+        for (uint32_t t0 = 0; t0 < tiles; t0 += 1024) {
+            uint32_t t = t0 + threadIdx.x;
+            uint32_t v = t < tiles ? hist[(size_t)t * kMaxLevels + p] : 0u;
+            uint32_t tot;
+            uint32_t ex = block_sum_excl<1024>(v, tmp, &tot);
+            uint32_t c = carry;
+            if (t < tiles) hist[(size_t)t * kMaxLevels + p] = c + ex;
+            __syncthreads();
+            if (threadIdx.x == 0) carry = c + tot;
+            __syncthreads();
+        }
+    }
+}
+
+// Canonical rank of every node start: starts of power p in boundary order.
+// Within a tile, a warp walks its boundaries in order with ballots.
+__global__ void __launch_bounds__(256) k_dump_rank(const uint8_t* __restrict__ P, const uint8_t* __restrict__ node_info, uint32_t r,
+                                                   const uint32_t* __restrict__ hist, uint32_t* __restrict__ canon_idx) {
+    __shared__ uint32_t run[kMaxLevels];
+    if (threadIdx.x < kMaxLevels) run[threadIdx.x] = hist[(size_t)blockIdx.x * kMaxLevels + threadIdx.x];
+    __syncthreads();
+    // one warp walks the whole tile in order, 32 boundaries per step
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    uint32_t base = blockIdx.x * kMaskTile;
+    for (uint32_t q0 = 0; q0 < (uint32_t)kMaskTile; q0 += 32) {
+        uint32_t j = base + q0 + lane + 1;
+        bool st = j < r && (node_info[j] & 0x80);
+        uint32_t p = st ? P[j] : 0xFFu;
+        uint32_t peers = __match_any_sync(0xffffffffu, p);
+        uint32_t below_me = __popc(peers & ((1u << lane) - 1));
+        uint32_t cnt = __popc(peers);
+        uint32_t leader = __ffs(peers) - 1;
+        uint32_t basep = 0;
+        if (st) basep = run[p];
+        __syncwarp();
+        if (st) canon_idx[j] = basep + below_me;
+        if (st && (uint32_t)lane == leader) run[p] = basep + cnt;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_dump_nodes(MinTree T, uint32_t r, int k, const uint32_t* __restrict__ rs,
+                                                    const uint8_t* __restrict__ node_info, const uint32_t* __restrict__ canon_idx,
+                                                    const uint32_t* __restrict__ node_first, uint32_t* __restrict__ out_nodes,
+                                                    uint32_t* __restrict__ status) {
+    const uint8_t* P = T.lv[0];
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (j >= r || !(node_info[j] & 0x80)) return;
+    uint32_t v = P[j];
+    NodeShape s;
+    if (!node_shape(T, P, j, v, k, s)) dev_fail(status, kDevDegree);
+    uint32_t parent = kNone;
+    uint32_t pl = P[s.L], pr = P[s.R];
+    if (pl != 0 || pr != 0) {
+        uint32_t q = pl >= pr ? s.L : s.R;
+        parent = canon_idx[node_first[q]];
+    }
+    uint32_t idx = canon_idx[j];
+    uint32_t* o = out_nodes + (size_t)idx * 4;
+    o[0] = s.L;
+    o[1] = s.R;
+    o[2] = v | (s.d << 8);
+    o[3] = parent;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- launchers
+
+void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st) {
+    // level t has ws.lv_len[t] valid entries; padding of 255 up to a multiple of 32
+    for (int t = 0; t + 1 < ws.nlv; t += 2) {
+        uint32_t src_len = ws.lv_len[t];
+        uint32_t blocks = (src_len + 1023) / 1024;
+        uint8_t* dst2 = (t + 2 < ws.nlv) ? ws.lv[t + 2] : nullptr;
+        uint32_t pad_from = blocks, pad_to = (blocks + 31) / 32 * 32;
+        k_mintree<<<blocks, 1024, 0, st>>>(ws.lv[t], src_len, ws.lv[t + 1], dst2, pad_from, pad_to);
+    }
+}
+
+void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView& ws, cudaStream_t st) {
+    uint32_t nb = r - 1;
+    uint32_t tiles = (uint32_t)ceil_div(nb, kMaskTile);
+    k_mask_reduce<<<tiles, kMaskThreads, 0, st>>>(ws.powers, r, ws.mt_f, ws.mt_g);
+    k_mask_scan<<<1, 1024, 0, st>>>(ws.mt_f, ws.mt_g, tiles, ws.mt_fpre, ws.mt_gsuf);
+    k_mask_apply<<<tiles, kMaskThreads, 0, st>>>(ws.powers, r, ws.mt_fpre, ws.mt_gsuf, ws.node_info,
+                                                  dump_leaf ? leaf_depth : nullptr);
+}
+
+void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st) {
+    uint32_t nb = r - 1;
+    k_node_pass<<<(uint32_t)ceil_div(nb, 256), 256, 0, st>>>(make_mintree(ws), r, k, tmax, ws.run_starts, ws.node_info,
+                                                              ws.counters, ws.nodes_raw, ws.nodes_cap, ws.fr_end, ws.fr_depth);
+}
+
+void launch_bucket(uint32_t total, const uint32_t* level_off, const WsView& ws, cudaStream_t st) {
+    if (!total) return;
+    k_bucket<<<(uint32_t)ceil_div(total, 256), 256, 0, st>>>(ws.nodes_raw, total, level_off, ws.counters, ws.nodes_lvl);
+}
+
+void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first, void* nodes, uint64_t* counts_out,
+                      cudaStream_t st) {
+    (void)counts_out;
+    uint32_t nb = r - 1;
+    uint32_t tiles = (uint32_t)ceil_div(nb, kMaskTile);
+    MinTree T = make_mintree(ws);
+    k_dump_node_first<<<(uint32_t)ceil_div(r, 256), 256, 0, st>>>(T, r, ws.node_info, node_first);
+    k_dump_hist<<<tiles, 256, 0, st>>>(ws.powers, ws.node_info, r, ws.hist);
+    k_dump_hist_scan<<<1, 1024, 0, st>>>(ws.hist, tiles);
+    k_dump_rank<<<tiles, 256, 0, st>>>(ws.powers, ws.node_info, r, ws.hist, ws.canon_idx);
+    if (nodes)
+        k_dump_nodes<<<(uint32_t)ceil_div(nb, 256), 256, 0, st>>>(T, r, k, ws.run_starts, ws.node_info, ws.canon_idx, node_first,
+                                                                   reinterpret_cast<uint32_t*>(nodes),
+                                                                   reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
+}
+
+}  // namespace mps

@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libmps.so (include/mps.h).
+
+Argument marshalling only: every step of the sort runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current stream.  Keys are
+passed as tensors whose element size selects the key type (4 bytes: uint32,
+8 bytes: uint64); signed dtypes are accepted and their bits read as unsigned.
+If libmps.so is missing the binding raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from .build import LIB
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace too small", 4: "CUDA runtime error",
+          5: "timed out", 6: "budget exceeded", 7: "device-side check failed", 8: "not ready", 9: "cancelled"}
+
+NODE_DTYPE = np.dtype([("first_run", "<u4"), ("end_run", "<u4"), ("power", "u1"), ("degree", "u1"),
+                       ("pad", "<u2"), ("parent", "<u4")])
+
+
+class MpsError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class Tree(ctypes.Structure):
+    _fields_ = [("run_starts", ctypes.c_void_p), ("run_desc", ctypes.c_void_p), ("powers", ctypes.c_void_p),
+                ("node_first", ctypes.c_void_p), ("nodes", ctypes.c_void_p), ("leaf_depth", ctypes.c_void_p),
+                ("counts", ctypes.c_void_p)]
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("r", ctypes.c_uint64), ("merge_cost", ctypes.c_uint64),
+                ("frontier_nodes", ctypes.c_uint64), ("hbm_nodes", ctypes.c_uint64),
+                ("num_levels", ctypes.c_uint32), ("hbm_levels", ctypes.c_uint32),
+                ("bytes_fused", ctypes.c_uint64), ("bytes_levels", ctypes.c_uint64)]
+
+
+EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_tree", "mps_sort_keys_host",
+           "mps_profile_enable", "mps_profile_read", "mps_last_stats", "mps_status_string"]
+
+_lib = None
+
+
+def lib():
+    """Loads libmps.so (built by paper_2209_06909_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB.exists():
+        raise RuntimeError(f"{LIB} is missing: build it with paper_2209_06909_gb300.build.build() (no CPU fallback)")
+    L = ctypes.CDLL(str(LIB))
+    P, U64, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+    L.mps_workspace_size.argtypes = [U64, I, I, I, ctypes.POINTER(ctypes.c_size_t)]
+    L.mps_sort_keys.argtypes = [P, P, U64, I, I, P, ctypes.c_size_t, P, P]
+    L.mps_sort_pairs.argtypes = [P, P, P, P, U64, I, I, P, ctypes.c_size_t, P, P]
+    L.mps_merge_tree.argtypes = [P, U64, I, I, P, P, ctypes.c_size_t, P]
+    L.mps_sort_keys_host.argtypes = [P, P, U64, I, I, P, P, P, ctypes.c_size_t, P]
+    L.mps_profile_enable.argtypes = [I]
+    L.mps_profile_enable.restype = None
+    L.mps_profile_read.argtypes = [P, I]
+    L.mps_profile_read.restype = I
+    L.mps_last_stats.argtypes = [P]
+    L.mps_status_string.argtypes = [I]
+    L.mps_status_string.restype = ctypes.c_char_p
+    for fn in ("mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_tree", "mps_sort_keys_host",
+               "mps_last_stats"):
+        getattr(L, fn).restype = I
+    _lib = L
+    return L
+
+
+def _check(fn, code):
+    if code != 0:
+        raise MpsError(fn, code)
+
+
+def _key_type(t: torch.Tensor) -> int:
+    if t.element_size() == 4:
+        return 0
+    if t.element_size() == 8:
+        return 1
+    raise TypeError("keys must have 4-byte or 8-byte elements")
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def workspace_size(n: int, key_bytes: int, has_payload: bool = False, k: int = 4) -> int:
+    out = ctypes.c_size_t(0)
+    _check("mps_workspace_size", lib().mps_workspace_size(n, 0 if key_bytes == 4 else 1, int(has_payload), k,
+                                                          ctypes.byref(out)))
+    return out.value
+
+
+def workspace(n: int, key_bytes: int, has_payload: bool = False, k: int = 4, device="cuda") -> torch.Tensor:
+    return torch.empty(max(workspace_size(n, key_bytes, has_payload, k), 16), dtype=torch.uint8, device=device)
+
+
+@dataclass
+class TreeBuffers:
+    """Device buffers for the tree outputs (sized for n runs)."""
+    run_starts: torch.Tensor
+    run_desc: torch.Tensor
+    powers: torch.Tensor
+    node_first: torch.Tensor
+    nodes: torch.Tensor
+    leaf_depth: torch.Tensor
+    counts: torch.Tensor
+
+    @staticmethod
+    def alloc(n: int, device) -> "TreeBuffers":
+        m = max(n, 1)
+        return TreeBuffers(
+            run_starts=torch.zeros(m + 2, dtype=torch.int32, device=device),
+            run_desc=torch.zeros(m + 1, dtype=torch.uint8, device=device),
+            powers=torch.zeros(m + 2, dtype=torch.uint8, device=device),
+            node_first=torch.zeros(m + 1, dtype=torch.int32, device=device),
+            nodes=torch.zeros((m + 1) * 4, dtype=torch.int32, device=device),
+            leaf_depth=torch.zeros(m + 1, dtype=torch.uint8, device=device),
+            counts=torch.zeros(4, dtype=torch.int64, device=device))
+
+    def struct(self) -> Tree:
+        return Tree(self.run_starts.data_ptr(), self.run_desc.data_ptr(), self.powers.data_ptr(),
+                    self.node_first.data_ptr(), self.nodes.data_ptr(), self.leaf_depth.data_ptr(),
+                    self.counts.data_ptr())
+
+    def to_numpy(self) -> dict:
+        """Host copy trimmed to the actual sizes (canonical encoding)."""
+        counts = self.counts.cpu().numpy().astype(np.uint64)
+        r, nn, lv, mc = (int(x) for x in counts)
+        nodes = self.nodes.cpu().numpy().view(np.uint32)[: 4 * nn].view(NODE_DTYPE)
+        return {"r": r, "num_nodes": nn, "num_levels": lv, "merge_cost": mc,
+                "run_starts": self.run_starts.cpu().numpy().view(np.uint32)[: r + 1].copy(),
+                "run_desc": self.run_desc.cpu().numpy()[:r].copy(),
+                "powers": self.powers.cpu().numpy()[: r + 1].copy(),
+                "node_first": self.node_first.cpu().numpy().view(np.uint32)[:r].copy(),
+                "nodes": nodes.copy(),
+                "leaf_depth": self.leaf_depth.cpu().numpy()[:r].copy()}
+
+
+def sort_keys(keys: torch.Tensor, k: int = 4, out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+              tree: TreeBuffers | None = None, stream=None) -> torch.Tensor:
+    """Sorts a device tensor of uint32/uint64 keys (mps_sort_keys)."""
+    n = keys.numel()
+    kt = _key_type(keys)
+    if out is None:
+        out = torch.empty_like(keys)
+    if ws is None:
+        ws = workspace(n, keys.element_size(), False, k, keys.device)
+    ts = ctypes.byref(tree.struct()) if tree is not None else None
+    _check("mps_sort_keys", lib().mps_sort_keys(keys.data_ptr(), out.data_ptr(), n, kt, k, ws.data_ptr(),
+                                                ws.numel(), ts, _stream(stream)))
+    return out
+
+
+def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, k: int = 4, out_keys=None, out_vals=None, ws=None,
+               tree: TreeBuffers | None = None, stream=None):
+    """Stable key/value sort (mps_sort_pairs); vals are 4-byte payloads."""
+    n = keys.numel()
+    kt = _key_type(keys)
+    if vals.element_size() != 4 or vals.numel() != n:
+        raise TypeError("vals must be n 4-byte values")
+    out_keys = torch.empty_like(keys) if out_keys is None else out_keys
+    out_vals = torch.empty_like(vals) if out_vals is None else out_vals
+    if ws is None:
+        ws = workspace(n, keys.element_size(), True, k, keys.device)
+    ts = ctypes.byref(tree.struct()) if tree is not None else None
+    _check("mps_sort_pairs", lib().mps_sort_pairs(keys.data_ptr(), vals.data_ptr(), out_keys.data_ptr(),
+                                                  out_vals.data_ptr(), n, kt, k, ws.data_ptr(), ws.numel(), ts,
+                                                  _stream(stream)))
+    return out_keys, out_vals
+
+
+def merge_tree(keys: torch.Tensor, k: int = 4, ws=None, stream=None) -> TreeBuffers:
+    """Run structure, powers and canonical merge tree (mps_merge_tree)."""
+    n = keys.numel()
+    tb = TreeBuffers.alloc(n, keys.device)
+    if ws is None:
+        ws = workspace(n, keys.element_size(), False, k, keys.device)
+    t = tb.struct()
+    _check("mps_merge_tree", lib().mps_merge_tree(keys.data_ptr(), n, _key_type(keys), k, ctypes.byref(t),
+                                                  ws.data_ptr(), ws.numel(), _stream(stream)))
+    return tb
+
+
+def sort_keys_host(h_in: torch.Tensor, h_out: torch.Tensor, d_in: torch.Tensor, d_out: torch.Tensor,
+                   ws: torch.Tensor, k: int = 4, stream=None) -> None:
+    """End-to-end sort from (pinned) host memory through mps_sort_keys_host."""
+    n = h_in.numel()
+    _check("mps_sort_keys_host", lib().mps_sort_keys_host(h_in.data_ptr(), h_out.data_ptr(), n, _key_type(h_in), k,
+                                                          d_in.data_ptr(), d_out.data_ptr(), ws.data_ptr(),
+                                                          ws.numel(), _stream(stream)))
+
+
+def profile_enable(on: bool = True) -> None:
+    lib().mps_profile_enable(int(on))
+
+
+def profile_read() -> list[dict]:
+    cap = 64
+    arr = (ProfileEntry * cap)()
+    m = lib().mps_profile_read(ctypes.cast(arr, ctypes.c_void_p), cap)
+    return [{"name": arr[i].name.decode(), "launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms),
+             "bytes": float(arr[i].bytes)} for i in range(min(m, cap))]
+
+
+def last_stats() -> dict:
+    s = Stats()
+    _check("mps_last_stats", lib().mps_last_stats(ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+
+def to_device(a: np.ndarray, device="cuda") -> torch.Tensor:
+    """uint32/uint64 numpy array -> device tensor with the same bits."""
+    signed = {np.dtype(np.uint32): np.int32, np.dtype(np.uint64): np.int64}[a.dtype]
+    return torch.from_numpy(np.ascontiguousarray(a).view(signed)).to(device)
+
+
+def to_numpy(t: torch.Tensor, dtype) -> np.ndarray:
+    """Device tensor -> numpy array of the given unsigned dtype (same bits)."""
+    return t.cpu().numpy().view(dtype)

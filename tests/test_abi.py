@@ -1,0 +1,56 @@
+"""The C ABI library builds, loads and exports every entry point declared in
+include/mps.h; host-side argument checks (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2209_06909_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(str(path))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "mps.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mps_[a-z_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 9
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    from paper_2209_06909_gb300 import mps
+    assert sorted(mps.EXPORTS) == sorted(n for n in declared_functions())
+
+
+def test_workspace_size_host_checks(lib):
+    from paper_2209_06909_gb300 import mps
+    small = mps.workspace_size(1000, 4, False, 4)
+    big = mps.workspace_size(1 << 20, 4, False, 4)
+    pairs = mps.workspace_size(1 << 20, 8, True, 4)
+    assert 0 < small < big < pairs
+    with pytest.raises(mps.MpsError) as e:
+        mps.workspace_size(1000, 4, False, 3)
+    assert e.value.code == 2
+    with pytest.raises(mps.MpsError):
+        mps.workspace_size(1 << 31, 4, False, 4)
+
+
+def test_sort_rejects_bad_fan_in_before_any_device_work(lib):
+    P = ctypes.c_void_p
+    lib.mps_sort_keys.argtypes = [P, P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P, P]
+    assert lib.mps_sort_keys(None, None, 10, 0, 3, None, 0, None, None) == 2
+    assert lib.mps_sort_keys(None, None, 1 << 31, 0, 4, None, 0, None, None) == 2
+    lib.mps_status_string.restype = ctypes.c_char_p
+    assert lib.mps_status_string(3) == b"workspace too small"
