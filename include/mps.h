@@ -142,6 +142,7 @@ typedef struct {
     uint64_t n, r, merge_cost, frontier_nodes, hbm_nodes;
     uint32_t num_levels, hbm_levels;
     uint64_t bytes_fused, bytes_levels; /* algorithmic bytes of the merge kernels */
+    uint64_t launches;                  /* CUDA kernels launched by the call */
 } mps_stats;
 
 mps_status mps_last_stats(mps_stats* out);

@@ -24,6 +24,8 @@
 
 namespace mps {
 
+thread_local uint64_t g_launches = 0;
+
 namespace {
 
 constexpr size_t kAlign = 256;
@@ -210,6 +212,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
     g_last = mps_stats{};
     g_last.n = n;
+    g_launches = 0;
     if (n == 0) {
         if (tree && tree->counts) MPS_CUDA(cudaMemsetAsync(tree->counts, 0, 4 * sizeof(uint64_t), st));
         MPS_CUDA(cudaStreamSynchronize(st));
@@ -257,6 +260,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
         }
         MPS_CUDA(cudaGetLastError());
         MPS_CUDA(cudaStreamSynchronize(st));
+        g_last.launches = g_launches;
         return MPS_OK;
     }
 
@@ -289,6 +293,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
         uint32_t* level_off = reinterpret_cast<uint32_t*>(static_cast<char*>(d_ws) + plan.o_lvloff);
         if (hbm_total) {
             k_level_offsets<<<1, 32, 0, st>>>(ws.counters, level_off);
+            g_launches += 1;
             launch_bucket((uint32_t)hbm_total, level_off, ws, st);
         }
         if (h_ctr[kCtrFrontier]) {
@@ -310,8 +315,12 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
             uint32_t cnt = (uint32_t)h_ctr[kCtrHbmCount + p];
             uint64_t elems = h_ctr[kCtrHbmSize + p];
             lvl_bytes += (uint64_t)(2 * b * elems);
+            {
+                ProfScope ps("level_plan", (double)cnt * 64.0, st);
+                launch_level_plan<K>(it->second, cnt, k, keys_in, keys_out, g, ws, st);
+            }
             ProfScope ps("level_merge", 2.0 * b * (double)elems, st);
-            launch_level<K, V>(it->second, cnt, elems, k, keys_in, vals_in, keys_out, vals_out, g, ws, st);
+            launch_level_merge<K, V>(it->second, cnt, elems, k, keys_in, vals_in, keys_out, vals_out, g, ws, st);
         }
         g_last.bytes_levels = lvl_bytes;
         MPS_CUDA(cudaGetLastError());
@@ -337,6 +346,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     MPS_CUDA(cudaStreamSynchronize(st));
     if (status) return MPS_ERR_DEVICE_CHECK;
     g_last.bytes_fused = (uint64_t)(2 * b * (double)h_ctr[kCtrFrontierElems]);
+    g_last.launches = g_launches;
     return MPS_OK;
 }
 

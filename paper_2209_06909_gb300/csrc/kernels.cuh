@@ -86,6 +86,9 @@ struct MergeGeom {
 
 MergeGeom merge_geom(int key_bytes, bool vals, int k);
 
+// Number of kernels launched by this thread since the counter was last reset.
+extern thread_local uint64_t g_launches;
+
 // runs.cu
 template <typename K> void launch_detect(const K* keys, uint64_t n, const WsView& ws, cudaStream_t st);
 void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t st);
@@ -102,10 +105,13 @@ void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first,
 template <typename K, bool V>
 void launch_fused(const K* leaf_keys, const uint32_t* leaf_vals, K* out, uint32_t* vout, uint64_t n,
                   const MergeGeom& g, const WsView& ws, cudaStream_t st);
+template <typename K>
+void launch_level_plan(uint32_t level_off, uint32_t nnodes, int k, const K* leaf_keys, K* out, const MergeGeom& g,
+                       const WsView& ws, cudaStream_t st);
 template <typename K, bool V>
-void launch_level(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys,
-                  const uint32_t* leaf_vals, K* out, uint32_t* vout, const MergeGeom& g, const WsView& ws,
-                  cudaStream_t st);
+void launch_level_merge(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys,
+                        const uint32_t* leaf_vals, K* out, uint32_t* vout, const MergeGeom& g, const WsView& ws,
+                        cudaStream_t st);
 template <typename K, bool V>
 void launch_copy_single_run(const K* in, const uint32_t* vin, K* out, uint32_t* vout, uint64_t n,
                             const WsView& ws, cudaStream_t st);

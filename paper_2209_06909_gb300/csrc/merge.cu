@@ -598,24 +598,34 @@ void launch_fused(const K* leaf_keys, const uint32_t* leaf_vals, K* out, uint32_
     k_fused<K, V><<<grid, kMergeThreads, smem, st>>>(leaf_keys, leaf_vals, out, tmp, vout, ws.vals_tmp, ws.run_starts,
                                                      ws.run_desc, ws.powers, ws.fr_end, ws.fr_depth, ws.first_run,
                                                      g.c_fused, g.k, reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
+    g_launches += 1;
     (void)n;
 }
 
-template <typename K, bool V>
-void launch_level(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys,
-                  const uint32_t* leaf_vals, K* out, uint32_t* vout, const MergeGeom& g, const WsView& ws,
-                  cudaStream_t st) {
+template <typename K>
+void launch_level_plan(uint32_t level_off, uint32_t nnodes, int k, const K* leaf_keys, K* out, const MergeGeom& g,
+                       const WsView& ws, cudaStream_t st) {
     LevelNode* nodes = ws.nodes_lvl + level_off;
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
     k_level_prep<<<1, 1024, 0, st>>>(nodes, nnodes, ws.run_starts, g.ts, ws.counters);
     k_level_split<K><<<nnodes, 256, 0, st>>>(nodes, ws.run_starts, ws.run_desc, leaf_keys, out, tmp, g.ts, k,
                                               ws.unit_node, ws.split_tab);
+    g_launches += 2;
+}
+
+template <typename K, bool V>
+void launch_level_merge(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys,
+                        const uint32_t* leaf_vals, K* out, uint32_t* vout, const MergeGeom& g, const WsView& ws,
+                        cudaStream_t st) {
+    LevelNode* nodes = ws.nodes_lvl + level_off;
+    K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
     size_t smem = (size_t)2 * g.c_level * (sizeof(K) + (V ? 4 : 0));
     cudaFuncSetAttribute(k_level_merge<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     uint64_t bound = level_elems / g.ts + nnodes + 1;
     k_level_merge<K, V><<<(uint32_t)bound, kMergeThreads, smem, st>>>(
         nodes, ws.unit_node, ws.split_tab, ws.counters, ws.run_starts, ws.run_desc, leaf_keys, leaf_vals, out, tmp, vout,
         ws.vals_tmp, g.c_level, k, reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
+    g_launches += 1;
 }
 
 template <typename K, bool V>
@@ -623,13 +633,14 @@ void launch_copy_single_run(const K* in, const uint32_t* vin, K* out, uint32_t* 
                             cudaStream_t st) {
     uint32_t grid = (uint32_t)std::min<uint64_t>(ceil_div(n, 256), 152 * 8);
     k_copy_single_run<K, V><<<grid, 256, 0, st>>>(in, vin, out, vout, n, ws.run_desc);
+    g_launches += 1;
 }
 
 #define MPS_INST(K, V)                                                                                                  \
     template void launch_fused<K, V>(const K*, const uint32_t*, K*, uint32_t*, uint64_t, const MergeGeom&,             \
                                      const WsView&, cudaStream_t);                                                      \
-    template void launch_level<K, V>(uint32_t, uint32_t, uint64_t, int, const K*, const uint32_t*, K*, uint32_t*,      \
-                                     const MergeGeom&, const WsView&, cudaStream_t);                                    \
+    template void launch_level_merge<K, V>(uint32_t, uint32_t, uint64_t, int, const K*, const uint32_t*, K*, uint32_t*, \
+                                           const MergeGeom&, const WsView&, cudaStream_t);                              \
     template void launch_copy_single_run<K, V>(const K*, const uint32_t*, K*, uint32_t*, uint64_t, const WsView&,      \
                                                cudaStream_t);
 MPS_INST(uint32_t, false)
@@ -637,5 +648,9 @@ MPS_INST(uint32_t, true)
 MPS_INST(uint64_t, false)
 MPS_INST(uint64_t, true)
 #undef MPS_INST
+template void launch_level_plan<uint32_t>(uint32_t, uint32_t, int, const uint32_t*, uint32_t*, const MergeGeom&,
+                                          const WsView&, cudaStream_t);
+template void launch_level_plan<uint64_t>(uint32_t, uint32_t, int, const uint64_t*, uint64_t*, const MergeGeom&,
+                                          const WsView&, cudaStream_t);
 
 }  // namespace mps

@@ -216,6 +216,7 @@ void launch_detect(const K* keys, uint64_t n, const WsView& ws, cudaStream_t st)
     k_det_reduce<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.det_sum);
     k_det_scan<<<1, 1024, 0, st>>>(ws.det_sum, tiles, ws.det_pref, ws.counters, ws.run_starts, n);
     k_det_write<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.det_pref, ws.run_starts, ws.run_desc, ws.fr_end);
+    g_launches += 3;
 }
 
 template void launch_detect<uint32_t>(const uint32_t*, uint64_t, const WsView&, cudaStream_t);
@@ -231,6 +232,7 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
     k_powers<<<blocks, threads, 0, st>>>(ws.run_starts, ws.counters, n, w, magic, log2k, ws.powers,
                                           reinterpret_cast<unsigned long long*>(ws.counters + kCtrLevelBits),
                                           ws.first_run, ws.tfix, ws.windows);
+    g_launches += 1;
 }
 
 }  // namespace mps

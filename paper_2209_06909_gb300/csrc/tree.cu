@@ -465,6 +465,7 @@ void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st) {
         uint8_t* dst2 = (t + 2 < ws.nlv) ? ws.lv[t + 2] : nullptr;
         uint32_t pad_from = blocks, pad_to = (blocks + 31) / 32 * 32;
         k_mintree<<<blocks, 1024, 0, st>>>(ws.lv[t], src_len, ws.lv[t + 1], dst2, pad_from, pad_to);
+        g_launches += 1;
     }
 }
 
@@ -475,17 +476,20 @@ void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView&
     k_mask_scan<<<1, 1024, 0, st>>>(ws.mt_f, ws.mt_g, tiles, ws.mt_fpre, ws.mt_gsuf);
     k_mask_apply<<<tiles, kMaskThreads, 0, st>>>(ws.powers, r, ws.mt_fpre, ws.mt_gsuf, ws.node_info,
                                                   dump_leaf ? leaf_depth : nullptr);
+    g_launches += 3;
 }
 
 void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st) {
     uint32_t nb = r - 1;
     k_node_pass<<<(uint32_t)ceil_div(nb, 256), 256, 0, st>>>(make_mintree(ws), r, k, tmax, ws.run_starts, ws.node_info,
                                                               ws.counters, ws.nodes_raw, ws.nodes_cap, ws.fr_end, ws.fr_depth);
+    g_launches += 1;
 }
 
 void launch_bucket(uint32_t total, const uint32_t* level_off, const WsView& ws, cudaStream_t st) {
     if (!total) return;
     k_bucket<<<(uint32_t)ceil_div(total, 256), 256, 0, st>>>(ws.nodes_raw, total, level_off, ws.counters, ws.nodes_lvl);
+    g_launches += 1;
 }
 
 void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first, void* nodes, uint64_t* counts_out,
@@ -502,6 +506,7 @@ void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first,
         k_dump_nodes<<<(uint32_t)ceil_div(nb, 256), 256, 0, st>>>(T, r, k, ws.run_starts, ws.node_info, ws.canon_idx, node_first,
                                                                    reinterpret_cast<uint32_t*>(nodes),
                                                                    reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
+    g_launches += nodes ? 5 : 4;
 }
 
 }  // namespace mps

@@ -44,7 +44,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("r", ctypes.c_uint64), ("merge_cost", ctypes.c_uint64),
                 ("frontier_nodes", ctypes.c_uint64), ("hbm_nodes", ctypes.c_uint64),
                 ("num_levels", ctypes.c_uint32), ("hbm_levels", ctypes.c_uint32),
-                ("bytes_fused", ctypes.c_uint64), ("bytes_levels", ctypes.c_uint64)]
+                ("bytes_fused", ctypes.c_uint64), ("bytes_levels", ctypes.c_uint64), ("launches", ctypes.c_uint64)]
 
 
 EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_tree", "mps_sort_keys_host",
