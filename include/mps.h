@@ -123,6 +123,27 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
                               void* d_keys_in, void* d_keys_out, void* d_ws, size_t ws_bytes,
                               cudaStream_t stream);
 
+/* Sort without any device allocation by the caller or the library (no
+ * counterpart in the paper: this is a deployment convenience).  Meant for
+ * callers that cannot call cudaMalloc when they need a sort -- code running
+ * inside a memory pool it does not own, plugin hosts that forbid device
+ * allocations after start-up, or latency-critical paths where an allocation
+ * and its implicit synchronisation are not allowed.  The caller passes only
+ * its input and output arrays; the workspace is a 16 MiB scratch array
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.
+ *   n      : at most 2^20 keys (uint32 or uint64, any k in {2,4,8});
+ *            larger n returns MPS_ERR_WORKSPACE without touching the GPU.
+ *   Other arguments and outputs are those of mps_sort_keys (no tree output).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one scratch
+ * array, which keeps the previous call's contents (the sort clears what it
+ * needs zeroed), so calls that overlap on the GPU -- e.g. from two host
+ * threads or on two streams at once -- race and must be serialised. */
+mps_status mps_sort_keys_noalloc(const void* d_keys_in, void* d_keys_out, uint64_t n, mps_key_type kt, int k,
+                                 cudaStream_t stream);
+
 /* Per-kernel timing with CUDA events recorded on the launching stream.
  * mps_profile_enable(1) clears and starts recording; mps_profile_read fills
  * up to `cap` entries (kernel name, launches, total milliseconds) after

@@ -48,7 +48,10 @@ class Stats(ctypes.Structure):
 
 
 EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_tree", "mps_sort_keys_host",
-           "mps_profile_enable", "mps_profile_read", "mps_last_stats", "mps_status_string"]
+           "mps_profile_enable", "mps_profile_read", "mps_last_stats", "mps_status_string", "mps_sort_keys_noalloc"]
+
+# Largest n accepted by mps_sort_keys_noalloc (its scratch is compiled into the library).
+NOALLOC_MAX_N = 1 << 20
 
 _lib = None
 
@@ -72,6 +75,8 @@ def lib():
     L.mps_profile_read.argtypes = [P, I]
     L.mps_profile_read.restype = I
     L.mps_last_stats.argtypes = [P]
+    L.mps_sort_keys_noalloc.argtypes = [P, P, U64, I, I, P]
+    L.mps_sort_keys_noalloc.restype = I
     L.mps_status_string.argtypes = [I]
     L.mps_status_string.restype = ctypes.c_char_p
     for fn in ("mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_tree", "mps_sort_keys_host",
@@ -204,6 +209,15 @@ def sort_keys_host(h_in: torch.Tensor, h_out: torch.Tensor, d_in: torch.Tensor, 
     _check("mps_sort_keys_host", lib().mps_sort_keys_host(h_in.data_ptr(), h_out.data_ptr(), n, _key_type(h_in), k,
                                                           d_in.data_ptr(), d_out.data_ptr(), ws.data_ptr(),
                                                           ws.numel(), _stream(stream)))
+
+
+def sort_keys_noalloc(keys: torch.Tensor, out: torch.Tensor, k: int = 4, stream=None) -> torch.Tensor:
+    """Sorts up to NOALLOC_MAX_N keys with the library's built-in scratch
+    (mps_sort_keys_noalloc): for callers that cannot allocate device memory.
+    Calls that overlap on the GPU share that scratch and must be serialised."""
+    _check("mps_sort_keys_noalloc", lib().mps_sort_keys_noalloc(keys.data_ptr(), out.data_ptr(), keys.numel(),
+                                                                _key_type(keys), k, _stream(stream)))
+    return out
 
 
 def profile_enable(on: bool = True) -> None:
