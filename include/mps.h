@@ -129,7 +129,7 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
  * inside a memory pool it does not own, plugin hosts that forbid device
  * allocations after start-up, or latency-critical paths where an allocation
  * and its implicit synchronisation are not allowed.  The caller passes only
- * its input and output arrays; the workspace is a 16 MiB scratch array
+ * its input and output arrays; the workspace is a 32 MiB scratch array
  * compiled into the library, which every GPU that loads the library holds
  * until the process exits.
  *   n      : at most 2^20 keys (uint32 or uint64, any k in {2,4,8});

@@ -21,7 +21,7 @@
 namespace {
 
 constexpr uint64_t kNoAllocMaxN = 1ull << 20;                 // keys per call
-constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;     // 16 MiB
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;     // 32 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
