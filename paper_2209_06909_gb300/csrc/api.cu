@@ -39,22 +39,22 @@ struct Plan {
     bool vals = false;
     int k = 4;
     MergeGeom g{};
-    uint64_t rmax = 0, det_tiles = 0, mask_tiles = 0, windows = 0;
-    uint32_t nodes_cap = 0, unit_cap = 0;
+    uint64_t rmax = 0, det_tiles = 0, mask_tiles = 0;
+    uint32_t nodes_cap = 0, unit_cap = 0, fused_cap = 0;
     uint64_t lv_cap[kMinTreeLevels] = {};
     int nlv_max = 0;
     // offsets
-    size_t o_ctr, o_lvloff, o_det_sum, o_det_pref, o_rs, o_rdesc, o_fr_end, o_fr_depth, o_lv[kMinTreeLevels], o_info,
-        o_mt, o_first_run, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_hist, o_ktmp, o_vtmp, total;
+    size_t o_ctr, o_lvloff, o_det_sum, o_det_pref, o_rs, o_rdesc, o_fused, o_canon, o_lv[kMinTreeLevels], o_info,
+        o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_hist, o_ktmp, o_vtmp, total;
 
     explicit Plan(uint64_t n_, int kb_, bool vals_, int k_) : n(n_), kb(kb_), vals(vals_), k(k_) {
         g = merge_geom(kb, vals, k);
         rmax = n / 2 + 2;
         det_tiles = ceil_div(std::max<uint64_t>(n, 1), kDetTile);
         mask_tiles = ceil_div(rmax, kMaskTile);
-        windows = ceil_div(std::max<uint64_t>(n, 1), g.tfix) + 1;
         nodes_cap = (uint32_t)(34 * (n / g.tmax + 1) + 64);
         unit_cap = (uint32_t)(n / g.ts + n / g.tmax + 64);
+        fused_cap = (uint32_t)k * nodes_cap + 64;
         uint64_t len = rmax + 1;
         nlv_max = 0;
         while (true) {
@@ -71,16 +71,16 @@ struct Plan {
         o_det_pref = take(det_tiles * 8);
         o_rs = take((rmax + 2) * 4);
         o_rdesc = take(rmax + 1);
-        o_fr_end = take((rmax + 1) * 4);
-        o_fr_depth = take(rmax + 1);
+        o_fused = take((size_t)fused_cap * 16);
+        o_canon = take((rmax + 1) * 4);
         for (int t = 0; t < kMinTreeLevels; t++) o_lv[t] = t < nlv_max ? take(lv_cap[t]) : 0;
         o_info = take(rmax + 1);
         o_mt = take(mask_tiles * 8 * 4);
-        o_first_run = take((windows + 1) * 4);
         o_nodes_raw = take((size_t)nodes_cap * sizeof(LevelNode));
         o_nodes_lvl = take((size_t)nodes_cap * sizeof(LevelNode));
         o_unit_node = take((size_t)unit_cap * 4);
         o_split = take((size_t)(unit_cap + 1) * k * 4);
+        o_udesc = take((size_t)unit_cap * 128);
         o_hist = take(mask_tiles * kMaxLevels * 4);
         o_ktmp = take(n * kb);
         o_vtmp = vals ? take(n * 4) : o;
@@ -95,8 +95,8 @@ struct Plan {
         w.det_pref = reinterpret_cast<uint2*>(b + o_det_pref);
         w.run_starts = reinterpret_cast<uint32_t*>(b + o_rs);
         w.run_desc = reinterpret_cast<uint8_t*>(b + o_rdesc);
-        w.fr_end = reinterpret_cast<uint32_t*>(b + o_fr_end);
-        w.fr_depth = reinterpret_cast<uint8_t*>(b + o_fr_depth);
+        w.fused_list = reinterpret_cast<uint4*>(b + o_fused);
+        w.fused_cap = fused_cap;
         for (int t = 0; t < kMinTreeLevels; t++) w.lv[t] = t < nlv_max ? reinterpret_cast<uint8_t*>(b + o_lv[t]) : nullptr;
         w.powers = w.lv[0];
         w.node_info = reinterpret_cast<uint8_t*>(b + o_info);
@@ -105,16 +105,14 @@ struct Plan {
         w.mt_g = mt + mask_tiles;
         w.mt_fpre = mt + 2 * mask_tiles;
         w.mt_gsuf = mt + 3 * mask_tiles;
-        w.first_run = reinterpret_cast<uint32_t*>(b + o_first_run);
-        w.tfix = g.tfix;
-        w.windows = (uint32_t)windows;
         w.nodes_raw = reinterpret_cast<LevelNode*>(b + o_nodes_raw);
         w.nodes_lvl = reinterpret_cast<LevelNode*>(b + o_nodes_lvl);
         w.nodes_cap = nodes_cap;
         w.unit_node = reinterpret_cast<uint32_t*>(b + o_unit_node);
         w.split_tab = reinterpret_cast<uint32_t*>(b + o_split);
+        w.unit_desc = b + o_udesc;
         w.unit_cap = unit_cap;
-        w.canon_idx = w.fr_end;  // the tree dump runs after the merges no longer need fr_end
+        w.canon_idx = reinterpret_cast<uint32_t*>(b + o_canon);
         w.hist = reinterpret_cast<uint32_t*>(b + o_hist);
         w.keys_tmp = b + o_ktmp;
         w.vals_tmp = vals ? reinterpret_cast<uint32_t*>(b + o_vtmp) : nullptr;
@@ -283,7 +281,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     MPS_CUDA(cudaStreamSynchronize(st));
     if ((uint32_t)h_ctr[kCtrStatus]) return MPS_ERR_DEVICE_CHECK;
     const uint64_t hbm_total = h_ctr[kCtrHbmTotal];
-    if (hbm_total > plan.nodes_cap) return MPS_ERR_DEVICE_CHECK;
+    if (hbm_total > plan.nodes_cap || h_ctr[kCtrFrontier] > plan.fused_cap) return MPS_ERR_DEVICE_CHECK;
     g_last.merge_cost = h_ctr[kCtrM];
     g_last.frontier_nodes = h_ctr[kCtrFrontier];
     g_last.hbm_nodes = hbm_total;
@@ -299,7 +297,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
         if (h_ctr[kCtrFrontier]) {
             // algorithmic bytes: each element of a fused subtree is read and written once
             ProfScope ps("fused_merge", 2.0 * b * (double)h_ctr[kCtrFrontierElems], st);
-            launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, n, g, ws, st);
+            launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, h_ctr[kCtrFrontier], g, ws, st);
         }
         uint32_t off = 0;
         std::vector<std::pair<int, uint32_t>> levels;
@@ -317,7 +315,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
             lvl_bytes += (uint64_t)(2 * b * elems);
             {
                 ProfScope ps("level_plan", (double)cnt * 64.0, st);
-                launch_level_plan<K>(it->second, cnt, k, keys_in, keys_out, g, ws, st);
+                launch_level_plan<K>(it->second, cnt, elems, k, keys_in, keys_out, g, ws, st);
             }
             ProfScope ps("level_merge", 2.0 * b * (double)elems, st);
             launch_level_merge<K, V>(it->second, cnt, elems, k, keys_in, vals_in, keys_out, vals_out, g, ws, st);

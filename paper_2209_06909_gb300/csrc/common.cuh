@@ -78,6 +78,12 @@ __device__ __forceinline__ T block_scan_excl(T v, Op op, typename NoDeduce<T>::t
 }
 
 struct OpAdd32 { __device__ uint32_t operator()(uint32_t a, uint32_t b) const { return a + b; } };
+struct OpAddU64 {
+    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a + b; }
+};
+struct OpOrU64 {
+    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a | b; }
+};
 struct OpMax32 { __device__ uint32_t operator()(uint32_t a, uint32_t b) const { return a > b ? a : b; } };
 
 template <int NT>

@@ -11,7 +11,6 @@ constexpr int kDetTile = 4096;     // elements per run-detection tile
 constexpr int kMaskTile = 4096;    // boundaries per mask-scan tile
 constexpr int kMaxLevels = 64;     // bound on distinct powers (P <= 32 for n < 2^31)
 constexpr int kMinTreeLevels = 8;  // fan-out 32 min-tree over the powers
-constexpr int kMaxFrontierPerWindow = 512;
 
 // Indices into the 64-bit device counter block.
 enum : int {
@@ -19,7 +18,7 @@ enum : int {
     kCtrLevelBits = 1,  // bit p set if some boundary has power p
     kCtrM = 2,          // merge cost (sum of node sizes)
     kCtrHbmTotal = 3,   // number of nodes executed as level merges
-    kCtrFrontier = 4,   // number of fused subtrees
+    kCtrFrontier = 4,   // number of fused subtrees (entries of fused_list)
     kCtrStatus = 5,     // device error word (low 32 bits)
     kCtrNodes = 6,      // number of tree nodes
     kCtrUnits = 7,      // work units of the current level
@@ -27,6 +26,7 @@ enum : int {
     kCtrHbmSize = 72,   // [64] elements per power (level merges only)
     kCtrHbmFill = 136,  // [64] fill counters for bucketing
     kCtrFrontierElems = 200,  // elements inside fused subtrees
+    kCtrSplits = 201,   // splitters of the current level
     kCtrWords = 256
 };
 
@@ -39,7 +39,8 @@ struct __align__(16) LevelNode {
     uint32_t nunits;          // number of work units
     uint32_t b[9];            // child boundaries (run indices)
     uint8_t power, depth, degree, pad;
-    uint32_t pad2[2];
+    uint32_t split_off;       // first splitter of this node (per level)
+    uint32_t nsplit;          // number of splitters
 };
 static_assert(sizeof(LevelNode) == 64, "LevelNode layout");
 
@@ -49,8 +50,6 @@ struct WsView {
     uint2* det_pref;
     uint32_t* run_starts;
     uint8_t* run_desc;
-    uint32_t* fr_end;
-    uint8_t* fr_depth;
     uint8_t* lv[kMinTreeLevels];   // lv[0] = powers[0..r] (+ padding)
     uint32_t lv_len[kMinTreeLevels];
     int nlv;
@@ -60,13 +59,14 @@ struct WsView {
     unsigned long long* mt_g;
     unsigned long long* mt_fpre;
     unsigned long long* mt_gsuf;
-    uint32_t* first_run;           // window -> first run with start >= window start
-    uint32_t tfix, windows;
+    uint4* fused_list;             // fused subtrees: {first run, end run, depth, 0}
+    uint32_t fused_cap;
     LevelNode* nodes_raw;
     LevelNode* nodes_lvl;
     uint32_t nodes_cap;
     uint32_t* unit_node;
     uint32_t* split_tab;
+    void* unit_desc;               // 128-byte work-unit descriptors of the current level
     uint32_t unit_cap;
     uint32_t* canon_idx;           // dump: canonical index of each node start
     uint32_t* hist;                // dump: per-tile power histograms
@@ -77,11 +77,12 @@ struct WsView {
 // Sizes of the merge stages for one key/payload type.
 struct MergeGeom {
     uint32_t c_fused;   // elements of shared memory per fused tile
-    uint32_t tfix;      // window of frontier starts per fused tile
-    uint32_t tmax;      // largest fused subtree
+    uint32_t tmax;      // largest fused subtree (== c_fused)
     uint32_t c_level;   // elements per level-merge unit
     uint32_t ts;        // splitter spacing per child (c_level / k)
     int k;              // fan-in
+    uint32_t level_grid;  // blocks of the persistent level merge
+    uint32_t fused_grid;  // blocks of the persistent fused-subtree kernel
 };
 
 MergeGeom merge_geom(int key_bytes, bool vals, int k);
@@ -103,11 +104,11 @@ void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first,
 
 // merge.cu
 template <typename K, bool V>
-void launch_fused(const K* leaf_keys, const uint32_t* leaf_vals, K* out, uint32_t* vout, uint64_t n,
+void launch_fused(const K* leaf_keys, const uint32_t* leaf_vals, K* out, uint32_t* vout, uint64_t nfused,
                   const MergeGeom& g, const WsView& ws, cudaStream_t st);
 template <typename K>
-void launch_level_plan(uint32_t level_off, uint32_t nnodes, int k, const K* leaf_keys, K* out, const MergeGeom& g,
-                       const WsView& ws, cudaStream_t st);
+void launch_level_plan(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys, K* out,
+                       const MergeGeom& g, const WsView& ws, cudaStream_t st);
 template <typename K, bool V>
 void launch_level_merge(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys,
                         const uint32_t* leaf_vals, K* out, uint32_t* vout, const MergeGeom& g, const WsView& ws,

@@ -33,11 +33,48 @@ namespace mps {
 
 namespace {
 
-constexpr int kMergeThreads = 512;
-constexpr int kIPT = 8;
+constexpr int kFusedThreads = 256;
+// outputs per thread in a merge pass; odd, so that the lanes of a warp touch
+// 32 different shared-memory banks when they walk their outputs in step
+constexpr int kIPT = 15;
 constexpr uint32_t kNoMid = 0xFFFFu;
-// boundary-list entries one thread holds while compacting: ceil((C/2 + 8) / 512)
-constexpr int kKeepMax = 24;
+// boundary-list entries one thread holds while compacting: ceil((C/2 + 8) / 256), odd
+constexpr int kKeepMax = 25;
+
+// Number of elements of A = src[s..m) among the first `diag` outputs of the
+// stable merge of A and B = src[m..e) (A first on equal keys): merge path.
+template <typename K>
+__device__ __forceinline__ uint32_t merge_path(const K* __restrict__ src, uint32_t s, uint32_t m, uint32_t e, uint32_t diag) {
+    const uint32_t na = m - s, nbn = e - m;
+    uint32_t l = diag > nbn ? diag - nbn : 0u, h = min(diag, na);
+    while (l < h) {
+        const uint32_t mid = (l + h) >> 1;
+        if (src[s + mid] <= src[m + diag - 1 - mid]) l = mid + 1; else h = mid;
+    }
+    return l;
+}
+
+// Writes outputs [o, stop) of the stable merge of src[ia..m) and src[ib..e)
+// (ties to A).  Branch-free: every step loads the next element of the side it
+// took; reads are clamped to e - 1 so they stay inside the buffer.
+template <typename K, bool V>
+__device__ __forceinline__ void serial_merge(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
+                                             uint32_t* __restrict__ vdst, uint32_t ia, uint32_t m, uint32_t ib, uint32_t e,
+                                             uint32_t o, uint32_t stop) {
+    const uint32_t last = e - 1;
+    K ka = src[min(ia, last)];
+    K kb = src[min(ib, last)];
+    for (; o < stop; o++) {
+        const bool take_a = (ib >= e) || (ia < m && ka <= kb);
+        dst[o] = take_a ? ka : kb;
+        if (V) vdst[o] = vsrc[take_a ? ia : ib];
+        ia += take_a ? 1u : 0u;
+        ib += take_a ? 0u : 1u;
+        const K kn = src[min(take_a ? ia : ib, last)];
+        ka = take_a ? kn : ka;
+        kb = take_a ? kb : kn;
+    }
+}
 
 // One pass of stable 2-way merges over [0, len): segment i covers
 // [seg_start[i], seg_start[i+1]) and merges its halves at seg_mid[i], or is
@@ -46,12 +83,12 @@ template <typename K, bool V>
 __device__ __forceinline__ void merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
                                            uint32_t* __restrict__ vdst, uint32_t len, const uint16_t* __restrict__ seg_start,
                                            const uint16_t* __restrict__ seg_mid, uint32_t ns) {
-    for (uint32_t base = threadIdx.x * kIPT; base < len; base += kMergeThreads * kIPT) {
+    for (uint32_t base = threadIdx.x * kIPT; base < len; base += kFusedThreads * kIPT) {
         uint32_t o = base;
         const uint32_t oe = min(base + (uint32_t)kIPT, len);
         uint32_t lo = 0, hi = ns;
         while (hi - lo > 1) {
-            uint32_t m = (lo + hi) >> 1;
+            const uint32_t m = (lo + hi) >> 1;
             if (seg_start[m] <= o) lo = m; else hi = m;
         }
         uint32_t i = lo;
@@ -64,37 +101,24 @@ __device__ __forceinline__ void merge_pass(const K* __restrict__ src, K* __restr
                     if (V) vdst[o] = vsrc[o];
                 }
             } else {
-                const uint32_t na = m - s, nbn = e - m, diag = o - s;
-                uint32_t l = diag > nbn ? diag - nbn : 0u, h = min(diag, na);
-                while (l < h) {
-                    uint32_t mid = (l + h) >> 1;
-                    if (src[s + mid] <= src[m + diag - 1 - mid]) l = mid + 1; else h = mid;
-                }
-                uint32_t ia = s + l, ib = m + diag - l;
-                K ka = ia < m ? src[ia] : K(0);
-                K kb = ib < e ? src[ib] : K(0);
-                for (; o < stop; o++) {
-                    bool take_a = ia < m && (ib >= e || ka <= kb);
-                    if (take_a) {
-                        dst[o] = ka;
-                        if (V) vdst[o] = vsrc[ia];
-                        ia++;
-                        ka = ia < m ? src[ia] : K(0);
-                    } else {
-                        dst[o] = kb;
-                        if (V) vdst[o] = vsrc[ib];
-                        ib++;
-                        kb = ib < e ? src[ib] : K(0);
-                    }
-                }
+                const uint32_t l = merge_path(src, s, m, e, o - s);
+                serial_merge<K, V>(src, dst, vsrc, vdst, s + l, m, m + (o - s) - l, e, o, stop);
+                o = stop;
             }
             i++;
         }
     }
 }
 
+// Items per thread for a blocked loop over m items: ceil(m / threads), rounded
+// up to an odd number (conflict-free shared-memory strides).
+__device__ __forceinline__ uint32_t odd_chunk(uint32_t m) {
+    uint32_t per = (m + kFusedThreads - 1) / kFusedThreads;
+    return per | 1u;
+}
+
 // Entry of the shared-memory boundary list: bits 0..15 element offset,
-// 16..23 power (0 = never merged here), 24..31 index q within its group.
+// 16..23 power, 24..31 index q within its group of equal powers.
 __device__ __forceinline__ uint32_t be_off(uint32_t e) { return e & 0xFFFFu; }
 __device__ __forceinline__ uint32_t be_pow(uint32_t e) { return (e >> 16) & 0xFFu; }
 __device__ __forceinline__ uint32_t be_q(uint32_t e) { return e >> 24; }
@@ -105,22 +129,35 @@ struct OpSegCount {
         return (Y & 0x80000000u) ? Y : ((X & 0x80000000u) | ((X & 0x7FFFFFFFu) + Y));
     }
 };
+// (segmented count, plain count)
+struct OpQ {
+    __device__ uint4 operator()(uint4 X, uint4 Y) const { return make_uint4(OpSegCount()(X.x, Y.x), X.y + Y.y, 0u, 0u); }
+};
+struct OpMax2 {
+    __device__ uint4 operator()(uint4 X, uint4 Y) const { return make_uint4(max(X.x, Y.x), max(X.y, Y.y), 0u, 0u); }
+};
 
 template <typename K, bool V>
-struct SmemLayout {
+struct FusedSmem {
     static __host__ __device__ size_t bytes(uint32_t C) {
-        uint32_t bmax = C / 2 + 8;
+        const uint32_t bmax = C / 2 + 8;
         return (size_t)2 * C * sizeof(K) + (V ? (size_t)2 * C * 4 : 0) + (size_t)2 * bmax * 4;
     }
 };
 
+// Fused subtrees: persistent blocks over the list of maximal subtrees of at
+// most C elements.  A block loads one subtree (reversing strictly descending
+// runs), executes all its levels in shared memory, largest power first, and
+// writes the subtree root's output.  Level p: the boundaries of power p form
+// groups between boundaries of smaller power (one group = one node); the
+// group index q of each boundary gives the tournament round ctz(q) in which
+// its two sides meet.
 template <typename K, bool V>
-__global__ void __launch_bounds__(kMergeThreads, 1)
-    k_fused(const K* __restrict__ leaf, const uint32_t* __restrict__ vleaf, K* __restrict__ out0, K* __restrict__ out1,
-            uint32_t* __restrict__ vout0, uint32_t* __restrict__ vout1, const uint32_t* __restrict__ rs,
-            const uint8_t* __restrict__ rdesc, const uint8_t* __restrict__ P, const uint32_t* __restrict__ fr_end,
-            const uint8_t* __restrict__ fr_depth, const uint32_t* __restrict__ first_run, uint32_t C, int k,
-            uint32_t* __restrict__ status) {
+__global__ void __launch_bounds__(kFusedThreads)
+    k_fused(const uint4* __restrict__ flist, const uint64_t* __restrict__ ctr, const K* __restrict__ leaf,
+            const uint32_t* __restrict__ vleaf, K* __restrict__ out0, K* __restrict__ out1, uint32_t* __restrict__ vout0,
+            uint32_t* __restrict__ vout1, const uint32_t* __restrict__ rs, const uint8_t* __restrict__ rdesc,
+            const uint8_t* __restrict__ P, uint32_t C, int k, uint32_t* __restrict__ status) {
     extern __shared__ uint4 smem_raw[];
     const uint32_t BMAX = C / 2 + 8;
     K* kA = reinterpret_cast<K*>(smem_raw);
@@ -129,226 +166,172 @@ __global__ void __launch_bounds__(kMergeThreads, 1)
     uint32_t* vB = V ? vA + C : nullptr;
     uint32_t* bl0 = V ? (vB + C) : reinterpret_cast<uint32_t*>(kB + C);
     uint32_t* bl1 = bl0 + BMAX;
-    __shared__ uint32_t fl_lo[kMaxFrontierPerWindow];
-    __shared__ uint32_t fl_hi[kMaxFrontierPerWindow];
-    __shared__ uint32_t stmp[kMergeThreads / 32 + 1];
-    __shared__ uint32_t sh_total;
-
+    __shared__ uint32_t stmp[kFusedThreads / 32 + 1];
+    __shared__ uint4 stmp4[kFusedThreads / 32 + 1];
     const uint32_t tid = threadIdx.x;
-    const uint32_t ra = first_run[blockIdx.x], rb = first_run[blockIdx.x + 1];
-    if (ra >= rb) return;
+    const uint32_t F = (uint32_t)ctr[kCtrFrontier];
 
-    // ---- 1. frontier nodes starting in this window (ordered compaction)
-    const uint32_t nw = rb - ra;
-    uint32_t per = (nw + kMergeThreads - 1) / kMergeThreads;
-    uint32_t w0 = min(nw, tid * per), w1 = min(nw, w0 + per);
-    uint32_t cnt = 0;
-    for (uint32_t q = w0; q < w1; q++) cnt += fr_end[ra + q] != 0;
-    uint32_t F;
-    uint32_t pos = block_sum_excl<kMergeThreads>(cnt, stmp, &F);
-    if (F == 0) return;
-    if (F > (uint32_t)kMaxFrontierPerWindow) {
-        if (tid == 0) dev_fail(status, kDevCapacity);
-        return;
-    }
-    for (uint32_t q = w0; q < w1; q++) {
-        uint32_t R = fr_end[ra + q];
-        if (R) {
-            fl_lo[pos] = ra + q;
-            fl_hi[pos] = R | ((uint32_t)(fr_depth[ra + q] & 1u) << 31);
-            pos++;
+    for (uint32_t f = blockIdx.x; f < F; f += gridDim.x) {
+        const uint4 fr = flist[f];
+        const uint32_t L = fr.x, R = fr.y;
+        const bool odd = fr.z & 1u;
+        const uint32_t s_lo = rs[L];
+        const uint32_t len = rs[R] - s_lo;
+        if (len > C) {
+            if (tid == 0) dev_fail(status, kDevRange);
+            return;
         }
-    }
-    __syncthreads();
-    const uint32_t lo_run = fl_lo[0];
-    const uint32_t hi_run = fl_hi[F - 1] & 0x7FFFFFFFu;
-    const uint32_t s_lo = rs[lo_run];
-    const uint32_t len = rs[hi_run] - s_lo;
-    if (len > C) {
-        if (tid == 0) dev_fail(status, kDevRange);
-        return;
-    }
-    const uint32_t nruns = hi_run - lo_run;
-    const uint32_t nb = nruns - 1;
+        const uint32_t nruns = R - L;
+        const uint32_t nb = nruns - 1;
 
-    // ---- 2. boundary list; boundaries outside every frontier node never merge
-    int8_t* mk = reinterpret_cast<int8_t*>(kB);
-    for (uint32_t e = tid; e < nb; e += kMergeThreads) mk[e] = 0;
-    __syncthreads();
-    for (uint32_t f = tid; f < F; f += kMergeThreads) {
-        uint32_t L = fl_lo[f], R = fl_hi[f] & 0x7FFFFFFFu;
-        mk[L - lo_run] = 1;
-        if (R - lo_run - 1 < nb) mk[R - lo_run - 1] = -1;
-    }
-    __syncthreads();
-    per = (nb + kMergeThreads - 1) / kMergeThreads;
-    uint32_t e0 = min(nb, tid * per), e1 = min(nb, e0 + per);
-    {
-        uint32_t s = 0;
-        for (uint32_t e = e0; e < e1; e++) s += (uint32_t)(int32_t)mk[e];
-        uint32_t run = block_sum_excl<kMergeThreads>(s, stmp, nullptr);
-        for (uint32_t e = e0; e < e1; e++) {
-            run += (uint32_t)(int32_t)mk[e];
-            uint32_t j = lo_run + 1 + e;
-            uint32_t p = (int32_t)run > 0 ? P[j] : 0u;
-            bl0[e] = (rs[j] - s_lo) | (p << 16);
+        // ---- load boundaries, keys and run directions
+        for (uint32_t e = tid; e < nb; e += kFusedThreads) {
+            const uint32_t j = L + 1 + e;
+            bl0[e] = (rs[j] - s_lo) | ((uint32_t)P[j] << 16);
         }
-    }
-    // frontier ranges as element offsets (+ output parity)
-    __syncthreads();
-    for (uint32_t f = tid; f < F; f += kMergeThreads) {
-        uint32_t L = fl_lo[f], h = fl_hi[f];
-        fl_lo[f] = rs[L] - s_lo;
-        fl_hi[f] = (rs[h & 0x7FFFFFFFu] - s_lo) | (h & 0x80000000u);
-    }
-
-    // ---- 3. load the keys, then reverse the strictly descending runs
-    for (uint32_t x = tid; x < len; x += kMergeThreads) {
-        kA[x] = leaf[s_lo + x];
-        if (V) vA[x] = vleaf[s_lo + x];
-    }
-    uint8_t* dflag = reinterpret_cast<uint8_t*>(bl1);
-    for (uint32_t q = tid; q < nruns; q += kMergeThreads) dflag[q] = rdesc[lo_run + q];
-    __syncthreads();
-    {
-        uint32_t pe = (len + kMergeThreads - 1) / kMergeThreads;
-        uint32_t x0 = min(len, tid * pe), x1 = min(len, x0 + pe);
-        if (x0 < x1) {
-            uint32_t lo = 0, hi = nb;  // runs before x0: boundaries with offset <= x0
-            while (lo < hi) {
-                uint32_t m = (lo + hi) >> 1;
-                if (be_off(bl0[m]) <= x0) lo = m + 1; else hi = m;
-            }
-            uint32_t rho = lo;
-            uint32_t rs0 = rho ? be_off(bl0[rho - 1]) : 0u;
-            uint32_t re0 = rho < nb ? be_off(bl0[rho]) : len;
-            for (uint32_t x = x0; x < x1; x++) {
-                while (x >= re0) {
-                    rho++;
-                    rs0 = re0;
-                    re0 = rho < nb ? be_off(bl0[rho]) : len;
-                }
-                uint32_t src = dflag[rho] ? (rs0 + re0 - 1 - x) : x;
-                kB[x] = kA[src];
-                if (V) vB[x] = vA[src];
-            }
+        for (uint32_t x = tid; x < len; x += kFusedThreads) {
+            kA[x] = leaf[s_lo + x];
+            if (V) vA[x] = vleaf[s_lo + x];
         }
-    }
-    __syncthreads();
-    K* cur = kB;
-    K* oth = kA;
-    uint32_t* vcur = vB;
-    uint32_t* voth = vA;
-
-    // ---- 4. levels of the subtrees, largest power first
-    uint32_t pmax = 0, pmin = 255;
-    for (uint32_t e = e0; e < e1; e++) {
-        uint32_t p = be_pow(bl0[e]);
-        if (p) { pmax = max(pmax, p); pmin = min(pmin, p); }
-    }
-    pmax = block_reduce<kMergeThreads>(pmax, OpMax32(), 0u, stmp);
-    pmin = 255u - block_reduce<kMergeThreads>(255u - pmin, OpMax32(), 0u, stmp);
-    uint32_t na = nb;
-    uint16_t* seg_start = reinterpret_cast<uint16_t*>(bl1);
-    uint16_t* seg_mid = seg_start + BMAX + 2;
-
-    for (uint32_t p = pmax; p >= pmin && p >= 1; p--) {
-        per = (na + kMergeThreads - 1) / kMergeThreads;
-        e0 = min(na, tid * per);
-        e1 = min(na, e0 + per);
-        // group index q of every power-p boundary
-        uint32_t acc = 0;
-        for (uint32_t e = e0; e < e1; e++) {
-            uint32_t pw = be_pow(bl0[e]);
-            uint32_t x = pw < p ? 0x80000000u : (pw == p ? 1u : 0u);
-            acc = OpSegCount()(acc, x);
-        }
-        uint32_t pre = block_scan_excl<kMergeThreads, false>(acc, OpSegCount(), 0u, stmp, nullptr);
-        uint32_t neq = 0;
-        for (uint32_t e = e0; e < e1; e++) {
-            uint32_t v = bl0[e];
-            uint32_t pw = be_pow(v);
-            uint32_t x = pw < p ? 0x80000000u : (pw == p ? 1u : 0u);
-            pre = OpSegCount()(pre, x);
-            if (pw == p) {
-                bl0[e] = (v & 0x00FFFFFFu) | ((pre & 0x7FFFFFFFu) << 24);
-                neq++;
-            }
-        }
-        neq = block_reduce<kMergeThreads>(neq, OpAdd32(), 0u, stmp);
-        if (neq == 0) continue;
-        // tournament rounds
-        for (uint32_t t = 0; (1u << t) < (uint32_t)k; t++) {
-            uint32_t nd = 0, nm = 0;
-            for (uint32_t e = e0; e < e1; e++) {
-                uint32_t v = bl0[e];
-                uint32_t pw = be_pow(v);
-                uint32_t cz = pw == p ? (uint32_t)__ffs(be_q(v)) - 1 : 0u;
-                nd += (pw < p) || (pw == p && cz > t);
-                nm += (pw == p && cz == t);
-            }
-            uint32_t ndel;
-            uint32_t dpos = block_sum_excl<kMergeThreads>(nd, stmp, &ndel);
-            uint32_t nmt = block_reduce<kMergeThreads>(nm, OpAdd32(), 0u, stmp);
-            if (nmt == 0) break;
-            const uint32_t ns = ndel + 1;
-            for (uint32_t i = tid; i < ns; i += kMergeThreads) seg_mid[i] = (uint16_t)kNoMid;
-            if (tid == 0) {
-                seg_start[0] = 0;
-                seg_start[ns] = (uint16_t)len;
-            }
-            for (uint32_t e = e0; e < e1; e++) {
-                uint32_t v = bl0[e];
-                uint32_t pw = be_pow(v);
-                uint32_t cz = pw == p ? (uint32_t)__ffs(be_q(v)) - 1 : 0u;
-                if ((pw < p) || (pw == p && cz > t)) seg_start[1 + dpos++] = (uint16_t)be_off(v);
-            }
-            __syncthreads();
-            dpos -= nd;
-            for (uint32_t e = e0; e < e1; e++) {
-                uint32_t v = bl0[e];
-                uint32_t pw = be_pow(v);
-                uint32_t cz = pw == p ? (uint32_t)__ffs(be_q(v)) - 1 : 0u;
-                bool del = (pw < p) || (pw == p && cz > t);
-                if (pw == p && cz == t) seg_mid[dpos] = (uint16_t)be_off(v);
-                dpos += del;
-            }
-            __syncthreads();
-            merge_pass<K, V>(cur, oth, vcur, voth, len, seg_start, seg_mid, ns);
-            __syncthreads();
-            K* tk = cur; cur = oth; oth = tk;
-            uint32_t* tv = vcur; vcur = voth; voth = tv;
-        }
-        // drop the boundaries consumed at this level
-        uint32_t keep[kKeepMax];
-        uint32_t nk = 0;
-        for (uint32_t e = e0; e < e1; e++) {
-            uint32_t v = bl0[e];
-            if (be_pow(v) < p) keep[nk++] = v & 0x00FFFFFFu;
-        }
-        uint32_t ntot;
-        uint32_t kpos = block_sum_excl<kMergeThreads>(nk, stmp, &ntot);
-        for (uint32_t q = 0; q < nk; q++) bl0[kpos + q] = keep[q];
-        na = ntot;
+        uint8_t* dflag = reinterpret_cast<uint8_t*>(bl1);
+        for (uint32_t q = tid; q < nruns; q += kFusedThreads) dflag[q] = rdesc[L + q];
         __syncthreads();
-    }
 
-    // ---- 5. write every frontier node's output
-    for (uint32_t x = tid; x < len; x += kMergeThreads) {
-        uint32_t lo = 0, hi = F;
-        while (hi - lo > 1) {
-            uint32_t m = (lo + hi) >> 1;
-            if (fl_lo[m] <= x) lo = m; else hi = m;
-        }
-        uint32_t h = fl_hi[lo];
-        if (x >= fl_lo[lo] && x < (h & 0x7FFFFFFFu)) {
-            K* o = (h >> 31) ? out1 : out0;
-            o[s_lo + x] = cur[x];
-            if (V) {
-                uint32_t* vo = (h >> 31) ? vout1 : vout0;
-                vo[s_lo + x] = vcur[x];
+        // ---- reverse the strictly descending runs (kA -> kB)
+        {
+            const uint32_t pe = odd_chunk(len);
+            const uint32_t x0 = min(len, tid * pe), x1 = min(len, x0 + pe);
+            if (x0 < x1) {
+                uint32_t lo = 0, hi = nb;  // runs before x0: boundaries with offset <= x0
+                while (lo < hi) {
+                    const uint32_t m = (lo + hi) >> 1;
+                    if (be_off(bl0[m]) <= x0) lo = m + 1; else hi = m;
+                }
+                uint32_t rho = lo;
+                uint32_t rs0 = rho ? be_off(bl0[rho - 1]) : 0u;
+                uint32_t re0 = rho < nb ? be_off(bl0[rho]) : len;
+                for (uint32_t x = x0; x < x1; x++) {
+                    while (x >= re0) {
+                        rho++;
+                        rs0 = re0;
+                        re0 = rho < nb ? be_off(bl0[rho]) : len;
+                    }
+                    const uint32_t src = dflag[rho] ? (rs0 + re0 - 1 - x) : x;
+                    kB[x] = kA[src];
+                    if (V) vB[x] = vA[src];
+                }
             }
         }
+
+        // ---- range of powers in the subtree
+        uint32_t per = odd_chunk(nb);
+        uint32_t e0 = min(nb, tid * per), e1 = min(nb, e0 + per);
+        uint32_t pmax, pmin;
+        {
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            for (uint32_t e = e0; e < e1; e++) {
+                const uint32_t p = be_pow(bl0[e]);
+                v.x = max(v.x, p);
+                v.y = max(v.y, 255u - p);
+            }
+            const uint4 t = block_reduce<kFusedThreads>(v, OpMax2(), make_uint4(0u, 0u, 0u, 0u), stmp4);
+            pmax = t.x;
+            pmin = 255u - t.y;
+        }
+        K* cur = kB;
+        K* oth = kA;
+        uint32_t* vcur = vB;
+        uint32_t* voth = vA;
+        uint32_t na = nb;
+        uint16_t* seg_start = reinterpret_cast<uint16_t*>(bl1);
+        uint16_t* seg_mid = seg_start + BMAX + 2;
+
+        for (uint32_t p = pmax; p >= pmin && p >= 1; p--) {
+            per = odd_chunk(na);
+            e0 = min(na, tid * per);
+            e1 = min(na, e0 + per);
+            // group index q of every power-p boundary (segmented count), and their number
+            uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+            for (uint32_t e = e0; e < e1; e++) {
+                const uint32_t pw = be_pow(bl0[e]);
+                acc = OpQ()(acc, make_uint4(pw < p ? 0x80000000u : (pw == p ? 1u : 0u), pw == p ? 1u : 0u, 0u, 0u));
+            }
+            uint4 tot;
+            const uint4 pre = block_scan_excl<kFusedThreads, false>(acc, OpQ(), make_uint4(0u, 0u, 0u, 0u), stmp4, &tot);
+            if (tot.y == 0) continue;
+            {
+                uint32_t run = pre.x;
+                for (uint32_t e = e0; e < e1; e++) {
+                    const uint32_t v = bl0[e];
+                    const uint32_t pw = be_pow(v);
+                    run = OpSegCount()(run, pw < p ? 0x80000000u : (pw == p ? 1u : 0u));
+                    if (pw == p) bl0[e] = (v & 0x00FFFFFFu) | ((run & 0x7FFFFFFFu) << 24);
+                }
+            }
+            // tournament rounds
+            for (uint32_t t = 0; (1u << t) < (uint32_t)k; t++) {
+                uint32_t nd = 0, nm = 0;
+                for (uint32_t e = e0; e < e1; e++) {
+                    const uint32_t v = bl0[e];
+                    const uint32_t pw = be_pow(v);
+                    const uint32_t cz = pw == p ? (uint32_t)__ffs(be_q(v)) - 1 : 0u;
+                    nd += (pw < p) || (pw == p && cz > t);
+                    nm += (pw == p && cz == t);
+                }
+                uint32_t tot2;
+                const uint32_t dp = block_sum_excl<kFusedThreads>(nd | (nm << 16), stmp, &tot2);
+                if ((tot2 >> 16) == 0) break;
+                const uint32_t ns = (tot2 & 0xFFFFu) + 1;
+                for (uint32_t i = tid; i < ns; i += kFusedThreads) seg_mid[i] = (uint16_t)kNoMid;
+                if (tid == 0) {
+                    seg_start[0] = 0;
+                    seg_start[ns] = (uint16_t)len;
+                }
+                uint32_t dpos = dp & 0xFFFFu;
+                for (uint32_t e = e0; e < e1; e++) {
+                    const uint32_t v = bl0[e];
+                    const uint32_t pw = be_pow(v);
+                    const uint32_t cz = pw == p ? (uint32_t)__ffs(be_q(v)) - 1 : 0u;
+                    if ((pw < p) || (pw == p && cz > t)) seg_start[1 + dpos++] = (uint16_t)be_off(v);
+                }
+                __syncthreads();
+                dpos = dp & 0xFFFFu;
+                for (uint32_t e = e0; e < e1; e++) {
+                    const uint32_t v = bl0[e];
+                    const uint32_t pw = be_pow(v);
+                    const uint32_t cz = pw == p ? (uint32_t)__ffs(be_q(v)) - 1 : 0u;
+                    const bool del = (pw < p) || (pw == p && cz > t);
+                    if (pw == p && cz == t) seg_mid[dpos] = (uint16_t)be_off(v);
+                    dpos += del;
+                }
+                __syncthreads();
+                merge_pass<K, V>(cur, oth, vcur, voth, len, seg_start, seg_mid, ns);
+                __syncthreads();
+                K* tk = cur; cur = oth; oth = tk;
+                uint32_t* tv = vcur; vcur = voth; voth = tv;
+            }
+            // drop the boundaries consumed at this level
+            uint32_t keep[kKeepMax];
+            uint32_t nk = 0;
+            for (uint32_t e = e0; e < e1; e++) {
+                const uint32_t v = bl0[e];
+                if (be_pow(v) < p) keep[nk++] = v & 0x00FFFFFFu;
+            }
+            uint32_t ntot;
+            const uint32_t kpos = block_sum_excl<kFusedThreads>(nk, stmp, &ntot);
+            for (uint32_t q = 0; q < nk; q++) bl0[kpos + q] = keep[q];
+            na = ntot;
+            __syncthreads();
+        }
+
+        // ---- the subtree's output
+        K* o = odd ? out1 : out0;
+        uint32_t* vo = odd ? vout1 : vout0;
+        for (uint32_t x = tid; x < len; x += kFusedThreads) {
+            o[s_lo + x] = cur[x];
+            if (V) vo[s_lo + x] = vcur[x];
+        }
+        __syncthreads();
     }
 }
 
@@ -377,188 +360,289 @@ __device__ __forceinline__ K child_get(const Child& ch, const K* leaf, const K* 
     return inner[ch.base + pos];
 }
 
+__device__ __forceinline__ uint32_t node_splitters(const LevelNode& nd, const uint32_t* rs, uint32_t ts) {
+    uint32_t s = 0;
+    for (int c = 0; c < nd.degree; c++) {
+        uint32_t len = rs[nd.b[c + 1]] - rs[nd.b[c]];
+        uint32_t m = (len + ts - 1) / ts;
+        s += m > 0 ? m - 1 : 0;
+    }
+    return s;
+}
+
+// Per node of the level: number of splitters and work units (one unit more
+// than splitters), their offsets, and unit_node for each node's first unit.
 __global__ void __launch_bounds__(1024) k_level_prep(LevelNode* __restrict__ nodes, uint32_t nn, const uint32_t* __restrict__ rs,
-                                                     uint32_t ts, uint64_t* __restrict__ ctr) {
+                                                     uint32_t ts, uint64_t* __restrict__ ctr, uint32_t* __restrict__ unit_node) {
     __shared__ uint32_t tmp[1024 / 32 + 1];
     uint32_t per = (nn + 1023) / 1024;
     uint32_t b = min(nn, threadIdx.x * per), e = min(nn, b + per);
     uint32_t acc = 0;
-    for (uint32_t v = b; v < e; v++) {
-        const LevelNode& nd = nodes[v];
-        uint32_t s = 0;
-        for (int c = 0; c < nd.degree; c++) {
-            uint32_t len = rs[nd.b[c + 1]] - rs[nd.b[c]];
-            uint32_t m = (len + ts - 1) / ts;
-            s += m > 0 ? m - 1 : 0;
-        }
-        acc += s + 1;
-    }
+    for (uint32_t v = b; v < e; v++) acc += node_splitters(nodes[v], rs, ts);
     uint32_t tot;
     uint32_t pre = block_sum_excl<1024>(acc, tmp, &tot);
     for (uint32_t v = b; v < e; v++) {
         LevelNode& nd = nodes[v];
-        uint32_t s = 0;
-        for (int c = 0; c < nd.degree; c++) {
-            uint32_t len = rs[nd.b[c + 1]] - rs[nd.b[c]];
-            uint32_t m = (len + ts - 1) / ts;
-            s += m > 0 ? m - 1 : 0;
-        }
-        nd.unit_off = pre;
+        uint32_t s = node_splitters(nd, rs, ts);
+        nd.split_off = pre;
+        nd.nsplit = s;
+        nd.unit_off = pre + v;   // units of node v: splitters before it plus one per earlier node
         nd.nunits = s + 1;
-        pre += s + 1;
+        unit_node[pre + v] = v;
+        pre += s;
     }
-    if (threadIdx.x == 0) ctr[kCtrUnits] = tot;
+    if (threadIdx.x == 0) {
+        ctr[kCtrSplits] = tot;
+        ctr[kCtrUnits] = tot + nn;
+    }
 }
 
-// One block per node: fills unit -> node and the splitter table.  Splitter g
-// of the node is element (m+1)*ts of child c; k lanes compute its position in
-// every child under the order (key, child, position) and its slot among the
-// node's splitters in that order.
+// k lanes per splitter, all splitters of the level across the grid.  Splitter
+// g of node v is element (m+1)*ts of child c; lane c' finds its position in
+// child c' under the order (key, child, position); the k positions give the
+// splitter's slot among the node's splitters, i.e. the work unit it starts.
 template <typename K>
-__global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ rs,
+__global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict__ nodes, uint32_t nn,
+                                                     const uint64_t* __restrict__ ctr, const uint32_t* __restrict__ rs,
                                                      const uint8_t* __restrict__ rdesc, const K* __restrict__ leaf,
                                                      const K* __restrict__ buf0, const K* __restrict__ buf1, uint32_t ts, int k,
                                                      uint32_t* __restrict__ unit_node, uint32_t* __restrict__ tab) {
-    const LevelNode nd = nodes[blockIdx.x];
-    const int d = nd.degree;
-    const K* inner = ((nd.depth + 1) & 1) ? buf1 : buf0;
-    for (uint32_t u = threadIdx.x; u < nd.nunits; u += blockDim.x) unit_node[nd.unit_off + u] = blockIdx.x;
-    Child ch[8];
-    uint32_t cnt[8];
-    uint32_t nsplit = 0;
-    for (int c = 0; c < d; c++) {
-        ch[c] = child_of(nd, c, rs, rdesc);
-        uint32_t m = (ch[c].len + ts - 1) / ts;
-        cnt[c] = m > 0 ? m - 1 : 0;
-        nsplit += cnt[c];
-    }
-    const uint32_t groups = blockDim.x / k;
-    const uint32_t my_c = threadIdx.x % k;
-    const uint32_t iters = (nsplit + groups - 1) / groups;
-    for (uint32_t it = 0; it < iters; it++) {
-        uint32_t g = it * groups + threadIdx.x / k;
-        bool active = g < nsplit;
-        uint32_t split = 0;
-        if (active) {
-            uint32_t c = 0, gg = g;
-            while (gg >= cnt[c]) { gg -= cnt[c]; c++; }
-            uint32_t q = (gg + 1) * ts;
-            K key = child_get(ch[c], leaf, inner, q);
-            if ((int)my_c < d) {
-                if (my_c == c) {
-                    split = q;
-                } else {
-                    const Child& o = ch[my_c];
-                    uint32_t lo = 0, hi = o.len;
-                    bool upper = my_c < c;  // earlier children win ties: count keys <= key
-                    while (lo < hi) {
-                        uint32_t mid = (lo + hi) >> 1;
-                        K x = child_get(o, leaf, inner, mid);
-                        bool before = upper ? (x <= key) : (x < key);
-                        if (before) lo = mid + 1; else hi = mid;
-                    }
-                    split = lo;
+    const uint32_t total = (uint32_t)ctr[kCtrSplits];
+    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t g = gid / k;
+    const uint32_t my_c = gid % k;
+    const bool active = g < total;
+    uint32_t split = 0, v = 0, c = 0, unit_base = 0;
+    int d = 0;
+    if (active) {
+        uint32_t lo = 0, hi = nn;  // last node with split_off <= g
+        while (hi - lo > 1) {
+            uint32_t m = (lo + hi) >> 1;
+            if (nodes[m].split_off <= g) lo = m; else hi = m;
+        }
+        v = lo;
+        const LevelNode nd = nodes[v];
+        d = nd.degree;
+        unit_base = nd.unit_off;
+        const K* inner = ((nd.depth + 1) & 1) ? buf1 : buf0;
+        uint32_t gg = g - nd.split_off;
+        Child ch_c;
+        for (c = 0; c < (uint32_t)d; c++) {
+            ch_c = child_of(nd, c, rs, rdesc);
+            uint32_t m = (ch_c.len + ts - 1) / ts;
+            uint32_t cnt = m > 0 ? m - 1 : 0;
+            if (gg < cnt) break;
+            gg -= cnt;
+        }
+        const uint32_t q = (gg + 1) * ts;
+        const K key = child_get(ch_c, leaf, inner, q);
+        if ((int)my_c < d) {
+            if (my_c == c) {
+                split = q;
+            } else {
+                const Child o = child_of(nd, my_c, rs, rdesc);
+                uint32_t l = 0, h = o.len;
+                const bool upper = my_c < c;  // earlier children win ties: count keys <= key
+                while (l < h) {
+                    uint32_t mid = (l + h) >> 1;
+                    K x = child_get(o, leaf, inner, mid);
+                    bool before = upper ? (x <= key) : (x < key);
+                    if (before) l = mid + 1; else h = mid;
                 }
+                split = l;
             }
         }
-        uint32_t m = split ? (split + ts - 1) / ts - 1 : 0u;
-        uint32_t slot = m;
-        for (int o = 1; o < k; o <<= 1) slot += __shfl_xor_sync(0xffffffffu, slot, o);
-        if (active && (int)my_c < d) tab[(size_t)(nd.unit_off + slot + 1) * k + my_c] = split;
+    }
+    uint32_t slot = split ? (split + ts - 1) / ts - 1 : 0u;
+    for (int o = 1; o < k; o <<= 1) slot += __shfl_xor_sync(0xffffffffu, slot, o);
+    if (active) {
+        if ((int)my_c < d) tab[(size_t)(unit_base + slot + 1) * k + my_c] = split;
+        if (my_c == 0) unit_node[unit_base + slot + 1] = v;
     }
 }
 
-template <typename K, bool V>
-__global__ void __launch_bounds__(kMergeThreads)
-    k_level_merge(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ unit_node, const uint32_t* __restrict__ tab,
-                  const uint64_t* __restrict__ ctr, const uint32_t* __restrict__ rs, const uint8_t* __restrict__ rdesc,
-                  const K* __restrict__ leaf, const uint32_t* __restrict__ vleaf, K* __restrict__ buf0, K* __restrict__ buf1,
-                  uint32_t* __restrict__ vbuf0, uint32_t* __restrict__ vbuf1, uint32_t C, int k, uint32_t* __restrict__ status) {
-    extern __shared__ uint4 smem_raw[];
-    K* kA = reinterpret_cast<K*>(smem_raw);
-    K* kB = kA + C;
-    uint32_t* vA = V ? reinterpret_cast<uint32_t*>(kB + C) : nullptr;
-    uint32_t* vB = V ? vA + C : nullptr;
-    __shared__ uint32_t st_c[8], off_c[9];
-    __shared__ uint16_t seg_start[10], seg_mid[9];
-    __shared__ uint32_t sh_ns;
-    __shared__ Child chs[8];
+// One work unit of a level: a contiguous slice of each child of one node
+// (128 bytes, copied to shared memory with cp.async one unit ahead).
+struct __align__(16) UnitDesc {
+    uint32_t out_base;     // first output element
+    uint32_t total;        // elements in the unit
+    uint32_t d;            // number of children
+    uint32_t flags;        // bit c: slice c is a leaf; bit 8+c: read backwards; bit 31: odd depth
+    uint32_t off[9];       // slice offsets in shared memory (off[d] = total)
+    uint32_t src[8];       // element of the slice's source that lands at off[c]
+    uint32_t pad[11];
+};
+static_assert(sizeof(UnitDesc) == 128, "UnitDesc layout");
 
-    const uint32_t u = blockIdx.x;
+// One thread per work unit of the level: fills its descriptor.
+__global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ unit_node,
+                                                    const uint32_t* __restrict__ tab, const uint64_t* __restrict__ ctr,
+                                                    const uint32_t* __restrict__ rs, const uint8_t* __restrict__ rdesc, int k,
+                                                    UnitDesc* __restrict__ out) {
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= (uint32_t)ctr[kCtrUnits]) return;
-    const LevelNode nd = nodes[unit_node[u]];
-    const int d = nd.degree;
+    const LevelNode& nd = nodes[unit_node[u]];
+    const uint32_t d = nd.degree;
     const uint32_t local = u - nd.unit_off;
-    const bool depth_odd = nd.depth & 1;
-    const K* inner = depth_odd ? buf0 : buf1;               // children sit at depth + 1
-    const uint32_t* vinner = depth_odd ? vbuf0 : vbuf1;
-    K* out = depth_odd ? buf1 : buf0;
-    uint32_t* vout = depth_odd ? vbuf1 : vbuf0;
+    const bool first = local == 0, last = local + 1 == nd.nunits;
+    UnitDesc D;
+    uint32_t acc = 0, ob = nd.sL, flags = (nd.depth & 1u) << 31;
+    for (uint32_t c = 0; c < 8; c++) {
+        if (c < d) {
+            const uint32_t a = nd.b[c], b = nd.b[c + 1];
+            const uint32_t base = rs[a], len = rs[b] - base;
+            const uint32_t st = first ? 0u : tab[(size_t)u * k + c];
+            const uint32_t en = last ? len : tab[(size_t)(u + 1) * k + c];
+            const uint32_t leaf = (b == a + 1);
+            const uint32_t rev = leaf ? rdesc[a] : 0u;
+            D.src[c] = rev ? base + len - 1 - st : base + st;
+            flags |= (leaf << c) | (rev << (8 + c));
+            D.off[c] = acc;
+            acc += en - st;
+            ob += st;
+        } else {
+            D.src[c] = 0;
+            D.off[c] = acc;
+        }
+    }
+    D.off[8] = acc;
+    D.out_base = ob;
+    D.total = acc;
+    D.d = d;
+    D.flags = flags;
+    for (int q = 0; q < 11; q++) D.pad[q] = 0;
+    out[u] = D;
+}
 
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int c = 0; c < d; c++) {
-            Child ch = child_of(nd, c, rs, rdesc);
-            chs[c] = ch;
-            uint32_t s = local == 0 ? 0u : tab[(size_t)(nd.unit_off + local) * k + c];
-            uint32_t e = local + 1 == nd.nunits ? ch.len : tab[(size_t)(nd.unit_off + local + 1) * k + c];
-            st_c[c] = s;
-            off_c[c] = acc;
-            acc += e - s;
+// ---- asynchronous global -> shared copies (cp.async)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (BYTES == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else if (BYTES == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int kLvlThreads = 128;
+constexpr int kLvlIPT = 15;  // odd: conflict-free strides
+
+template <typename K, bool V>
+__device__ __forceinline__ void issue_unit_copies(const UnitDesc& D, K* dst, uint32_t* vdst, const K* __restrict__ leaf,
+                                                  const uint32_t* __restrict__ vleaf, const K* __restrict__ inner,
+                                                  const uint32_t* __restrict__ vinner) {
+    for (uint32_t c = 0; c < D.d; c++) {
+        const uint32_t o = D.off[c], m = D.off[c + 1] - o, s = D.src[c];
+        const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (8 + c)) & 1u;
+        const K* srck = lf ? leaf : inner;
+        const uint32_t* srcv = lf ? vleaf : vinner;
+        for (uint32_t i = threadIdx.x; i < m; i += kLvlThreads) {
+            const uint32_t g = rv ? s - i : s + i;
+            cp_async<sizeof(K)>(dst + o + i, srck + g);
+            if (V) cp_async<4>(vdst + o + i, srcv + g);
         }
-        off_c[d] = acc;
     }
-    __syncthreads();
-    const uint32_t total = off_c[d];
-    if (total > C) {
-        if (threadIdx.x == 0) dev_fail(status, kDevRange);
-        return;
-    }
-    uint32_t out_base = nd.sL;
-    for (int c = 0; c < d; c++) out_base += st_c[c];
-    for (int c = 0; c < d; c++) {
-        const Child ch = chs[c];
-        const uint32_t s = st_c[c], o = off_c[c], m = off_c[c + 1] - o;
-        for (uint32_t i = threadIdx.x; i < m; i += kMergeThreads) {
-            uint32_t pos = s + i;
-            uint32_t src = ch.leaf ? (ch.rev ? ch.base + ch.len - 1 - pos : ch.base + pos) : ch.base + pos;
-            kA[o + i] = ch.leaf ? leaf[src] : inner[src];
-            if (V) vA[o + i] = ch.leaf ? vleaf[src] : vinner[src];
-        }
-    }
-    __syncthreads();
-    K* cur = kA;
-    K* oth = kB;
-    uint32_t* vcur = vA;
-    uint32_t* voth = vB;
-    for (uint32_t t = 0; (1 << t) < d; t++) {
-        if (threadIdx.x == 0) {
-            uint32_t ns = 0;
-            seg_start[0] = 0;
-            seg_mid[0] = (uint16_t)kNoMid;
-            for (int c = 1; c < d; c++) {
-                uint32_t cz = __ffs(c) - 1;
-                if (cz > t) {
-                    ns++;
-                    seg_start[ns] = (uint16_t)off_c[c];
-                    seg_mid[ns] = (uint16_t)kNoMid;
-                } else if (cz == t) {
-                    seg_mid[ns] = (uint16_t)off_c[c];
+}
+
+// Round t of the tournament over the unit's d slices: slices are grouped in
+// blocks of 2^(t+1); the two halves of every block are merged (stable, left
+// first), a block without a right half is copied.
+template <typename K, bool V>
+__device__ __forceinline__ void unit_round(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
+                                           uint32_t* __restrict__ vdst, const uint32_t* __restrict__ off, uint32_t d,
+                                           uint32_t t) {
+    const uint32_t step = 1u << (t + 1), half = 1u << t;
+    const uint32_t total = off[d];
+    for (uint32_t base = threadIdx.x * kLvlIPT; base < total; base += kLvlThreads * kLvlIPT) {
+        uint32_t o = base;
+        const uint32_t oe = min(base + (uint32_t)kLvlIPT, total);
+        uint32_t c0 = 0;
+        for (uint32_t c = step; c < d; c += step)
+            if (off[c] <= o) c0 = c;
+        while (o < oe) {
+            const uint32_t cm = c0 + half, c1 = min(c0 + step, d);
+            const uint32_t s = off[c0], e = off[c1];
+            const uint32_t stop = min(e, oe);
+            if (cm >= d) {
+                for (; o < stop; o++) {
+                    dst[o] = src[o];
+                    if (V) vdst[o] = vsrc[o];
                 }
+            } else {
+                const uint32_t m = off[cm];
+                const uint32_t l = merge_path(src, s, m, e, o - s);
+                serial_merge<K, V>(src, dst, vsrc, vdst, s + l, m, m + (o - s) - l, e, o, stop);
+                o = stop;
             }
-            ns++;
-            seg_start[ns] = (uint16_t)total;
-            sh_ns = ns;
+            c0 = c1;
+        }
+    }
+}
+
+// Level merge: persistent blocks, each over a contiguous range of work units.
+// Per unit: read its descriptor, copy its slices to shared memory, merge them
+// in tournament rounds, write the result.  Small blocks (128 threads, 2*C
+// elements of shared memory) keep many blocks resident per SM, which hides
+// the copy latency of one block behind the merging of the others.
+template <typename K, bool V>
+__global__ void __launch_bounds__(kLvlThreads)
+    k_level_merge(const UnitDesc* __restrict__ udesc, const uint64_t* __restrict__ ctr, const K* __restrict__ leaf,
+                  const uint32_t* __restrict__ vleaf, K* __restrict__ buf0, K* __restrict__ buf1, uint32_t* __restrict__ vbuf0,
+                  uint32_t* __restrict__ vbuf1, uint32_t C, uint32_t* __restrict__ status) {
+    extern __shared__ uint4 smem_raw[];
+    K* La = reinterpret_cast<K*>(smem_raw);
+    K* Lb = La + C;
+    uint32_t* vLa = V ? reinterpret_cast<uint32_t*>(Lb + C) : nullptr;
+    uint32_t* vLb = V ? vLa + C : nullptr;
+    __shared__ UnitDesc D;
+
+    const uint32_t total_units = (uint32_t)ctr[kCtrUnits];
+    const uint32_t per = (total_units + gridDim.x - 1) / gridDim.x;
+    const uint32_t u0 = blockIdx.x * per;
+    const uint32_t u1 = min(total_units, u0 + per);
+    for (uint32_t u = u0; u < u1; u++) {
+        if (threadIdx.x < 8) reinterpret_cast<uint4*>(&D)[threadIdx.x] = reinterpret_cast<const uint4*>(udesc + u)[threadIdx.x];
+        __syncthreads();
+        const uint32_t total = D.total, d = D.d;
+        if (total > C) {
+            if (threadIdx.x == 0) dev_fail(status, kDevRange);
+            return;
+        }
+        const bool odd = D.flags >> 31;
+        const K* inner = odd ? buf0 : buf1;                 // children sit at depth + 1
+        const uint32_t* vinner = odd ? vbuf0 : vbuf1;
+        for (uint32_t c = 0; c < d; c++) {
+            const uint32_t o = D.off[c], m = D.off[c + 1] - o, s0 = D.src[c];
+            const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (8 + c)) & 1u;
+            const K* srck = lf ? leaf : inner;
+            const uint32_t* srcv = lf ? vleaf : vinner;
+            for (uint32_t i = threadIdx.x; i < m; i += kLvlThreads) {
+                const uint32_t g = rv ? s0 - i : s0 + i;
+                La[o + i] = srck[g];
+                if (V) vLa[o + i] = srcv[g];
+            }
         }
         __syncthreads();
-        merge_pass<K, V>(cur, oth, vcur, voth, total, seg_start, seg_mid, sh_ns);
+        K* cur = La;
+        K* oth = Lb;
+        uint32_t* vcur = vLa;
+        uint32_t* voth = vLb;
+        for (uint32_t t = 0; (1u << t) < d; t++) {
+            unit_round<K, V>(cur, oth, vcur, voth, D.off, d, t);
+            __syncthreads();
+            K* tk = cur; cur = oth; oth = tk;
+            uint32_t* tv = vcur; vcur = voth; voth = tv;
+        }
+        K* out = odd ? buf1 : buf0;
+        uint32_t* vout = odd ? vbuf1 : vbuf0;
+        const uint32_t ob = D.out_base;
+        for (uint32_t q = threadIdx.x; q < total; q += kLvlThreads) {
+            out[ob + q] = cur[q];
+            if (V) vout[ob + q] = vcur[q];
+        }
         __syncthreads();
-        K* tk = cur; cur = oth; oth = tk;
-        uint32_t* tv = vcur; vcur = voth; voth = tv;
-    }
-    for (uint32_t i = threadIdx.x; i < total; i += kMergeThreads) {
-        out[out_base + i] = cur[i];
-        if (V) vout[out_base + i] = vcur[i];
     }
 }
 
@@ -579,37 +663,43 @@ __global__ void k_copy_single_run(const K* __restrict__ in, const uint32_t* __re
 
 MergeGeom merge_geom(int key_bytes, bool vals, int k) {
     MergeGeom g;
-    if (key_bytes == 4 && !vals) { g.c_fused = 16384; g.tfix = 4096; g.c_level = 8192; }
-    else if (key_bytes == 8 && vals) { g.c_fused = 6144; g.tfix = 1536; g.c_level = 4096; }
-    else { g.c_fused = 8192; g.tfix = 2048; g.c_level = 4096; }
-    g.tmax = g.c_fused - g.tfix;
-    g.k = k;
+    if (key_bytes == 4 && !vals) { g.c_fused = 6144; g.c_level = 4096; }
+    else if (key_bytes == 8 && vals) { g.c_fused = 3072; g.c_level = 2048; }
+    else { g.c_fused = 4096; g.c_level = 2048; }
+    g.tmax = g.c_fused;
     g.ts = g.c_level / (uint32_t)k;
+    g.k = k;
+    // persistent level merge: two buffers of c_level elements per block
+    size_t lvl_smem = (size_t)2 * g.c_level * ((size_t)key_bytes + (vals ? 4 : 0)) + 256;
+    g.level_grid = 152 * (uint32_t)std::min<size_t>(16, (220 * 1024) / lvl_smem);
+    size_t fz_smem = (size_t)2 * g.c_fused * ((size_t)key_bytes + (vals ? 4 : 0)) + (size_t)2 * (g.c_fused / 2 + 8) * 4 + 1024;
+    g.fused_grid = 152 * (uint32_t)std::max<size_t>(1, std::min<size_t>(8, (220 * 1024) / fz_smem));
     return g;
 }
 
 template <typename K, bool V>
-void launch_fused(const K* leaf_keys, const uint32_t* leaf_vals, K* out, uint32_t* vout, uint64_t n, const MergeGeom& g,
-                  const WsView& ws, cudaStream_t st) {
-    size_t smem = SmemLayout<K, V>::bytes(g.c_fused);
+void launch_fused(const K* leaf_keys, const uint32_t* leaf_vals, K* out, uint32_t* vout, uint64_t nfused,
+                  const MergeGeom& g, const WsView& ws, cudaStream_t st) {
+    size_t smem = FusedSmem<K, V>::bytes(g.c_fused);
     cudaFuncSetAttribute(k_fused<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    uint32_t grid = ws.windows - 1;
+    uint32_t grid = (uint32_t)std::min<uint64_t>(nfused, g.fused_grid);
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
-    k_fused<K, V><<<grid, kMergeThreads, smem, st>>>(leaf_keys, leaf_vals, out, tmp, vout, ws.vals_tmp, ws.run_starts,
-                                                     ws.run_desc, ws.powers, ws.fr_end, ws.fr_depth, ws.first_run,
-                                                     g.c_fused, g.k, reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
+    k_fused<K, V><<<grid, kFusedThreads, smem, st>>>(ws.fused_list, ws.counters, leaf_keys, leaf_vals, out, tmp, vout,
+                                                     ws.vals_tmp, ws.run_starts, ws.run_desc, ws.powers, g.c_fused, g.k,
+                                                     reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
     g_launches += 1;
-    (void)n;
 }
 
 template <typename K>
-void launch_level_plan(uint32_t level_off, uint32_t nnodes, int k, const K* leaf_keys, K* out, const MergeGeom& g,
-                       const WsView& ws, cudaStream_t st) {
+void launch_level_plan(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys, K* out,
+                       const MergeGeom& g, const WsView& ws, cudaStream_t st) {
     LevelNode* nodes = ws.nodes_lvl + level_off;
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
-    k_level_prep<<<1, 1024, 0, st>>>(nodes, nnodes, ws.run_starts, g.ts, ws.counters);
-    k_level_split<K><<<nnodes, 256, 0, st>>>(nodes, ws.run_starts, ws.run_desc, leaf_keys, out, tmp, g.ts, k,
-                                              ws.unit_node, ws.split_tab);
+    k_level_prep<<<1, 1024, 0, st>>>(nodes, nnodes, ws.run_starts, g.ts, ws.counters, ws.unit_node);
+    uint64_t split_bound = level_elems / g.ts + 1;
+    uint32_t blocks = (uint32_t)ceil_div(split_bound * (uint64_t)k, 256);
+    k_level_split<K><<<blocks, 256, 0, st>>>(nodes, nnodes, ws.counters, ws.run_starts, ws.run_desc, leaf_keys, out, tmp,
+                                              g.ts, k, ws.unit_node, ws.split_tab);
     g_launches += 2;
 }
 
@@ -619,13 +709,17 @@ void launch_level_merge(uint32_t level_off, uint32_t nnodes, uint64_t level_elem
                         cudaStream_t st) {
     LevelNode* nodes = ws.nodes_lvl + level_off;
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
+    uint64_t bound = level_elems / g.ts + nnodes + 1;
+    UnitDesc* udesc = reinterpret_cast<UnitDesc*>(ws.unit_desc);
+    k_level_desc<<<(uint32_t)ceil_div(bound, 256), 256, 0, st>>>(nodes, ws.unit_node, ws.split_tab, ws.counters,
+                                                                 ws.run_starts, ws.run_desc, k, udesc);
     size_t smem = (size_t)2 * g.c_level * (sizeof(K) + (V ? 4 : 0));
     cudaFuncSetAttribute(k_level_merge<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    uint64_t bound = level_elems / g.ts + nnodes + 1;
-    k_level_merge<K, V><<<(uint32_t)bound, kMergeThreads, smem, st>>>(
-        nodes, ws.unit_node, ws.split_tab, ws.counters, ws.run_starts, ws.run_desc, leaf_keys, leaf_vals, out, tmp, vout,
-        ws.vals_tmp, g.c_level, k, reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
-    g_launches += 1;
+    uint32_t grid = (uint32_t)std::min<uint64_t>(bound, (uint64_t)g.level_grid);
+    k_level_merge<K, V><<<grid, kLvlThreads, smem, st>>>(udesc, ws.counters, leaf_keys, leaf_vals, out, tmp, vout,
+                                                          ws.vals_tmp, g.c_level,
+                                                          reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
+    g_launches += 2;
 }
 
 template <typename K, bool V>
@@ -648,9 +742,9 @@ MPS_INST(uint32_t, true)
 MPS_INST(uint64_t, false)
 MPS_INST(uint64_t, true)
 #undef MPS_INST
-template void launch_level_plan<uint32_t>(uint32_t, uint32_t, int, const uint32_t*, uint32_t*, const MergeGeom&,
-                                          const WsView&, cudaStream_t);
-template void launch_level_plan<uint64_t>(uint32_t, uint32_t, int, const uint64_t*, uint64_t*, const MergeGeom&,
-                                          const WsView&, cudaStream_t);
+template void launch_level_plan<uint32_t>(uint32_t, uint32_t, uint64_t, int, const uint32_t*, uint32_t*,
+                                          const MergeGeom&, const WsView&, cudaStream_t);
+template void launch_level_plan<uint64_t>(uint32_t, uint32_t, uint64_t, int, const uint64_t*, uint64_t*,
+                                          const MergeGeom&, const WsView&, cudaStream_t);
 
 }  // namespace mps

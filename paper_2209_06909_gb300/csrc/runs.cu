@@ -22,6 +22,8 @@
 // -- is w minus the index of the highest bit where x and y differ; b - a >= 1/n
 // guarantees x != y.  The predicate is monotone in q, so for k = 2^t the k-way
 // power is ceil(P2 / t) (the "squish" of Sec. 3.1 for t = 2).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -136,8 +138,7 @@ __global__ void __launch_bounds__(1024) k_det_scan(const uint4* __restrict__ til
 
 template <typename K>
 __global__ void __launch_bounds__(kDetThreads) k_det_write(const K* __restrict__ keys, uint64_t n, const uint2* __restrict__ tile_pref,
-                                                           uint32_t* __restrict__ run_starts, uint8_t* __restrict__ run_desc,
-                                                           uint32_t* __restrict__ fr_end) {
+                                                           uint32_t* __restrict__ run_starts, uint8_t* __restrict__ run_desc) {
     __shared__ uint4 tmp[kDetThreads / 32 + 1];
     uint64_t i0 = (uint64_t)blockIdx.x * kDetTile + (uint64_t)threadIdx.x * kDetItems;
     K v[kDetItems + 2];
@@ -156,7 +157,6 @@ __global__ void __launch_bounds__(kDetThreads) k_det_write(const K* __restrict__
             if (st == 0) {
                 run_starts[idx] = (uint32_t)i;
                 run_desc[idx] = (i + 1 < n && v[2 + j] < v[1 + j]) ? 1 : 0;
-                fr_end[idx] = 0;
                 idx++;
             }
         }
@@ -164,21 +164,20 @@ __global__ void __launch_bounds__(kDetThreads) k_det_write(const K* __restrict__
 }
 
 // Powers of boundaries 1..r-1, sentinels powers[0] = powers[r] = 0, padding
-// of 255 up to the next multiple of 32, the bit set of powers that occur,
-// and the window -> first run table used by the fused merge kernel.
+// of 255 up to the next multiple of 32, and the bit set of powers that occur.
 __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run_starts, const uint64_t* __restrict__ counters,
                                                 uint64_t n, uint32_t w, uint64_t magic, uint32_t log2k,
-                                                uint8_t* __restrict__ powers, unsigned long long* __restrict__ level_bits,
-                                                uint32_t* __restrict__ first_run, uint32_t tfix, uint32_t windows) {
+                                                uint8_t* __restrict__ powers, unsigned long long* __restrict__ level_bits) {
+    __shared__ unsigned long long red[256 / 32 + 1];
     const uint32_t r = (uint32_t)counters[kCtrR];
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long bits = 0;
-    if (i <= r) {
+    const uint64_t d = 2 * n;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= r; i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t si = run_starts[i];
+        uint32_t sp = i >= 1 ? run_starts[i - 1] : 0u;
         if (i >= 1 && i < r) {
-            uint64_t a2 = (uint64_t)run_starts[i - 1] + si;       // 2n * a
+            uint64_t a2 = (uint64_t)sp + si;                      // 2n * a
             uint64_t b2 = (uint64_t)si + run_starts[i + 1];       // 2n * b
-            uint64_t d = 2 * n;
             uint64_t X = a2 << w, Y = b2 << w;
             uint64_t x = __umul64hi(X, magic), y = __umul64hi(Y, magic);
             uint64_t rx = X - x * d, ry = Y - y * d;
@@ -188,7 +187,7 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
             uint32_t p2 = w - h;
             uint32_t pk = (p2 + log2k - 1) / log2k;
             powers[i] = (uint8_t)pk;
-            bits = 1ull << pk;
+            bits |= 1ull << pk;
         } else {
             powers[i] = 0;
         }
@@ -196,14 +195,9 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
             uint64_t pad_end = (r + 1 + 31) / 32 * 32;
             for (uint64_t q = r + 1; q < pad_end; q++) powers[q] = 255;
         }
-        // windows w with s_{i-1} < w * tfix <= s_i take first_run = i
-        uint32_t lo_w = (i == 0) ? 0u : run_starts[i - 1] / tfix + 1;
-        uint32_t hi_w = (i == r) ? windows - 1 : si / tfix;
-        for (uint32_t q = lo_w; q <= hi_w && q < windows; q++) first_run[q] = (uint32_t)i;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
-    if ((threadIdx.x & 31) == 0 && bits) atomicOr(level_bits, bits);
+    bits = block_reduce<256>(bits, OpOrU64(), 0ull, red);
+    if (threadIdx.x == 0 && bits) atomicOr(level_bits, bits);
 }
 
 }  // namespace
@@ -215,7 +209,7 @@ void launch_detect(const K* keys, uint64_t n, const WsView& ws, cudaStream_t st)
     uint32_t tiles = (uint32_t)ceil_div(n, kDetTile);
     k_det_reduce<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.det_sum);
     k_det_scan<<<1, 1024, 0, st>>>(ws.det_sum, tiles, ws.det_pref, ws.counters, ws.run_starts, n);
-    k_det_write<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.det_pref, ws.run_starts, ws.run_desc, ws.fr_end);
+    k_det_write<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.det_pref, ws.run_starts, ws.run_desc);
     g_launches += 3;
 }
 
@@ -228,10 +222,9 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
     uint64_t magic = ~0ull / (2 * n);
     uint32_t log2k = k == 2 ? 1 : (k == 4 ? 2 : 3);
     uint32_t threads = 256;
-    uint32_t blocks = (uint32_t)ceil_div((uint64_t)r + 1, threads);
+    uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r + 1, threads), 152 * 16);
     k_powers<<<blocks, threads, 0, st>>>(ws.run_starts, ws.counters, n, w, magic, log2k, ws.powers,
-                                          reinterpret_cast<unsigned long long*>(ws.counters + kCtrLevelBits),
-                                          ws.first_run, ws.tfix, ws.windows);
+                                          reinterpret_cast<unsigned long long*>(ws.counters + kCtrLevelBits));
     g_launches += 1;
 }
 

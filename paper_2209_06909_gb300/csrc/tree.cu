@@ -22,6 +22,8 @@
 //   depth(run i)       = |F(P_1..P_i) | G(P_{i+1}..P_{r-1})|,
 // and B_j starts its node iff P_j is not among the suffix minima to its left.
 // (Sec. 2.2: M = sum_i d_i L_i; Fact 3.2: depth(m(B_j)) <= P_j - 1.)
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -272,65 +274,69 @@ __device__ __forceinline__ bool node_shape(const MinTree& T, const uint8_t* P, u
     return ok;
 }
 
+// One pass over the boundaries (grid-stride).  For every node start j: its
+// delimiters L, R (nearest smaller powers) and size.  Nodes larger than T_max
+// become level-merge records; such a node also appends each child that is an
+// inner node of at most T_max elements to the list of fused subtrees (its
+// parent is large, so it is maximal).  A small root is a fused subtree too.
 __global__ void __launch_bounds__(256) k_node_pass(MinTree T, uint32_t r, int k, uint32_t tmax,
                                                    const uint32_t* __restrict__ rs, const uint8_t* __restrict__ node_info,
                                                    uint64_t* __restrict__ ctr, LevelNode* __restrict__ nodes_raw, uint32_t nodes_cap,
-                                                   uint32_t* __restrict__ fr_end, uint8_t* __restrict__ fr_depth) {
+                                                   uint4* __restrict__ fused_list, uint32_t fused_cap) {
+    __shared__ unsigned long long red[256 / 32 + 1];
     const uint8_t* P = T.lv[0];
-    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    uint32_t* status = reinterpret_cast<uint32_t*>(ctr + kCtrStatus);
     unsigned long long msize = 0, nstarts = 0;
-    if (j < r) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x + 1; j < r; j += gridDim.x * blockDim.x) {
         uint8_t info = node_info[j];
-        if (info & 0x80) {
-            nstarts = 1;
-            uint32_t v = P[j];
-            uint32_t depth = info & 0x7F;
+        if (!(info & 0x80)) continue;
+        nstarts++;
+        const uint32_t v = P[j];
+        const uint32_t L = nsv_left(T, j, v, true);
+        const uint32_t R = nsv_right(T, j, v, true);
+        const uint32_t sL = rs[L], sR = rs[R];
+        const uint32_t size = sR - sL;
+        msize += size;
+        const uint32_t depth = info & 0x7F;
+        if (size > tmax) {
             NodeShape s;
-            if (!node_shape(T, P, j, v, k, s)) dev_fail(reinterpret_cast<uint32_t*>(ctr + kCtrStatus), kDevDegree);
-            uint32_t sL = rs[s.L], sR = rs[s.R];
-            uint32_t size = sR - sL;
-            msize = size;
-            if (size > tmax) {
-                uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmTotal), 1ull);
-                if (slot < nodes_cap) {
-                    LevelNode nd;
-                    nd.sL = sL; nd.sR = sR; nd.unit_off = 0; nd.nunits = 0;
+            if (!node_shape(T, P, j, v, k, s)) dev_fail(status, kDevDegree);
+            uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmTotal), 1ull);
+            if (slot < nodes_cap) {
+                LevelNode nd;
+                nd.sL = sL; nd.sR = sR; nd.unit_off = 0; nd.nunits = 0;
 #pragma unroll
-                    for (int q = 0; q < 9; q++) nd.b[q] = q <= (int)s.d ? s.b[q] : 0u;
-                    nd.power = (uint8_t)v; nd.depth = (uint8_t)depth; nd.degree = (uint8_t)s.d; nd.pad = 0;
-                    nd.pad2[0] = nd.pad2[1] = 0;
-                    nodes_raw[slot] = nd;
-                } else {
-                    dev_fail(reinterpret_cast<uint32_t*>(ctr + kCtrStatus), kDevCapacity);
-                }
-                atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmCount + v), 1ull);
-                atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmSize + v), (unsigned long long)size);
+                for (int q = 0; q < 9; q++) nd.b[q] = q <= (int)s.d ? s.b[q] : 0u;
+                nd.power = (uint8_t)v; nd.depth = (uint8_t)depth; nd.degree = (uint8_t)s.d; nd.pad = 0;
+                nd.split_off = nd.nsplit = 0;
+                nodes_raw[slot] = nd;
             } else {
-                bool frontier;
-                uint32_t pl = P[s.L], pr = P[s.R];
-                if (pl == 0 && pr == 0) {
-                    frontier = true;
-                } else {
-                    uint32_t q = pl >= pr ? s.L : s.R;
-                    uint32_t pq = P[q];
-                    uint32_t lq = nsv_left(T, q, pq, true), rq = nsv_right(T, q, pq, true);
-                    frontier = (rs[rq] - rs[lq]) > tmax;
-                }
-                if (frontier) {
-                    fr_end[s.L] = s.R;
-                    fr_depth[s.L] = (uint8_t)depth;
-                    atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
-                    atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), (unsigned long long)size);
+                dev_fail(status, kDevCapacity);
+            }
+            atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmCount + v), 1ull);
+            atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmSize + v), (unsigned long long)size);
+            unsigned long long fe = 0;
+            for (uint32_t c = 0; c < s.d; c++) {
+                uint32_t a = s.b[c], e = s.b[c + 1];
+                uint32_t cs = rs[e] - rs[a];
+                if (e - a >= 2 && cs <= tmax) {
+                    uint32_t fs = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
+                    if (fs < fused_cap) fused_list[fs] = make_uint4(a, e, depth + 1, 0u);
+                    else dev_fail(status, kDevCapacity);
+                    fe += cs;
                 }
             }
+            if (fe) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), fe);
+        } else if (L == 0 && R == r) {
+            uint32_t fs = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
+            if (fs < fused_cap) fused_list[fs] = make_uint4(0u, r, 0u, 0u);
+            else dev_fail(status, kDevCapacity);
+            atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), (unsigned long long)size);
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        msize += __shfl_xor_sync(0xffffffffu, msize, o);
-        nstarts += __shfl_xor_sync(0xffffffffu, nstarts, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
+    msize = block_reduce<256>(msize, OpAddU64(), 0ull, red);
+    nstarts = block_reduce<256>(nstarts, OpAddU64(), 0ull, red);
+    if (threadIdx.x == 0) {
         if (msize) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrM), msize);
         if (nstarts) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrNodes), nstarts);
     }
@@ -481,8 +487,9 @@ void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView&
 
 void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st) {
     uint32_t nb = r - 1;
-    k_node_pass<<<(uint32_t)ceil_div(nb, 256), 256, 0, st>>>(make_mintree(ws), r, k, tmax, ws.run_starts, ws.node_info,
-                                                              ws.counters, ws.nodes_raw, ws.nodes_cap, ws.fr_end, ws.fr_depth);
+    uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(nb, 256), 152 * 16);
+    k_node_pass<<<blocks, 256, 0, st>>>(make_mintree(ws), r, k, tmax, ws.run_starts, ws.node_info,
+                                                              ws.counters, ws.nodes_raw, ws.nodes_cap, ws.fused_list, ws.fused_cap);
     g_launches += 1;
 }
 
