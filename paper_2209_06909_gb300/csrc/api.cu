@@ -45,7 +45,7 @@ struct Plan {
     int nlv_max = 0;
     // offsets
     size_t o_ctr, o_lvloff, o_det_sum, o_det_pref, o_rs, o_rdesc, o_fused, o_canon, o_lv[kMinTreeLevels], o_info,
-        o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_hist, o_ktmp, o_vtmp, total;
+        o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_ufirst, o_ptiles, o_hist, o_ktmp, o_vtmp, total;
 
     explicit Plan(uint64_t n_, int kb_, bool vals_, int k_) : n(n_), kb(kb_), vals(vals_), k(k_) {
         g = merge_geom(kb, vals, k);
@@ -81,6 +81,8 @@ struct Plan {
         o_unit_node = take((size_t)unit_cap * 4);
         o_split = take((size_t)(unit_cap + 1) * k * 4);
         o_udesc = take((size_t)unit_cap * 128);
+        o_ufirst = take((size_t)unit_cap * 4);
+        o_ptiles = take((size_t)(unit_cap / 4096 + 2) * 4);
         o_hist = take(mask_tiles * kMaxLevels * 4);
         o_ktmp = take(n * kb);
         o_vtmp = vals ? take(n * 4) : o;
@@ -111,6 +113,8 @@ struct Plan {
         w.unit_node = reinterpret_cast<uint32_t*>(b + o_unit_node);
         w.split_tab = reinterpret_cast<uint32_t*>(b + o_split);
         w.unit_desc = b + o_udesc;
+        w.unit_first = reinterpret_cast<uint32_t*>(b + o_ufirst);
+        w.pack_tiles = reinterpret_cast<uint32_t*>(b + o_ptiles);
         w.unit_cap = unit_cap;
         w.canon_idx = reinterpret_cast<uint32_t*>(b + o_canon);
         w.hist = reinterpret_cast<uint32_t*>(b + o_hist);

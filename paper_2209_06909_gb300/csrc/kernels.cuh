@@ -27,6 +27,7 @@ enum : int {
     kCtrHbmFill = 136,  // [64] fill counters for bucketing
     kCtrFrontierElems = 200,  // elements inside fused subtrees
     kCtrSplits = 201,   // splitters of the current level
+    kCtrIntervals = 202,  // splitter intervals of the current level (packed into units)
     kCtrWords = 256
 };
 
@@ -67,6 +68,8 @@ struct WsView {
     uint32_t* unit_node;
     uint32_t* split_tab;
     void* unit_desc;               // 128-byte work-unit descriptors of the current level
+    uint32_t* unit_first;          // first splitter interval of each packed work unit
+    uint32_t* pack_tiles;          // per-tile counts / offsets of the packing scan
     uint32_t unit_cap;
     uint32_t* canon_idx;           // dump: canonical index of each node start
     uint32_t* hist;                // dump: per-tile power histograms
@@ -79,7 +82,8 @@ struct MergeGeom {
     uint32_t c_fused;   // elements of shared memory per fused tile
     uint32_t tmax;      // largest fused subtree (== c_fused)
     uint32_t c_level;   // elements per level-merge unit
-    uint32_t ts;        // splitter spacing per child (c_level / k)
+    uint32_t ts;        // splitter spacing per child (c_level / 2k)
+    uint32_t q;         // packing quantum: units are cut where rank / q increases (c_level / 2)
     int k;              // fan-in
     uint32_t level_grid;  // blocks of the persistent level merge
     uint32_t fused_grid;  // blocks of the persistent fused-subtree kernel

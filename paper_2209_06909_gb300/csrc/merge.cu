@@ -33,6 +33,18 @@ namespace mps {
 
 namespace {
 
+// ---- asynchronous global -> shared copies (cp.async)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (BYTES == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else if (BYTES == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 constexpr int kFusedThreads = 256;
 // outputs per thread in a merge pass; odd, so that the lanes of a warp touch
 // 32 different shared-memory banks when they walk their outputs in step
@@ -184,17 +196,27 @@ __global__ void __launch_bounds__(kFusedThreads)
         const uint32_t nruns = R - L;
         const uint32_t nb = nruns - 1;
 
-        // ---- load boundaries, keys and run directions
-        for (uint32_t e = tid; e < nb; e += kFusedThreads) {
-            const uint32_t j = L + 1 + e;
-            bl0[e] = (rs[j] - s_lo) | ((uint32_t)P[j] << 16);
-        }
+        // ---- load boundaries, keys and run directions (asynchronous copies)
+        // run starts -> kB (as u32), powers and directions -> bl1 (bytes, from
+        // 4-byte aligned supersets; both arrays are padded past r)
+        uint32_t* rsS = reinterpret_cast<uint32_t*>(kB);
+        uint8_t* PS = reinterpret_cast<uint8_t*>(bl1);
+        uint8_t* dflag = PS + (C / 2 + 64);
+        const uint32_t pa = (L + 1) & ~3u, pb = (R + 3) & ~3u;
+        const uint32_t da = L & ~3u, db = (R + 3) & ~3u;
+        for (uint32_t e = tid; e < nb; e += kFusedThreads) cp_async<4>(rsS + e, rs + L + 1 + e);
+        for (uint32_t q = pa + 4 * tid; q < pb; q += 4 * kFusedThreads) cp_async<4>(PS + (q - pa), P + q);
+        for (uint32_t q = da + 4 * tid; q < db; q += 4 * kFusedThreads) cp_async<4>(dflag + (q - da), rdesc + q);
         for (uint32_t x = tid; x < len; x += kFusedThreads) {
-            kA[x] = leaf[s_lo + x];
-            if (V) vA[x] = vleaf[s_lo + x];
+            cp_async<sizeof(K)>(kA + x, leaf + s_lo + x);
+            if (V) cp_async<4>(vA + x, vleaf + s_lo + x);
         }
-        uint8_t* dflag = reinterpret_cast<uint8_t*>(bl1);
-        for (uint32_t q = tid; q < nruns; q += kFusedThreads) dflag[q] = rdesc[L + q];
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        for (uint32_t e = tid; e < nb; e += kFusedThreads)
+            bl0[e] = (rsS[e] - s_lo) | ((uint32_t)PS[e + (L + 1 - pa)] << 16);
+        dflag += L - da;  // dflag[q] = direction of run L + q
         __syncthreads();
 
         // ---- reverse the strictly descending runs (kA -> kB)
@@ -393,7 +415,7 @@ __global__ void __launch_bounds__(1024) k_level_prep(LevelNode* __restrict__ nod
     }
     if (threadIdx.x == 0) {
         ctr[kCtrSplits] = tot;
-        ctr[kCtrUnits] = tot + nn;
+        ctr[kCtrIntervals] = tot + nn;
     }
 }
 
@@ -474,25 +496,106 @@ struct __align__(16) UnitDesc {
 };
 static_assert(sizeof(UnitDesc) == 128, "UnitDesc layout");
 
-// One thread per work unit of the level: fills its descriptor.
+// Splitter intervals are packed into work units: a unit starts at interval
+// i when rank(i) / q exceeds rank(i-1) / q, where rank(i) is the output
+// position of the interval's first element (the sum of its start positions
+// in the children).  With spacing ts = c/(2k) no interval exceeds c/2, so a
+// unit stays below q + c/2 = c elements and averages about c/2.
+constexpr int kPackThreads = 256;
+constexpr int kPackItems = 16;
+constexpr int kPackTile = kPackThreads * kPackItems;
+
+__device__ __forceinline__ uint32_t interval_rank(const uint32_t* __restrict__ tab, uint32_t i, int k, uint32_t d) {
+    uint32_t r = 0;
+    for (uint32_t c = 0; c < d; c++) r += tab[(size_t)i * k + c];
+    return r;
+}
+
+__device__ __forceinline__ bool starts_unit(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ unit_node,
+                                            const uint32_t* __restrict__ tab, uint32_t i, int k, uint32_t q) {
+    const LevelNode& nd = nodes[unit_node[i]];
+    const uint32_t local = i - nd.unit_off;
+    if (local == 0) return true;
+    const uint32_t rc = interval_rank(tab, i, k, nd.degree);
+    const uint32_t rp = local == 1 ? 0u : interval_rank(tab, i - 1, k, nd.degree);
+    return rc / q > rp / q;
+}
+
+__global__ void __launch_bounds__(kPackThreads) k_pack_reduce(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ unit_node,
+                                                              const uint32_t* __restrict__ tab, const uint64_t* __restrict__ ctr,
+                                                              int k, uint32_t q, uint32_t* __restrict__ tiles) {
+    __shared__ uint32_t tmp[kPackThreads / 32 + 1];
+    const uint32_t ni = (uint32_t)ctr[kCtrIntervals];
+    const uint32_t i0 = blockIdx.x * kPackTile + threadIdx.x * kPackItems;
+    uint32_t cnt = 0;
+    for (uint32_t j = 0; j < (uint32_t)kPackItems; j++)
+        if (i0 + j < ni) cnt += starts_unit(nodes, unit_node, tab, i0 + j, k, q);
+    uint32_t tot;
+    block_sum_excl<kPackThreads>(cnt, tmp, &tot);
+    if (threadIdx.x == 0) tiles[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_pack_scan(uint32_t* __restrict__ tiles, uint32_t ntiles, uint64_t* __restrict__ ctr) {
+    __shared__ uint32_t tmp[1024 / 32 + 1];
+    const uint32_t per = (ntiles + 1023) / 1024;
+    const uint32_t b = min(ntiles, threadIdx.x * per), e = min(ntiles, b + per);
+    uint32_t acc = 0;
+    for (uint32_t t = b; t < e; t++) acc += tiles[t];
+    uint32_t tot;
+    uint32_t pre = block_sum_excl<1024>(acc, tmp, &tot);
+    for (uint32_t t = b; t < e; t++) {
+        const uint32_t c = tiles[t];
+        tiles[t] = pre;
+        pre += c;
+    }
+    if (threadIdx.x == 0) ctr[kCtrUnits] = tot;
+}
+
+__global__ void __launch_bounds__(kPackThreads) k_pack_apply(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ unit_node,
+                                                             const uint32_t* __restrict__ tab, const uint64_t* __restrict__ ctr,
+                                                             int k, uint32_t q, const uint32_t* __restrict__ tiles,
+                                                             uint32_t* __restrict__ unit_first) {
+    __shared__ uint32_t tmp[kPackThreads / 32 + 1];
+    const uint32_t ni = (uint32_t)ctr[kCtrIntervals];
+    const uint32_t i0 = blockIdx.x * kPackTile + threadIdx.x * kPackItems;
+    uint32_t flags = 0, cnt = 0;
+    for (uint32_t j = 0; j < (uint32_t)kPackItems; j++)
+        if (i0 + j < ni && starts_unit(nodes, unit_node, tab, i0 + j, k, q)) {
+            flags |= 1u << j;
+            cnt++;
+        }
+    uint32_t pos = tiles[blockIdx.x] + block_sum_excl<kPackThreads>(cnt, tmp, nullptr);
+    for (uint32_t j = 0; j < (uint32_t)kPackItems; j++)
+        if (flags & (1u << j)) unit_first[pos++] = i0 + j;
+}
+
+// One thread per packed work unit of the level: fills its descriptor.
 __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ unit_node,
-                                                    const uint32_t* __restrict__ tab, const uint64_t* __restrict__ ctr,
-                                                    const uint32_t* __restrict__ rs, const uint8_t* __restrict__ rdesc, int k,
-                                                    UnitDesc* __restrict__ out) {
+                                                    const uint32_t* __restrict__ unit_first, const uint32_t* __restrict__ tab,
+                                                    const uint64_t* __restrict__ ctr, const uint32_t* __restrict__ rs,
+                                                    const uint8_t* __restrict__ rdesc, int k, UnitDesc* __restrict__ out) {
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= (uint32_t)ctr[kCtrUnits]) return;
-    const LevelNode& nd = nodes[unit_node[u]];
+    const uint32_t nu = (uint32_t)ctr[kCtrUnits];
+    if (u >= nu) return;
+    const uint32_t i0 = unit_first[u];
+    const uint32_t v = unit_node[i0];
+    const LevelNode& nd = nodes[v];
     const uint32_t d = nd.degree;
-    const uint32_t local = u - nd.unit_off;
-    const bool first = local == 0, last = local + 1 == nd.nunits;
+    const uint32_t node_end = nd.unit_off + nd.nunits;   // one past the node's last interval
+    uint32_t i1 = node_end;
+    if (u + 1 < nu) {
+        const uint32_t nx = unit_first[u + 1];
+        if (nx < node_end) i1 = nx;
+    }
+    const bool first = i0 == nd.unit_off, last = i1 == node_end;
     UnitDesc D;
     uint32_t acc = 0, ob = nd.sL, flags = (nd.depth & 1u) << 31;
     for (uint32_t c = 0; c < 8; c++) {
         if (c < d) {
             const uint32_t a = nd.b[c], b = nd.b[c + 1];
             const uint32_t base = rs[a], len = rs[b] - base;
-            const uint32_t st = first ? 0u : tab[(size_t)u * k + c];
-            const uint32_t en = last ? len : tab[(size_t)(u + 1) * k + c];
+            const uint32_t st = first ? 0u : tab[(size_t)i0 * k + c];
+            const uint32_t en = last ? len : tab[(size_t)i1 * k + c];
             const uint32_t leaf = (b == a + 1);
             const uint32_t rev = leaf ? rdesc[a] : 0u;
             D.src[c] = rev ? base + len - 1 - st : base + st;
@@ -514,19 +617,7 @@ __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict_
     out[u] = D;
 }
 
-// ---- asynchronous global -> shared copies (cp.async)
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if (BYTES == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-    else if (BYTES == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-    else asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-constexpr int kLvlThreads = 128;
+constexpr int kLvlThreads = 256;
 constexpr int kLvlIPT = 15;  // odd: conflict-free strides
 
 template <typename K, bool V>
@@ -596,14 +687,19 @@ __global__ void __launch_bounds__(kLvlThreads)
     K* Lb = La + C;
     uint32_t* vLa = V ? reinterpret_cast<uint32_t*>(Lb + C) : nullptr;
     uint32_t* vLb = V ? vLa + C : nullptr;
-    __shared__ UnitDesc D;
+    __shared__ UnitDesc ring[2];
 
     const uint32_t total_units = (uint32_t)ctr[kCtrUnits];
     const uint32_t per = (total_units + gridDim.x - 1) / gridDim.x;
     const uint32_t u0 = blockIdx.x * per;
     const uint32_t u1 = min(total_units, u0 + per);
+    if (u0 < u1 && threadIdx.x < 8)
+        reinterpret_cast<uint4*>(&ring[0])[threadIdx.x] = reinterpret_cast<const uint4*>(udesc + u0)[threadIdx.x];
     for (uint32_t u = u0; u < u1; u++) {
-        if (threadIdx.x < 8) reinterpret_cast<uint4*>(&D)[threadIdx.x] = reinterpret_cast<const uint4*>(udesc + u)[threadIdx.x];
+        const UnitDesc& D = ring[(u - u0) & 1];
+        // the next unit's descriptor is read while this unit is merged
+        uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
+        if (u + 1 < u1 && threadIdx.x < 8) nxt = reinterpret_cast<const uint4*>(udesc + u + 1)[threadIdx.x];
         __syncthreads();
         const uint32_t total = D.total, d = D.d;
         if (total > C) {
@@ -620,10 +716,12 @@ __global__ void __launch_bounds__(kLvlThreads)
             const uint32_t* srcv = lf ? vleaf : vinner;
             for (uint32_t i = threadIdx.x; i < m; i += kLvlThreads) {
                 const uint32_t g = rv ? s0 - i : s0 + i;
-                La[o + i] = srck[g];
-                if (V) vLa[o + i] = srcv[g];
+                cp_async<sizeof(K)>(La + o + i, srck + g);
+                if (V) cp_async<4>(vLa + o + i, srcv + g);
             }
         }
+        cp_async_commit();
+        cp_async_wait<0>();
         __syncthreads();
         K* cur = La;
         K* oth = Lb;
@@ -642,6 +740,7 @@ __global__ void __launch_bounds__(kLvlThreads)
             out[ob + q] = cur[q];
             if (V) vout[ob + q] = vcur[q];
         }
+        if (u + 1 < u1 && threadIdx.x < 8) reinterpret_cast<uint4*>(&ring[(u + 1 - u0) & 1])[threadIdx.x] = nxt;
         __syncthreads();
     }
 }
@@ -663,11 +762,12 @@ __global__ void k_copy_single_run(const K* __restrict__ in, const uint32_t* __re
 
 MergeGeom merge_geom(int key_bytes, bool vals, int k) {
     MergeGeom g;
-    if (key_bytes == 4 && !vals) { g.c_fused = 6144; g.c_level = 4096; }
-    else if (key_bytes == 8 && vals) { g.c_fused = 3072; g.c_level = 2048; }
-    else { g.c_fused = 4096; g.c_level = 2048; }
+    if (key_bytes == 4 && !vals) { g.c_fused = 6144; g.c_level = 8192; }
+    else if (key_bytes == 8 && vals) { g.c_fused = 3072; g.c_level = 4096; }
+    else { g.c_fused = 4096; g.c_level = 4096; }
     g.tmax = g.c_fused;
-    g.ts = g.c_level / (uint32_t)k;
+    g.ts = g.c_level / (2u * (uint32_t)k);
+    g.q = g.c_level / 2;
     g.k = k;
     // persistent level merge: two buffers of c_level elements per block
     size_t lvl_smem = (size_t)2 * g.c_level * ((size_t)key_bytes + (vals ? 4 : 0)) + 256;
@@ -696,30 +796,36 @@ void launch_level_plan(uint32_t level_off, uint32_t nnodes, uint64_t level_elems
     LevelNode* nodes = ws.nodes_lvl + level_off;
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
     k_level_prep<<<1, 1024, 0, st>>>(nodes, nnodes, ws.run_starts, g.ts, ws.counters, ws.unit_node);
-    uint64_t split_bound = level_elems / g.ts + 1;
-    uint32_t blocks = (uint32_t)ceil_div(split_bound * (uint64_t)k, 256);
-    k_level_split<K><<<blocks, 256, 0, st>>>(nodes, nnodes, ws.counters, ws.run_starts, ws.run_desc, leaf_keys, out, tmp,
-                                              g.ts, k, ws.unit_node, ws.split_tab);
-    g_launches += 2;
+    const uint64_t split_bound = level_elems / g.ts + 1;
+    k_level_split<K><<<(uint32_t)ceil_div(split_bound * (uint64_t)k, 256), 256, 0, st>>>(
+        nodes, nnodes, ws.counters, ws.run_starts, ws.run_desc, leaf_keys, out, tmp, g.ts, k, ws.unit_node, ws.split_tab);
+    const uint64_t ivl_bound = split_bound + nnodes;
+    const uint32_t tiles = (uint32_t)ceil_div(ivl_bound, kPackTile);
+    k_pack_reduce<<<tiles, kPackThreads, 0, st>>>(nodes, ws.unit_node, ws.split_tab, ws.counters, k, g.q, ws.pack_tiles);
+    k_pack_scan<<<1, 1024, 0, st>>>(ws.pack_tiles, tiles, ws.counters);
+    k_pack_apply<<<tiles, kPackThreads, 0, st>>>(nodes, ws.unit_node, ws.split_tab, ws.counters, k, g.q, ws.pack_tiles,
+                                                 ws.unit_first);
+    k_level_desc<<<(uint32_t)ceil_div(ivl_bound, 256), 256, 0, st>>>(nodes, ws.unit_node, ws.unit_first, ws.split_tab,
+                                                                     ws.counters, ws.run_starts, ws.run_desc, k,
+                                                                     reinterpret_cast<UnitDesc*>(ws.unit_desc));
+    g_launches += 6;
 }
 
 template <typename K, bool V>
 void launch_level_merge(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys,
                         const uint32_t* leaf_vals, K* out, uint32_t* vout, const MergeGeom& g, const WsView& ws,
                         cudaStream_t st) {
-    LevelNode* nodes = ws.nodes_lvl + level_off;
+    (void)level_off;
+    (void)k;
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
-    uint64_t bound = level_elems / g.ts + nnodes + 1;
-    UnitDesc* udesc = reinterpret_cast<UnitDesc*>(ws.unit_desc);
-    k_level_desc<<<(uint32_t)ceil_div(bound, 256), 256, 0, st>>>(nodes, ws.unit_node, ws.split_tab, ws.counters,
-                                                                 ws.run_starts, ws.run_desc, k, udesc);
+    const uint64_t bound = level_elems / g.ts + nnodes + 1;
     size_t smem = (size_t)2 * g.c_level * (sizeof(K) + (V ? 4 : 0));
     cudaFuncSetAttribute(k_level_merge<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     uint32_t grid = (uint32_t)std::min<uint64_t>(bound, (uint64_t)g.level_grid);
-    k_level_merge<K, V><<<grid, kLvlThreads, smem, st>>>(udesc, ws.counters, leaf_keys, leaf_vals, out, tmp, vout,
-                                                          ws.vals_tmp, g.c_level,
+    k_level_merge<K, V><<<grid, kLvlThreads, smem, st>>>(reinterpret_cast<const UnitDesc*>(ws.unit_desc), ws.counters,
+                                                          leaf_keys, leaf_vals, out, tmp, vout, ws.vals_tmp, g.c_level,
                                                           reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
-    g_launches += 2;
+    g_launches += 1;
 }
 
 template <typename K, bool V>
