@@ -123,6 +123,52 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
                               void* d_keys_in, void* d_keys_out, void* d_ws, size_t ws_bytes,
                               cudaStream_t stream);
 
+/* ---------------------------------------------------------------- batches
+ * A batch is m independent arrays laid end to end in one key buffer:
+ * array a occupies [d_offsets[a], d_offsets[a+1]) with d_offsets[0] = 0 and
+ * d_offsets[m] = n (device memory, non-decreasing; empty arrays allowed).
+ * Every array is sorted on its own with its own runs, powers (Def. 3.1 with
+ * the array's length) and merge tree; one pass of each kernel covers all
+ * arrays, and the launch sequence makes no host synchronisation, so it can be
+ * captured in a CUDA graph (see mps_batch_graph_*).
+ *   max_len : an upper bound on the longest array (sizes the level loop);
+ *             0 means n.
+ *   k       : 2, 4, 8, or 0 for the fan-in chosen by mps_batch_autotune for
+ *             this key type and mean array size (4 until tuned).
+ * n must be below 2^31.  Workspace: mps_batch_workspace_size(n, m, kt,
+ * has_payload, k); k = 0 asks for the largest over k in {2, 4, 8}.
+ * mps_sort_batch and mps_sort_batch_pairs synchronise the stream once at the
+ * end to report device-side check failures. */
+mps_status mps_batch_workspace_size(uint64_t n, uint32_t m, mps_key_type kt, int has_payload, int k, size_t* bytes);
+
+mps_status mps_sort_batch(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
+                          uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Stable key-value form of mps_sort_batch (uint32 payload per key). */
+mps_status mps_sort_batch_pairs(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out,
+                                uint32_t* d_vals_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
+                                uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes,
+                                cudaStream_t stream);
+
+/* Times the batch with k = 2, 4 and 8 (keys only; the output buffer is
+ * overwritten) and records the fastest for this key type and mean array
+ * size; later calls with k = 0 use it.  *best_k receives the choice. */
+mps_status mps_batch_autotune(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m,
+                              uint64_t n, uint64_t max_len, mps_key_type kt, void* d_ws, size_t ws_bytes,
+                              cudaStream_t stream, int* best_k);
+
+/* A batch sort captured once into a CUDA graph for the given buffers (the
+ * graph replays the whole kernel sequence; the buffers must stay valid).
+ * create runs the batch once directly, then captures it on `stream` (which
+ * must not be the legacy default stream).  launch enqueues one replay; with
+ * check != 0 it also synchronises and reports device-side check failures. */
+typedef struct mps_batch_graph mps_batch_graph;
+mps_status mps_batch_graph_create(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m,
+                                  uint64_t n, uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes,
+                                  cudaStream_t stream, mps_batch_graph** out);
+mps_status mps_batch_graph_launch(mps_batch_graph* g, cudaStream_t stream, int check);
+mps_status mps_batch_graph_destroy(mps_batch_graph* g);
+
 /* Sort without any device allocation by the caller or the library (no
  * counterpart in the paper: this is a deployment convenience).  Meant for
  * callers that cannot call cudaMalloc when they need a sort -- code running
@@ -164,6 +210,8 @@ typedef struct {
     uint32_t num_levels, hbm_levels;
     uint64_t bytes_fused, bytes_levels; /* algorithmic bytes of the merge kernels */
     uint64_t launches;                  /* CUDA kernels launched by the call */
+    uint32_t device_status;             /* device-side check code (0 = none) */
+    uint32_t pad;
 } mps_stats;
 
 mps_status mps_last_stats(mps_stats* out);

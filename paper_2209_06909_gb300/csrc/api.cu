@@ -47,9 +47,12 @@ struct Plan {
     size_t o_ctr, o_lvloff, o_det_sum, o_det_pref, o_rs, o_rdesc, o_fused, o_canon, o_lv[kMinTreeLevels], o_info,
         o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_ufirst, o_ptiles, o_hist, o_ktmp, o_vtmp, total;
 
-    explicit Plan(uint64_t n_, int kb_, bool vals_, int k_) : n(n_), kb(kb_), vals(vals_), k(k_) {
+    uint32_t m = 0;  // arrays of a batch (0: a single array)
+    size_t o_bprm = 0;
+
+    explicit Plan(uint64_t n_, int kb_, bool vals_, int k_, uint32_t m_ = 0) : n(n_), kb(kb_), vals(vals_), k(k_), m(m_) {
         g = merge_geom(kb, vals, k);
-        rmax = n / 2 + 2;
+        rmax = n / 2 + m + 2;
         det_tiles = ceil_div(std::max<uint64_t>(n, 1), kDetTile);
         mask_tiles = ceil_div(rmax, kMaskTile);
         nodes_cap = (uint32_t)(34 * (n / g.tmax + 1) + 64);
@@ -84,6 +87,7 @@ struct Plan {
         o_ufirst = take((size_t)unit_cap * 4);
         o_ptiles = take((size_t)(unit_cap / 4096 + 2) * 4);
         o_hist = take(mask_tiles * kMaxLevels * 4);
+        o_bprm = take((size_t)2 * std::max<uint32_t>(m, 1) * 8);
         o_ktmp = take(n * kb);
         o_vtmp = vals ? take(n * 4) : o;
         total = o;
@@ -92,6 +96,7 @@ struct Plan {
     WsView view(void* base) const {
         char* b = static_cast<char*>(base);
         WsView w{};
+        w.n = n;
         w.counters = reinterpret_cast<uint64_t*>(b + o_ctr);
         w.det_sum = reinterpret_cast<uint4*>(b + o_det_sum);
         w.det_pref = reinterpret_cast<uint2*>(b + o_det_pref);
@@ -107,6 +112,7 @@ struct Plan {
         w.mt_g = mt + mask_tiles;
         w.mt_fpre = mt + 2 * mask_tiles;
         w.mt_gsuf = mt + 3 * mask_tiles;
+        w.level_off = reinterpret_cast<uint32_t*>(b + o_lvloff);
         w.nodes_raw = reinterpret_cast<LevelNode*>(b + o_nodes_raw);
         w.nodes_lvl = reinterpret_cast<LevelNode*>(b + o_nodes_lvl);
         w.nodes_cap = nodes_cap;
@@ -120,6 +126,9 @@ struct Plan {
         w.hist = reinterpret_cast<uint32_t*>(b + o_hist);
         w.keys_tmp = b + o_ktmp;
         w.vals_tmp = vals ? reinterpret_cast<uint32_t*>(b + o_vtmp) : nullptr;
+        w.batch_off = nullptr;
+        w.batch_m = 0;
+        w.batch_prm = reinterpret_cast<uint2*>(b + o_bprm);
         return w;
     }
 };
@@ -135,16 +144,6 @@ void set_levels(WsView& w, uint32_t r) {
         len = ceil_div(len, 32);
     }
     w.nlv = nl;
-}
-
-__global__ void k_level_offsets(const uint64_t* __restrict__ ctr, uint32_t* __restrict__ off) {
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int p = 0; p < kMaxLevels; p++) {
-            off[p] = acc;
-            acc += (uint32_t)ctr[kCtrHbmCount + p];
-        }
-    }
 }
 
 // ------------------------------------------------------------- profiling
@@ -283,6 +282,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     MPS_CUDA(cudaGetLastError());
     MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, sizeof(h_ctr), cudaMemcpyDeviceToHost, st));
     MPS_CUDA(cudaStreamSynchronize(st));
+    g_last.device_status = (uint32_t)h_ctr[kCtrStatus];
     if ((uint32_t)h_ctr[kCtrStatus]) return MPS_ERR_DEVICE_CHECK;
     const uint64_t hbm_total = h_ctr[kCtrHbmTotal];
     if (hbm_total > plan.nodes_cap || h_ctr[kCtrFrontier] > plan.fused_cap) return MPS_ERR_DEVICE_CHECK;
@@ -292,37 +292,25 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     g_last.num_levels = (uint32_t)__builtin_popcountll(h_ctr[kCtrLevelBits]);
 
     if (move_keys) {
-        uint32_t* level_off = reinterpret_cast<uint32_t*>(static_cast<char*>(d_ws) + plan.o_lvloff);
-        if (hbm_total) {
-            k_level_offsets<<<1, 32, 0, st>>>(ws.counters, level_off);
-            g_launches += 1;
-            launch_bucket((uint32_t)hbm_total, level_off, ws, st);
-        }
+        if (hbm_total) launch_bucket((uint32_t)hbm_total, ws, st);
         if (h_ctr[kCtrFrontier]) {
             // algorithmic bytes: each element of a fused subtree is read and written once
             ProfScope ps("fused_merge", 2.0 * b * (double)h_ctr[kCtrFrontierElems], st);
             launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, h_ctr[kCtrFrontier], g, ws, st);
         }
-        uint32_t off = 0;
-        std::vector<std::pair<int, uint32_t>> levels;
-        for (int p = 0; p < kMaxLevels; p++) {
-            uint32_t c = (uint32_t)h_ctr[kCtrHbmCount + p];
-            if (c) levels.push_back({p, off});
-            off += c;
-        }
-        g_last.hbm_levels = (uint32_t)levels.size();
         uint64_t lvl_bytes = 0;
-        for (auto it = levels.rbegin(); it != levels.rend(); ++it) {
-            int p = it->first;
-            uint32_t cnt = (uint32_t)h_ctr[kCtrHbmCount + p];
-            uint64_t elems = h_ctr[kCtrHbmSize + p];
+        for (int p = kMaxLevels - 1; p >= 1; p--) {
+            const uint32_t cnt = (uint32_t)h_ctr[kCtrHbmCount + p];
+            if (!cnt) continue;
+            const uint64_t elems = h_ctr[kCtrHbmSize + p];
+            g_last.hbm_levels++;
             lvl_bytes += (uint64_t)(2 * b * elems);
             {
                 ProfScope ps("level_plan", (double)cnt * 64.0, st);
-                launch_level_plan<K>(it->second, cnt, elems, k, keys_in, keys_out, g, ws, st);
+                launch_level_plan<K>(p, cnt, elems, k, keys_in, keys_out, g, ws, st);
             }
             ProfScope ps("level_merge", 2.0 * b * (double)elems, st);
-            launch_level_merge<K, V>(it->second, cnt, elems, k, keys_in, vals_in, keys_out, vals_out, g, ws, st);
+            launch_level_merge<K, V>(cnt, elems, keys_in, vals_in, keys_out, vals_out, g, ws, st);
         }
         g_last.bytes_levels = lvl_bytes;
         MPS_CUDA(cudaGetLastError());
@@ -346,9 +334,77 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     uint32_t status = 0;
     MPS_CUDA(cudaMemcpyAsync(&status, ws.counters + kCtrStatus, 4, cudaMemcpyDeviceToHost, st));
     MPS_CUDA(cudaStreamSynchronize(st));
+    g_last.device_status = status;
     if (status) return MPS_ERR_DEVICE_CHECK;
     g_last.bytes_fused = (uint64_t)(2 * b * (double)h_ctr[kCtrFrontierElems]);
     g_last.launches = g_launches;
+    return MPS_OK;
+}
+
+
+// Largest power that arrays of at most max_len elements can have, plus one:
+// P_k <= ceil((ceil(log2 n) + 1) / log2 k) (Sec. 3.3 bound, squished to k).
+int power_bound(uint64_t max_len, int k) {
+    int lg = 0;
+    while ((1ull << lg) < std::max<uint64_t>(max_len, 1)) lg++;
+    const int t = k == 2 ? 1 : (k == 4 ? 2 : 3);
+    return std::min(kMaxLevels - 1, (lg + 1 + t - 1) / t + 1);
+}
+
+// Batch of m arrays laid end to end (offsets d_off[0..m], d_off[m] = n).
+// Every launch takes its counts from device counters, so the sequence makes
+// no host synchronisation until the optional final status check and can be
+// captured into a CUDA graph.
+template <typename K, bool V>
+mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, uint64_t n,
+                      const uint64_t* d_off, uint32_t m, uint64_t max_len, int k, void* d_ws, size_t ws_bytes,
+                      bool sync_at_end, cudaStream_t st) {
+    if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    if (n == 0) return MPS_OK;
+    if (!keys_in || !keys_out || !d_off || !d_ws || m == 0) return MPS_ERR_INVALID_ARG;
+    if (V && (!vals_in || !vals_out)) return MPS_ERR_INVALID_ARG;
+    if (overlaps(keys_in, n * sizeof(K), keys_out, n * sizeof(K))) return MPS_ERR_INVALID_ARG;
+    if (V && overlaps(vals_in, n * 4, vals_out, n * 4)) return MPS_ERR_INVALID_ARG;
+    Plan plan(n, sizeof(K), V, k, m);
+    if (ws_bytes < plan.total) return MPS_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(d_ws) % 16) return MPS_ERR_INVALID_ARG;
+    WsView ws = plan.view(d_ws);
+    ws.batch_off = d_off;
+    ws.batch_m = m;
+    const MergeGeom& g = plan.g;
+    g_launches = 0;
+    const uint32_t r_bound = (uint32_t)std::min<uint64_t>(plan.rmax, n + 1);
+    set_levels(ws, r_bound);
+    MPS_CUDA(cudaMemsetAsync(ws.counters, 0, kCtrWords * 8, st));
+    launch_detect<K>(keys_in, n, ws, st);
+    launch_powers(n, r_bound, k, ws, st);
+    launch_mintree(r_bound, ws, st);
+    launch_masks(r_bound, false, nullptr, ws, st);
+    launch_node_pass(r_bound, k, g.tmax, ws, st);
+    launch_copy_lone_runs<K, V>(keys_in, vals_in, keys_out, vals_out, r_bound, ws, st);
+    launch_bucket(plan.nodes_cap, ws, st);
+    launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, plan.fused_cap, g, ws, st);
+    const uint32_t nn_bound = (uint32_t)(n / g.tmax + 1);
+    for (int p = power_bound(max_len ? max_len : n, k); p >= 1; p--) {
+        launch_level_plan<K>(p, nn_bound, n, k, keys_in, keys_out, g, ws, st);
+        launch_level_merge<K, V>(nn_bound, n, keys_in, vals_in, keys_out, vals_out, g, ws, st);
+    }
+    MPS_CUDA(cudaGetLastError());
+    if (sync_at_end) {
+        uint64_t h_ctr[8];
+        MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, sizeof(h_ctr), cudaMemcpyDeviceToHost, st));
+        MPS_CUDA(cudaStreamSynchronize(st));
+        g_last = mps_stats{};
+        g_last.n = n;
+        g_last.device_status = (uint32_t)h_ctr[kCtrStatus];
+        if ((uint32_t)h_ctr[kCtrStatus]) return MPS_ERR_DEVICE_CHECK;
+        g_last.r = h_ctr[kCtrR];
+        g_last.merge_cost = h_ctr[kCtrM];
+        g_last.frontier_nodes = h_ctr[kCtrFrontier];
+        g_last.hbm_nodes = h_ctr[kCtrHbmTotal];
+        g_last.launches = g_launches;
+    }
     return MPS_OK;
 }
 
@@ -415,6 +471,185 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
     if (cudaStreamSynchronize(stream) != cudaSuccess) return MPS_ERR_CUDA;
     return MPS_OK;
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------- batches
+
+namespace mps {
+namespace {
+
+std::mutex g_tune_mu;
+int g_tuned_k[2][2][64];  // [key type][payload][log2 of mean array size]; 0 = not tuned
+
+int tuned_k(mps_key_type kt, bool vals, uint64_t n, uint32_t m) {
+    uint64_t mean = m ? n / m : n;
+    int b = 0;
+    while ((1ull << (b + 1)) <= std::max<uint64_t>(mean, 1) && b < 63) b++;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int kk = g_tuned_k[kt == MPS_U64][vals][b];
+    return kk ? kk : 4;
+}
+
+void set_tuned_k(mps_key_type kt, bool vals, uint64_t n, uint32_t m, int kk) {
+    uint64_t mean = m ? n / m : n;
+    int b = 0;
+    while ((1ull << (b + 1)) <= std::max<uint64_t>(mean, 1) && b < 63) b++;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned_k[kt == MPS_U64][vals][b] = kk;
+}
+
+}  // namespace
+
+mps_status batch_dispatch(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out, uint64_t n,
+                          const uint64_t* d_off, uint32_t m, uint64_t max_len, mps_key_type kt, int k, void* d_ws,
+                          size_t ws_bytes, bool sync_at_end, cudaStream_t st) {
+    const bool vals = vals_in != nullptr || vals_out != nullptr;
+    if (k == 0) k = tuned_k(kt, vals, n, m);
+    if (kt == MPS_U32) {
+        if (vals)
+            return batch_impl<uint32_t, true>((const uint32_t*)keys_in, vals_in, (uint32_t*)keys_out, vals_out, n, d_off, m,
+                                              max_len, k, d_ws, ws_bytes, sync_at_end, st);
+        return batch_impl<uint32_t, false>((const uint32_t*)keys_in, nullptr, (uint32_t*)keys_out, nullptr, n, d_off, m,
+                                           max_len, k, d_ws, ws_bytes, sync_at_end, st);
+    }
+    if (kt == MPS_U64) {
+        if (vals)
+            return batch_impl<uint64_t, true>((const uint64_t*)keys_in, vals_in, (uint64_t*)keys_out, vals_out, n, d_off, m,
+                                              max_len, k, d_ws, ws_bytes, sync_at_end, st);
+        return batch_impl<uint64_t, false>((const uint64_t*)keys_in, nullptr, (uint64_t*)keys_out, nullptr, n, d_off, m,
+                                           max_len, k, d_ws, ws_bytes, sync_at_end, st);
+    }
+    return MPS_ERR_INVALID_ARG;
+}
+
+}  // namespace mps
+
+struct mps_batch_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t* counters = nullptr;  // device counter block of the captured workspace
+};
+
+extern "C" {
+
+mps_status mps_batch_workspace_size(uint64_t n, uint32_t m, mps_key_type kt, int has_payload, int k, size_t* bytes) {
+    if (!bytes) return MPS_ERR_INVALID_ARG;
+    if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
+    if (k != 0 && k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    size_t best = 0;
+    for (int kk : {2, 4, 8}) {
+        if (k != 0 && kk != k) continue;
+        Plan p(n, kt == MPS_U32 ? 4 : 8, has_payload != 0, kk, m);
+        best = std::max(best, p.total);
+    }
+    *bytes = best;
+    return MPS_OK;
+}
+
+mps_status mps_sort_batch(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
+                          uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    return batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes, true,
+                          stream);
+}
+
+mps_status mps_sort_batch_pairs(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out, uint32_t* d_vals_out,
+                                const uint64_t* d_offsets, uint32_t m, uint64_t n, uint64_t max_len, mps_key_type kt, int k,
+                                void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!d_vals_in || !d_vals_out) return n ? MPS_ERR_INVALID_ARG : MPS_OK;
+    return batch_dispatch(d_keys_in, d_vals_in, d_keys_out, d_vals_out, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes,
+                          true, stream);
+}
+
+mps_status mps_batch_autotune(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
+                              uint64_t max_len, mps_key_type kt, void* d_ws, size_t ws_bytes, cudaStream_t stream,
+                              int* best_k) {
+    float best_ms = 0.f;
+    int best = 0;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return MPS_ERR_CUDA;
+    mps_status s = MPS_OK;
+    for (int kk : {2, 4, 8}) {
+        s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, kk, d_ws, ws_bytes, true,
+                           stream);
+        if (s != MPS_OK) break;
+        cudaEventRecord(a, stream);
+        for (int rep = 0; rep < 2; rep++)
+            batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, kk, d_ws, ws_bytes, false,
+                           stream);
+        cudaEventRecord(b, stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) { s = MPS_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (!best || ms < best_ms) { best = kk; best_ms = ms; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (s != MPS_OK) return s;
+    set_tuned_k(kt, false, n, m, best);
+    if (best_k) *best_k = best;
+    return MPS_OK;
+}
+
+mps_status mps_batch_graph_create(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
+                                  uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes, cudaStream_t stream,
+                                  mps_batch_graph** out) {
+    if (!out || !stream) return MPS_ERR_INVALID_ARG;
+    *out = nullptr;
+    // one direct run validates the arguments and sets kernel attributes
+    mps_status s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes,
+                                  true, stream);
+    if (s != MPS_OK) return s;
+    mps_batch_graph* g = new mps_batch_graph();
+    g->counters = reinterpret_cast<uint64_t*>(d_ws);
+    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        delete g;
+        return MPS_ERR_CUDA;
+    }
+    s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes, false,
+                       stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(stream, &graph);
+    if (s != MPS_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        delete g;
+        return s != MPS_OK ? s : MPS_ERR_CUDA;
+    }
+    g->graph = graph;
+    if (cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        delete g;
+        return MPS_ERR_CUDA;
+    }
+    *out = g;
+    return MPS_OK;
+}
+
+mps_status mps_batch_graph_launch(mps_batch_graph* g, cudaStream_t stream, int check) {
+    if (!g || !g->exec) return MPS_ERR_INVALID_ARG;
+    if (cudaGraphLaunch(g->exec, stream) != cudaSuccess) return MPS_ERR_CUDA;
+    if (check) {
+        uint32_t status = 0;
+        if (cudaMemcpyAsync(&status, g->counters + kCtrStatus, 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+            return MPS_ERR_CUDA;
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return MPS_ERR_CUDA;
+        if (status) return MPS_ERR_DEVICE_CHECK;
+    }
+    return MPS_OK;
+}
+
+mps_status mps_batch_graph_destroy(mps_batch_graph* g) {
+    if (!g) return MPS_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return MPS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 void mps_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(g_prof_mu);

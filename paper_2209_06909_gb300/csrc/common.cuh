@@ -15,6 +15,11 @@ enum DevError : uint32_t {
     kDevDegree = 1,      // a node had more than k-1 equal-power boundaries
     kDevCapacity = 2,    // a per-call capacity bound was exceeded
     kDevRange = 3,       // a tile did not fit its shared-memory capacity
+    kDevUnitNode = 11,   // a work-unit interval pointed outside its level's nodes
+    kDevUnitRange = 12,  // a work unit's slices or output left the key range
+    kDevFusedRange = 13, // a fused subtree left the key range
+    kDevLoneRange = 14,  // a lone run left the key range
+    kDevPackNode = 15,   // packing saw an interval outside its level's nodes
 };
 
 __device__ __forceinline__ void dev_fail(uint32_t* status, uint32_t code) { atomicCAS(status, 0u, code); }

@@ -46,6 +46,7 @@ struct __align__(16) LevelNode {
 static_assert(sizeof(LevelNode) == 64, "LevelNode layout");
 
 struct WsView {
+    uint64_t n;                    // keys being sorted (all arrays of a batch)
     uint64_t* counters;
     uint4* det_sum;
     uint2* det_pref;
@@ -62,6 +63,7 @@ struct WsView {
     unsigned long long* mt_gsuf;
     uint4* fused_list;             // fused subtrees: {first run, end run, depth, 0}
     uint32_t fused_cap;
+    uint32_t* level_off;           // [64] first bucket entry of each power
     LevelNode* nodes_raw;
     LevelNode* nodes_lvl;
     uint32_t nodes_cap;
@@ -75,6 +77,10 @@ struct WsView {
     uint32_t* hist;                // dump: per-tile power histograms
     void* keys_tmp;
     uint32_t* vals_tmp;
+    // batch of arrays laid end to end (nullptr for a single array)
+    const uint64_t* batch_off;     // [m+1] array starts, batch_off[m] = n
+    uint32_t batch_m;
+    uint2* batch_prm;              // [2m] per-array power parameters
 };
 
 // Sizes of the merge stages for one key/payload type.
@@ -102,7 +108,7 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
 void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st);
 void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView& ws, cudaStream_t st);
 void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st);
-void launch_bucket(uint32_t total, const uint32_t* level_off, const WsView& ws, cudaStream_t st);
+void launch_bucket(uint32_t total_bound, const WsView& ws, cudaStream_t st);
 void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first, void* nodes,
                       uint64_t* counts_out, cudaStream_t st);
 
@@ -110,15 +116,21 @@ void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first,
 template <typename K, bool V>
 void launch_fused(const K* leaf_keys, const uint32_t* leaf_vals, K* out, uint32_t* vout, uint64_t nfused,
                   const MergeGeom& g, const WsView& ws, cudaStream_t st);
+// One power level p of the level merges.  nn_bound / elems_bound bound the
+// level's node and element counts (exact values are read on the device).
 template <typename K>
-void launch_level_plan(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys, K* out,
+void launch_level_plan(int p, uint32_t nn_bound, uint64_t elems_bound, int k, const K* leaf_keys, K* out,
                        const MergeGeom& g, const WsView& ws, cudaStream_t st);
 template <typename K, bool V>
-void launch_level_merge(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys,
-                        const uint32_t* leaf_vals, K* out, uint32_t* vout, const MergeGeom& g, const WsView& ws,
-                        cudaStream_t st);
+void launch_level_merge(uint32_t nn_bound, uint64_t elems_bound, const K* leaf_keys, const uint32_t* leaf_vals, K* out,
+                        uint32_t* vout, const MergeGeom& g, const WsView& ws, cudaStream_t st);
 template <typename K, bool V>
 void launch_copy_single_run(const K* in, const uint32_t* vin, K* out, uint32_t* vout, uint64_t n,
                             const WsView& ws, cudaStream_t st);
+// Batches: arrays that consist of a single run are copied (reversed if
+// strictly descending) straight to the output.
+template <typename K, bool V>
+void launch_copy_lone_runs(const K* in, const uint32_t* vin, K* out, uint32_t* vout, uint32_t r_bound,
+                           const WsView& ws, cudaStream_t st);
 
 }  // namespace mps

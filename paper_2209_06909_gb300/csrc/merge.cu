@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kFusedThreads)
     k_fused(const uint4* __restrict__ flist, const uint64_t* __restrict__ ctr, const K* __restrict__ leaf,
             const uint32_t* __restrict__ vleaf, K* __restrict__ out0, K* __restrict__ out1, uint32_t* __restrict__ vout0,
             uint32_t* __restrict__ vout1, const uint32_t* __restrict__ rs, const uint8_t* __restrict__ rdesc,
-            const uint8_t* __restrict__ P, uint32_t C, int k, uint32_t* __restrict__ status) {
+            const uint8_t* __restrict__ P, uint32_t C, int k, uint64_t n_total, uint32_t* __restrict__ status) {
     extern __shared__ uint4 smem_raw[];
     const uint32_t BMAX = C / 2 + 8;
     K* kA = reinterpret_cast<K*>(smem_raw);
@@ -187,11 +187,19 @@ __global__ void __launch_bounds__(kFusedThreads)
         const uint4 fr = flist[f];
         const uint32_t L = fr.x, R = fr.y;
         const bool odd = fr.z & 1u;
+        if (L >= R) {
+            if (tid == 0) dev_fail(status, kDevFusedRange);
+            continue;
+        }
         const uint32_t s_lo = rs[L];
         const uint32_t len = rs[R] - s_lo;
         if (len > C) {
             if (tid == 0) dev_fail(status, kDevRange);
             return;
+        }
+        if ((uint64_t)s_lo + len > n_total) {
+            if (tid == 0) dev_fail(status, kDevFusedRange);
+            continue;
         }
         const uint32_t nruns = R - L;
         const uint32_t nb = nruns - 1;
@@ -394,8 +402,11 @@ __device__ __forceinline__ uint32_t node_splitters(const LevelNode& nd, const ui
 
 // Per node of the level: number of splitters and work units (one unit more
 // than splitters), their offsets, and unit_node for each node's first unit.
-__global__ void __launch_bounds__(1024) k_level_prep(LevelNode* __restrict__ nodes, uint32_t nn, const uint32_t* __restrict__ rs,
-                                                     uint32_t ts, uint64_t* __restrict__ ctr, uint32_t* __restrict__ unit_node) {
+__global__ void __launch_bounds__(1024) k_level_prep(LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off,
+                                                     int p, const uint32_t* __restrict__ rs, uint32_t ts,
+                                                     uint64_t* __restrict__ ctr, uint32_t* __restrict__ unit_node) {
+    LevelNode* nodes = nodes_lvl + level_off[p];
+    const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
     __shared__ uint32_t tmp[1024 / 32 + 1];
     uint32_t per = (nn + 1023) / 1024;
     uint32_t b = min(nn, threadIdx.x * per), e = min(nn, b + per);
@@ -424,15 +435,21 @@ __global__ void __launch_bounds__(1024) k_level_prep(LevelNode* __restrict__ nod
 // child c' under the order (key, child, position); the k positions give the
 // splitter's slot among the node's splitters, i.e. the work unit it starts.
 template <typename K>
-__global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict__ nodes, uint32_t nn,
+__global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict__ nodes_lvl,
+                                                     const uint32_t* __restrict__ level_off, int p,
                                                      const uint64_t* __restrict__ ctr, const uint32_t* __restrict__ rs,
                                                      const uint8_t* __restrict__ rdesc, const K* __restrict__ leaf,
                                                      const K* __restrict__ buf0, const K* __restrict__ buf1, uint32_t ts, int k,
                                                      uint32_t* __restrict__ unit_node, uint32_t* __restrict__ tab) {
+    const LevelNode* nodes = nodes_lvl + level_off[p];
+    const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
     const uint32_t total = (uint32_t)ctr[kCtrSplits];
-    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t g = gid / k;
-    const uint32_t my_c = gid % k;
+    const uint32_t my_c = threadIdx.x % k;
+    // grid-stride over splitters; the k lanes of a splitter stay in one warp
+    const uint32_t groups_per_grid = gridDim.x * (blockDim.x / k);
+    const uint32_t iters = (total + groups_per_grid - 1) / groups_per_grid;
+    for (uint32_t it = 0; it < iters; it++) {
+    const uint32_t g = it * groups_per_grid + blockIdx.x * (blockDim.x / k) + threadIdx.x / k;
     const bool active = g < total;
     uint32_t split = 0, v = 0, c = 0, unit_base = 0;
     int d = 0;
@@ -481,6 +498,7 @@ __global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict
         if ((int)my_c < d) tab[(size_t)(unit_base + slot + 1) * k + my_c] = split;
         if (my_c == 0) unit_node[unit_base + slot + 1] = v;
     }
+    }
 }
 
 // One work unit of a level: a contiguous slice of each child of one node
@@ -511,9 +529,15 @@ __device__ __forceinline__ uint32_t interval_rank(const uint32_t* __restrict__ t
     return r;
 }
 
-__device__ __forceinline__ bool starts_unit(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ unit_node,
-                                            const uint32_t* __restrict__ tab, uint32_t i, int k, uint32_t q) {
-    const LevelNode& nd = nodes[unit_node[i]];
+__device__ __forceinline__ bool starts_unit(const LevelNode* __restrict__ nodes, uint32_t nn, const uint32_t* __restrict__ unit_node,
+                                            const uint32_t* __restrict__ tab, uint32_t i, int k, uint32_t q,
+                                            uint32_t* __restrict__ status) {
+    const uint32_t v = unit_node[i];
+    if (v >= nn) {
+        dev_fail(status, kDevPackNode);
+        return false;
+    }
+    const LevelNode& nd = nodes[v];
     const uint32_t local = i - nd.unit_off;
     if (local == 0) return true;
     const uint32_t rc = interval_rank(tab, i, k, nd.degree);
@@ -521,15 +545,19 @@ __device__ __forceinline__ bool starts_unit(const LevelNode* __restrict__ nodes,
     return rc / q > rp / q;
 }
 
-__global__ void __launch_bounds__(kPackThreads) k_pack_reduce(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ unit_node,
+__global__ void __launch_bounds__(kPackThreads) k_pack_reduce(const LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off, int p,
+                                                              const uint32_t* __restrict__ unit_node,
                                                               const uint32_t* __restrict__ tab, const uint64_t* __restrict__ ctr,
                                                               int k, uint32_t q, uint32_t* __restrict__ tiles) {
     __shared__ uint32_t tmp[kPackThreads / 32 + 1];
+    const LevelNode* nodes = nodes_lvl + level_off[p];
+    const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
+    uint32_t* status = reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(ctr) + kCtrStatus);
     const uint32_t ni = (uint32_t)ctr[kCtrIntervals];
     const uint32_t i0 = blockIdx.x * kPackTile + threadIdx.x * kPackItems;
     uint32_t cnt = 0;
     for (uint32_t j = 0; j < (uint32_t)kPackItems; j++)
-        if (i0 + j < ni) cnt += starts_unit(nodes, unit_node, tab, i0 + j, k, q);
+        if (i0 + j < ni) cnt += starts_unit(nodes, nn, unit_node, tab, i0 + j, k, q, status);
     uint32_t tot;
     block_sum_excl<kPackThreads>(cnt, tmp, &tot);
     if (threadIdx.x == 0) tiles[blockIdx.x] = tot;
@@ -551,16 +579,20 @@ __global__ void __launch_bounds__(1024) k_pack_scan(uint32_t* __restrict__ tiles
     if (threadIdx.x == 0) ctr[kCtrUnits] = tot;
 }
 
-__global__ void __launch_bounds__(kPackThreads) k_pack_apply(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ unit_node,
+__global__ void __launch_bounds__(kPackThreads) k_pack_apply(const LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off, int p,
+                                                              const uint32_t* __restrict__ unit_node,
                                                              const uint32_t* __restrict__ tab, const uint64_t* __restrict__ ctr,
                                                              int k, uint32_t q, const uint32_t* __restrict__ tiles,
                                                              uint32_t* __restrict__ unit_first) {
     __shared__ uint32_t tmp[kPackThreads / 32 + 1];
+    const LevelNode* nodes = nodes_lvl + level_off[p];
+    const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
+    uint32_t* status = reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(ctr) + kCtrStatus);
     const uint32_t ni = (uint32_t)ctr[kCtrIntervals];
     const uint32_t i0 = blockIdx.x * kPackTile + threadIdx.x * kPackItems;
     uint32_t flags = 0, cnt = 0;
     for (uint32_t j = 0; j < (uint32_t)kPackItems; j++)
-        if (i0 + j < ni && starts_unit(nodes, unit_node, tab, i0 + j, k, q)) {
+        if (i0 + j < ni && starts_unit(nodes, nn, unit_node, tab, i0 + j, k, q, status)) {
             flags |= 1u << j;
             cnt++;
         }
@@ -570,15 +602,25 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_apply(const LevelNode* __
 }
 
 // One thread per packed work unit of the level: fills its descriptor.
-__global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict__ nodes, const uint32_t* __restrict__ unit_node,
+__global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off,
+                                                    int p, const uint32_t* __restrict__ unit_node,
                                                     const uint32_t* __restrict__ unit_first, const uint32_t* __restrict__ tab,
                                                     const uint64_t* __restrict__ ctr, const uint32_t* __restrict__ rs,
                                                     const uint8_t* __restrict__ rdesc, int k, UnitDesc* __restrict__ out) {
-    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    const LevelNode* nodes = nodes_lvl + level_off[p];
+    const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
+    uint32_t* status = reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(ctr) + kCtrStatus);
     const uint32_t nu = (uint32_t)ctr[kCtrUnits];
-    if (u >= nu) return;
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x) {
     const uint32_t i0 = unit_first[u];
     const uint32_t v = unit_node[i0];
+    if (v >= nn) {
+        dev_fail(status, kDevUnitNode);
+        UnitDesc Z;
+        for (int q = 0; q < 32; q++) reinterpret_cast<uint32_t*>(&Z)[q] = 0;
+        out[u] = Z;
+        continue;
+    }
     const LevelNode& nd = nodes[v];
     const uint32_t d = nd.degree;
     const uint32_t node_end = nd.unit_off + nd.nunits;   // one past the node's last interval
@@ -615,6 +657,7 @@ __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict_
     D.flags = flags;
     for (int q = 0; q < 11; q++) D.pad[q] = 0;
     out[u] = D;
+    }
 }
 
 constexpr int kLvlThreads = 256;
@@ -681,7 +724,7 @@ template <typename K, bool V>
 __global__ void __launch_bounds__(kLvlThreads)
     k_level_merge(const UnitDesc* __restrict__ udesc, const uint64_t* __restrict__ ctr, const K* __restrict__ leaf,
                   const uint32_t* __restrict__ vleaf, K* __restrict__ buf0, K* __restrict__ buf1, uint32_t* __restrict__ vbuf0,
-                  uint32_t* __restrict__ vbuf1, uint32_t C, uint32_t* __restrict__ status) {
+                  uint32_t* __restrict__ vbuf1, uint32_t C, uint64_t n, uint32_t* __restrict__ status) {
     extern __shared__ uint4 smem_raw[];
     K* La = reinterpret_cast<K*>(smem_raw);
     K* Lb = La + C;
@@ -705,6 +748,18 @@ __global__ void __launch_bounds__(kLvlThreads)
         if (total > C) {
             if (threadIdx.x == 0) dev_fail(status, kDevRange);
             return;
+        }
+        bool bad = d > 8 || (uint64_t)D.out_base + total > n;
+        for (uint32_t c = 0; c < d && !bad; c++) {
+            const uint32_t m0 = D.off[c + 1] - D.off[c];
+            const bool rv = (D.flags >> (8 + c)) & 1u;
+            bad = m0 > total || (rv ? (m0 > 0 && (D.src[c] >= n || D.src[c] + 1 < m0))
+                                    : (uint64_t)D.src[c] + m0 > n);
+        }
+        if (bad) {
+            if (threadIdx.x == 0) dev_fail(status, kDevUnitRange);
+            __syncthreads();
+            continue;
         }
         const bool odd = D.flags >> 31;
         const K* inner = odd ? buf0 : buf1;                 // children sit at depth + 1
@@ -756,6 +811,32 @@ __global__ void k_copy_single_run(const K* __restrict__ in, const uint32_t* __re
     }
 }
 
+// Batch: run i is alone in its array iff both of its boundaries carry power 0
+// (array starts, or the virtual boundaries 0 and r).  One warp per such run.
+template <typename K, bool V>
+__global__ void k_copy_lone_runs(const K* __restrict__ in, const uint32_t* __restrict__ vin, K* __restrict__ out,
+                                 uint32_t* __restrict__ vout, const uint32_t* __restrict__ rs, const uint8_t* __restrict__ rdesc,
+                                 const uint8_t* __restrict__ P, const uint64_t* __restrict__ ctr, uint64_t n) {
+    const uint32_t r = (uint32_t)ctr[kCtrR];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = warp; i < r; i += nwarps) {
+        if (P[i] != 0 || P[i + 1] != 0) continue;
+        const uint32_t a = rs[i], len = rs[i + 1] - a;
+        if ((uint64_t)a + len > n) {
+            if (lane == 0) dev_fail(const_cast<uint32_t*>(reinterpret_cast<const uint32_t*>(ctr + kCtrStatus)), kDevLoneRange);
+            continue;
+        }
+        const bool rev = rdesc[i] != 0;
+        for (uint32_t q = lane; q < len; q += 32) {
+            const uint32_t src = rev ? a + len - 1 - q : a + q;
+            out[a + q] = in[src];
+            if (V) vout[a + q] = vin[src];
+        }
+    }
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------- launchers
@@ -786,45 +867,44 @@ void launch_fused(const K* leaf_keys, const uint32_t* leaf_vals, K* out, uint32_
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
     k_fused<K, V><<<grid, kFusedThreads, smem, st>>>(ws.fused_list, ws.counters, leaf_keys, leaf_vals, out, tmp, vout,
                                                      ws.vals_tmp, ws.run_starts, ws.run_desc, ws.powers, g.c_fused, g.k,
-                                                     reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
+                                                     ws.n, reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
     g_launches += 1;
 }
 
 template <typename K>
-void launch_level_plan(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys, K* out,
+void launch_level_plan(int p, uint32_t nn_bound, uint64_t elems_bound, int k, const K* leaf_keys, K* out,
                        const MergeGeom& g, const WsView& ws, cudaStream_t st) {
-    LevelNode* nodes = ws.nodes_lvl + level_off;
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
-    k_level_prep<<<1, 1024, 0, st>>>(nodes, nnodes, ws.run_starts, g.ts, ws.counters, ws.unit_node);
-    const uint64_t split_bound = level_elems / g.ts + 1;
-    k_level_split<K><<<(uint32_t)ceil_div(split_bound * (uint64_t)k, 256), 256, 0, st>>>(
-        nodes, nnodes, ws.counters, ws.run_starts, ws.run_desc, leaf_keys, out, tmp, g.ts, k, ws.unit_node, ws.split_tab);
-    const uint64_t ivl_bound = split_bound + nnodes;
+    k_level_prep<<<1, 1024, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.run_starts, g.ts, ws.counters, ws.unit_node);
+    const uint64_t split_bound = elems_bound / g.ts + 1;
+    const uint32_t split_blocks = (uint32_t)std::min<uint64_t>(ceil_div(split_bound * (uint64_t)k, 256), 152 * 16);
+    k_level_split<K><<<split_blocks, 256, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.counters, ws.run_starts, ws.run_desc,
+                                                    leaf_keys, out, tmp, g.ts, k, ws.unit_node, ws.split_tab);
+    const uint64_t ivl_bound = split_bound + nn_bound;
     const uint32_t tiles = (uint32_t)ceil_div(ivl_bound, kPackTile);
-    k_pack_reduce<<<tiles, kPackThreads, 0, st>>>(nodes, ws.unit_node, ws.split_tab, ws.counters, k, g.q, ws.pack_tiles);
+    k_pack_reduce<<<tiles, kPackThreads, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.split_tab, ws.counters, k,
+                                                  g.q, ws.pack_tiles);
     k_pack_scan<<<1, 1024, 0, st>>>(ws.pack_tiles, tiles, ws.counters);
-    k_pack_apply<<<tiles, kPackThreads, 0, st>>>(nodes, ws.unit_node, ws.split_tab, ws.counters, k, g.q, ws.pack_tiles,
-                                                 ws.unit_first);
-    k_level_desc<<<(uint32_t)ceil_div(ivl_bound, 256), 256, 0, st>>>(nodes, ws.unit_node, ws.unit_first, ws.split_tab,
-                                                                     ws.counters, ws.run_starts, ws.run_desc, k,
-                                                                     reinterpret_cast<UnitDesc*>(ws.unit_desc));
+    k_pack_apply<<<tiles, kPackThreads, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.split_tab, ws.counters, k,
+                                                 g.q, ws.pack_tiles, ws.unit_first);
+    const uint32_t desc_blocks = (uint32_t)std::min<uint64_t>(ceil_div(ivl_bound, 256), 152 * 16);
+    k_level_desc<<<desc_blocks, 256, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.unit_first, ws.split_tab,
+                                              ws.counters, ws.run_starts, ws.run_desc, k,
+                                              reinterpret_cast<UnitDesc*>(ws.unit_desc));
     g_launches += 6;
 }
 
 template <typename K, bool V>
-void launch_level_merge(uint32_t level_off, uint32_t nnodes, uint64_t level_elems, int k, const K* leaf_keys,
-                        const uint32_t* leaf_vals, K* out, uint32_t* vout, const MergeGeom& g, const WsView& ws,
-                        cudaStream_t st) {
-    (void)level_off;
-    (void)k;
+void launch_level_merge(uint32_t nn_bound, uint64_t elems_bound, const K* leaf_keys, const uint32_t* leaf_vals, K* out,
+                        uint32_t* vout, const MergeGeom& g, const WsView& ws, cudaStream_t st) {
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
-    const uint64_t bound = level_elems / g.ts + nnodes + 1;
+    const uint64_t bound = elems_bound / g.ts + nn_bound + 1;
     size_t smem = (size_t)2 * g.c_level * (sizeof(K) + (V ? 4 : 0));
     cudaFuncSetAttribute(k_level_merge<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     uint32_t grid = (uint32_t)std::min<uint64_t>(bound, (uint64_t)g.level_grid);
     k_level_merge<K, V><<<grid, kLvlThreads, smem, st>>>(reinterpret_cast<const UnitDesc*>(ws.unit_desc), ws.counters,
                                                           leaf_keys, leaf_vals, out, tmp, vout, ws.vals_tmp, g.c_level,
-                                                          reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
+                                                          ws.n, reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
     g_launches += 1;
 }
 
@@ -836,21 +916,32 @@ void launch_copy_single_run(const K* in, const uint32_t* vin, K* out, uint32_t* 
     g_launches += 1;
 }
 
+template <typename K, bool V>
+void launch_copy_lone_runs(const K* in, const uint32_t* vin, K* out, uint32_t* vout, uint32_t r_bound, const WsView& ws,
+                           cudaStream_t st) {
+    uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r_bound * 32, 256), 152 * 8);
+    k_copy_lone_runs<K, V><<<blocks, 256, 0, st>>>(in, vin, out, vout, ws.run_starts, ws.run_desc, ws.powers, ws.counters,
+                                                    ws.n);
+    g_launches += 1;
+}
+
 #define MPS_INST(K, V)                                                                                                  \
     template void launch_fused<K, V>(const K*, const uint32_t*, K*, uint32_t*, uint64_t, const MergeGeom&,             \
                                      const WsView&, cudaStream_t);                                                      \
-    template void launch_level_merge<K, V>(uint32_t, uint32_t, uint64_t, int, const K*, const uint32_t*, K*, uint32_t*, \
+    template void launch_level_merge<K, V>(uint32_t, uint64_t, const K*, const uint32_t*, K*, uint32_t*,               \
                                            const MergeGeom&, const WsView&, cudaStream_t);                              \
     template void launch_copy_single_run<K, V>(const K*, const uint32_t*, K*, uint32_t*, uint64_t, const WsView&,      \
-                                               cudaStream_t);
+                                               cudaStream_t);                                                           \
+    template void launch_copy_lone_runs<K, V>(const K*, const uint32_t*, K*, uint32_t*, uint32_t, const WsView&,       \
+                                              cudaStream_t);
 MPS_INST(uint32_t, false)
 MPS_INST(uint32_t, true)
 MPS_INST(uint64_t, false)
 MPS_INST(uint64_t, true)
 #undef MPS_INST
-template void launch_level_plan<uint32_t>(uint32_t, uint32_t, uint64_t, int, const uint32_t*, uint32_t*,
-                                          const MergeGeom&, const WsView&, cudaStream_t);
-template void launch_level_plan<uint64_t>(uint32_t, uint32_t, uint64_t, int, const uint64_t*, uint64_t*,
-                                          const MergeGeom&, const WsView&, cudaStream_t);
+template void launch_level_plan<uint32_t>(int, uint32_t, uint64_t, int, const uint32_t*, uint32_t*, const MergeGeom&,
+                                          const WsView&, cudaStream_t);
+template void launch_level_plan<uint64_t>(int, uint32_t, uint64_t, int, const uint64_t*, uint64_t*, const MergeGeom&,
+                                          const WsView&, cudaStream_t);
 
 }  // namespace mps

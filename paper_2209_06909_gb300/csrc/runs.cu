@@ -35,6 +35,19 @@ constexpr int kDetThreads = 256;
 constexpr int kDetItems = 16;
 static_assert(kDetThreads * kDetItems == kDetTile, "detection tile");
 
+// Smallest array start >= x among off[0..m] (a batch of m arrays laid end to
+// end), or ~0 if none.  Without a batch (off == nullptr) element 0 is the only
+// start.
+__device__ __forceinline__ uint64_t next_start(const uint64_t* __restrict__ off, uint32_t m, uint64_t x) {
+    if (off == nullptr) return x == 0 ? 0ull : ~0ull;
+    uint32_t lo = 0, hi = m + 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo <= m ? off[lo] : ~0ull;
+}
+
 __device__ __forceinline__ uint32_t step_state(uint32_t s, bool lt) {
     // B = 0, A = 1, D = 2
     return lt ? (s == 1u ? 0u : 2u) : (s == 2u ? 0u : 1u);
@@ -82,13 +95,16 @@ __device__ __forceinline__ void load_window(const K* __restrict__ keys, uint64_t
 }
 
 template <typename K>
-__device__ __forceinline__ uint4 thread_runsum(const K (&v)[kDetItems + 2], uint64_t n, uint64_t i0) {
+__device__ __forceinline__ uint4 thread_runsum(const K (&v)[kDetItems + 2], uint64_t n, uint64_t i0,
+                                              const uint64_t* __restrict__ off, uint32_t m) {
     uint32_t s0 = 0, s1 = 1, s2 = 2, c0 = 0, c1 = 0, c2 = 0;
+    uint64_t nx = next_start(off, m, i0);
 #pragma unroll
     for (int j = 0; j < kDetItems; j++) {
         uint64_t i = i0 + j;
         if (i < n) {
-            if (i == 0) {
+            if (i == nx) {
+                nx = next_start(off, m, i + 1);
                 s0 = s1 = s2 = 0;
             } else {
                 bool lt = v[1 + j] < v[j];
@@ -101,12 +117,13 @@ __device__ __forceinline__ uint4 thread_runsum(const K (&v)[kDetItems + 2], uint
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kDetThreads) k_det_reduce(const K* __restrict__ keys, uint64_t n, uint4* __restrict__ tile_sum) {
+__global__ void __launch_bounds__(kDetThreads) k_det_reduce(const K* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
+                                                            uint32_t m, uint4* __restrict__ tile_sum) {
     __shared__ uint4 tmp[kDetThreads / 32 + 1];
     uint64_t i0 = (uint64_t)blockIdx.x * kDetTile + (uint64_t)threadIdx.x * kDetItems;
     K v[kDetItems + 2];
     load_window(keys, n, i0, v);
-    uint4 s = thread_runsum(v, n, i0);
+    uint4 s = thread_runsum(v, n, i0, off, m);
     uint4 tot;
     block_scan_excl<kDetThreads, false>(s, OpRunSum(), runsum_identity(), tmp, &tot);
     if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
@@ -137,26 +154,31 @@ __global__ void __launch_bounds__(1024) k_det_scan(const uint4* __restrict__ til
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kDetThreads) k_det_write(const K* __restrict__ keys, uint64_t n, const uint2* __restrict__ tile_pref,
+__global__ void __launch_bounds__(kDetThreads) k_det_write(const K* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
+                                                           uint32_t m, const uint2* __restrict__ tile_pref,
                                                            uint32_t* __restrict__ run_starts, uint8_t* __restrict__ run_desc) {
     __shared__ uint4 tmp[kDetThreads / 32 + 1];
     uint64_t i0 = (uint64_t)blockIdx.x * kDetTile + (uint64_t)threadIdx.x * kDetItems;
     K v[kDetItems + 2];
     load_window(keys, n, i0, v);
-    uint4 s = thread_runsum(v, n, i0);
+    uint4 s = thread_runsum(v, n, i0, off, m);
     uint4 pre = block_scan_excl<kDetThreads, false>(s, OpRunSum(), runsum_identity(), tmp, nullptr);
     uint2 tp = tile_pref[blockIdx.x];
     uint32_t st = map_get(pre.x, tp.x);
     uint32_t cnts[3] = {pre.y, pre.z, pre.w};
     uint32_t idx = tp.y + cnts[tp.x];
+    uint64_t nx = next_start(off, m, i0);
 #pragma unroll
     for (int j = 0; j < kDetItems; j++) {
         uint64_t i = i0 + j;
         if (i < n) {
-            st = (i == 0) ? 0u : step_state(st, v[1 + j] < v[j]);
+            const bool reset = (i == nx);
+            if (reset) nx = next_start(off, m, i + 1);
+            st = reset ? 0u : step_state(st, v[1 + j] < v[j]);
             if (st == 0) {
                 run_starts[idx] = (uint32_t)i;
-                run_desc[idx] = (i + 1 < n && v[2 + j] < v[1 + j]) ? 1 : 0;
+                // descending iff the next element is in the same array and smaller
+                run_desc[idx] = (i + 1 < n && i + 1 != nx && v[2 + j] < v[1 + j]) ? 1 : 0;
                 idx++;
             }
         }
@@ -167,17 +189,39 @@ __global__ void __launch_bounds__(kDetThreads) k_det_write(const K* __restrict__
 // of 255 up to the next multiple of 32, and the bit set of powers that occur.
 __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run_starts, const uint64_t* __restrict__ counters,
                                                 uint64_t n, uint32_t w, uint64_t magic, uint32_t log2k,
+                                                const uint64_t* __restrict__ off, uint32_t m,
+                                                const uint2* __restrict__ arr_param,
                                                 uint8_t* __restrict__ powers, unsigned long long* __restrict__ level_bits) {
     __shared__ unsigned long long red[256 / 32 + 1];
     const uint32_t r = (uint32_t)counters[kCtrR];
     unsigned long long bits = 0;
-    const uint64_t d = 2 * n;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= r; i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t si = run_starts[i];
         uint32_t sp = i >= 1 ? run_starts[i - 1] : 0u;
-        if (i >= 1 && i < r) {
-            uint64_t a2 = (uint64_t)sp + si;                      // 2n * a
-            uint64_t b2 = (uint64_t)si + run_starts[i + 1];       // 2n * b
+        // the array holding run i (a batch sorts each array on its own)
+        uint64_t base = 0, nn = n;
+        uint32_t ww = w;
+        uint64_t mg = magic;
+        bool arr_start = false;
+        if (off != nullptr && i >= 1 && i < r) {
+            uint32_t lo = 0, hi = m + 1;  // last a with off[a] <= si
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (off[mid] <= si) lo = mid; else hi = mid;
+            }
+            base = off[lo];
+            nn = off[lo + 1] - base;
+            arr_start = (base == si);
+            const uint2 prm = arr_param[lo];
+            ww = prm.x;
+            mg = ((uint64_t)prm.y << 32) | arr_param[m + lo].x;
+        }
+        const uint64_t d = 2 * nn;
+        if (i >= 1 && i < r && !arr_start) {
+            uint64_t a2 = (uint64_t)(sp - base) + (si - base);                 // 2n * a
+            uint64_t b2 = (uint64_t)(si - base) + (run_starts[i + 1] - base);  // 2n * b
+            const uint32_t w = ww;
+            const uint64_t magic = mg;
             uint64_t X = a2 << w, Y = b2 << w;
             uint64_t x = __umul64hi(X, magic), y = __umul64hi(Y, magic);
             uint64_t rx = X - x * d, ry = Y - y * d;
@@ -200,6 +244,20 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
     if (threadIdx.x == 0 && bits) atomicOr(level_bits, bits);
 }
 
+// Per-array power parameters of a batch: w = ceil(log2 n_a) and the 64-bit
+// reciprocal floor((2^64 - 1) / (2 n_a)), stored as prm[a] = (w, magic_hi),
+// prm[m + a].x = magic_lo.
+__global__ void k_array_params(const uint64_t* __restrict__ off, uint32_t m, uint2* __restrict__ prm) {
+    for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x) {
+        const uint64_t na = off[a + 1] - off[a];
+        uint32_t w = 0;
+        while ((1ull << w) < na) w++;
+        const uint64_t mg = na ? ~0ull / (2 * na) : 0ull;
+        prm[a] = make_uint2(w, (uint32_t)(mg >> 32));
+        prm[m + a] = make_uint2((uint32_t)mg, 0u);
+    }
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------- launchers
@@ -207,9 +265,9 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
 template <typename K>
 void launch_detect(const K* keys, uint64_t n, const WsView& ws, cudaStream_t st) {
     uint32_t tiles = (uint32_t)ceil_div(n, kDetTile);
-    k_det_reduce<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.det_sum);
+    k_det_reduce<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.batch_off, ws.batch_m, ws.det_sum);
     k_det_scan<<<1, 1024, 0, st>>>(ws.det_sum, tiles, ws.det_pref, ws.counters, ws.run_starts, n);
-    k_det_write<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.det_pref, ws.run_starts, ws.run_desc);
+    k_det_write<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.batch_off, ws.batch_m, ws.det_pref, ws.run_starts, ws.run_desc);
     g_launches += 3;
 }
 
@@ -223,7 +281,13 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
     uint32_t log2k = k == 2 ? 1 : (k == 4 ? 2 : 3);
     uint32_t threads = 256;
     uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r + 1, threads), 152 * 16);
-    k_powers<<<blocks, threads, 0, st>>>(ws.run_starts, ws.counters, n, w, magic, log2k, ws.powers,
+    if (ws.batch_off) {
+        k_array_params<<<(uint32_t)std::min<uint64_t>(ceil_div(ws.batch_m, 256), 1024), 256, 0, st>>>(ws.batch_off, ws.batch_m,
+                                                                                                  ws.batch_prm);
+        g_launches += 1;
+    }
+    k_powers<<<blocks, threads, 0, st>>>(ws.run_starts, ws.counters, n, w, magic, log2k, ws.batch_off, ws.batch_m,
+                                         ws.batch_prm, ws.powers,
                                           reinterpret_cast<unsigned long long*>(ws.counters + kCtrLevelBits));
     g_launches += 1;
 }

@@ -157,9 +157,10 @@ struct OpGRev {
 constexpr int kMaskThreads = 256;
 constexpr int kMaskItems = kMaskTile / kMaskThreads;
 
-__global__ void __launch_bounds__(kMaskThreads) k_mask_reduce(const uint8_t* __restrict__ powers, uint32_t r,
+__global__ void __launch_bounds__(kMaskThreads) k_mask_reduce(const uint8_t* __restrict__ powers, const uint64_t* __restrict__ ctr,
                                                               unsigned long long* __restrict__ tf, unsigned long long* __restrict__ tg) {
     __shared__ unsigned long long tmp[kMaskThreads / 32 + 1];
+    const uint32_t r = (uint32_t)ctr[kCtrR];
     uint32_t nb = r - 1;
     uint32_t b0 = blockIdx.x * kMaskTile + threadIdx.x * kMaskItems;
     unsigned long long f = kMaskIdentity, g = kMaskIdentity;
@@ -200,11 +201,12 @@ __global__ void __launch_bounds__(1024) k_mask_scan(const unsigned long long* __
     }
 }
 
-__global__ void __launch_bounds__(kMaskThreads) k_mask_apply(const uint8_t* __restrict__ powers, uint32_t r,
+__global__ void __launch_bounds__(kMaskThreads) k_mask_apply(const uint8_t* __restrict__ powers, const uint64_t* __restrict__ ctr,
                                                              const unsigned long long* __restrict__ fpre,
                                                              const unsigned long long* __restrict__ gsuf,
                                                              uint8_t* __restrict__ node_info, uint8_t* __restrict__ leaf_depth) {
     __shared__ unsigned long long tmp[kMaskThreads / 32 + 1];
+    const uint32_t r = (uint32_t)ctr[kCtrR];
     uint32_t nb = r - 1;
     uint32_t b0 = blockIdx.x * kMaskTile + threadIdx.x * kMaskItems;
     uint64_t e[kMaskItems];
@@ -233,14 +235,15 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask_apply(const uint8_t* __re
         if (b < nb) {
             uint32_t j = b + 1;
             uint32_t p = mmin(e[q]);
-            uint64_t left = pf & kBits, right = gex[q] & kBits;
+            uint64_t left = pf & kBits & ~1ull, right = gex[q] & kBits & ~1ull;
             uint32_t depth = __popcll((left | right) & below(p));
-            uint32_t start = ((left >> p) & 1ull) ? 0u : 1u;
+            // power 0 marks an array start inside a batch: never a node boundary
+            uint32_t start = (p == 0 || ((left >> p) & 1ull)) ? 0u : 1u;
             node_info[j] = (uint8_t)(depth | (start << 7));
             if (leaf_depth) {
-                uint64_t incl = OpF()(pf, e[q]) & kBits;
+                uint64_t incl = OpF()(pf, e[q]) & kBits & ~1ull;
                 leaf_depth[j] = (uint8_t)__popcll(incl | right);
-                if (j == 1) leaf_depth[0] = (uint8_t)__popcll(OpG()(e[q], gex[q]) & kBits);
+                if (j == 1) leaf_depth[0] = (uint8_t)__popcll(OpG()(e[q], gex[q]) & kBits & ~1ull);
             }
         }
         pf = OpF()(pf, e[q]);
@@ -279,7 +282,7 @@ __device__ __forceinline__ bool node_shape(const MinTree& T, const uint8_t* P, u
 // become level-merge records; such a node also appends each child that is an
 // inner node of at most T_max elements to the list of fused subtrees (its
 // parent is large, so it is maximal).  A small root is a fused subtree too.
-__global__ void __launch_bounds__(256) k_node_pass(MinTree T, uint32_t r, int k, uint32_t tmax,
+__global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tmax,
                                                    const uint32_t* __restrict__ rs, const uint8_t* __restrict__ node_info,
                                                    uint64_t* __restrict__ ctr, LevelNode* __restrict__ nodes_raw, uint32_t nodes_cap,
                                                    uint4* __restrict__ fused_list, uint32_t fused_cap) {
@@ -287,11 +290,13 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, uint32_t r, int k,
     const uint8_t* P = T.lv[0];
     uint32_t* status = reinterpret_cast<uint32_t*>(ctr + kCtrStatus);
     unsigned long long msize = 0, nstarts = 0;
+    const uint32_t r = (uint32_t)ctr[kCtrR];
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x + 1; j < r; j += gridDim.x * blockDim.x) {
         uint8_t info = node_info[j];
         if (!(info & 0x80)) continue;
-        nstarts++;
         const uint32_t v = P[j];
+        if (v == 0) continue;
+        nstarts++;
         const uint32_t L = nsv_left(T, j, v, true);
         const uint32_t R = nsv_right(T, j, v, true);
         const uint32_t sL = rs[L], sR = rs[R];
@@ -327,9 +332,10 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, uint32_t r, int k,
                 }
             }
             if (fe) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), fe);
-        } else if (L == 0 && R == r) {
+        } else if (P[L] == 0 && P[R] == 0) {
+            // a root (of the array, or of one array of a batch) that fits a fused tile
             uint32_t fs = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
-            if (fs < fused_cap) fused_list[fs] = make_uint4(0u, r, 0u, 0u);
+            if (fs < fused_cap) fused_list[fs] = make_uint4(L, R, 0u, 0u);
             else dev_fail(status, kDevCapacity);
             atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), (unsigned long long)size);
         }
@@ -344,13 +350,25 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, uint32_t r, int k,
 
 // Copies level-merge nodes into per-power buckets (order within a bucket is
 // irrelevant: nodes of one power are disjoint).
-__global__ void k_bucket(const LevelNode* __restrict__ raw, uint32_t total, const uint32_t* __restrict__ level_off,
-                         uint64_t* __restrict__ ctr, LevelNode* __restrict__ out) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    LevelNode nd = raw[i];
-    uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmFill + nd.power), 1ull);
-    out[level_off[nd.power] + slot] = nd;
+__global__ void k_bucket(const LevelNode* __restrict__ raw, const uint32_t* __restrict__ level_off,
+                         uint64_t* __restrict__ ctr, LevelNode* __restrict__ out, uint32_t cap) {
+    const uint32_t total = min((uint32_t)ctr[kCtrHbmTotal], cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        LevelNode nd = raw[i];
+        uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmFill + nd.power), 1ull);
+        out[level_off[nd.power] + slot] = nd;
+    }
+}
+
+// Exclusive offsets of the per-power node buckets (one thread).
+__global__ void k_level_offsets(const uint64_t* __restrict__ ctr, uint32_t* __restrict__ off) {
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int p = 0; p < kMaxLevels; p++) {
+            off[p] = acc;
+            acc += (uint32_t)ctr[kCtrHbmCount + p];
+        }
+    }
 }
 
 // ------------------------------------------------------------- tree dump
@@ -478,9 +496,9 @@ void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st) {
 void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView& ws, cudaStream_t st) {
     uint32_t nb = r - 1;
     uint32_t tiles = (uint32_t)ceil_div(nb, kMaskTile);
-    k_mask_reduce<<<tiles, kMaskThreads, 0, st>>>(ws.powers, r, ws.mt_f, ws.mt_g);
+    k_mask_reduce<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.mt_f, ws.mt_g);
     k_mask_scan<<<1, 1024, 0, st>>>(ws.mt_f, ws.mt_g, tiles, ws.mt_fpre, ws.mt_gsuf);
-    k_mask_apply<<<tiles, kMaskThreads, 0, st>>>(ws.powers, r, ws.mt_fpre, ws.mt_gsuf, ws.node_info,
+    k_mask_apply<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.mt_fpre, ws.mt_gsuf, ws.node_info,
                                                   dump_leaf ? leaf_depth : nullptr);
     g_launches += 3;
 }
@@ -488,15 +506,16 @@ void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView&
 void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st) {
     uint32_t nb = r - 1;
     uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(nb, 256), 152 * 16);
-    k_node_pass<<<blocks, 256, 0, st>>>(make_mintree(ws), r, k, tmax, ws.run_starts, ws.node_info,
+    k_node_pass<<<blocks, 256, 0, st>>>(make_mintree(ws), k, tmax, ws.run_starts, ws.node_info,
                                                               ws.counters, ws.nodes_raw, ws.nodes_cap, ws.fused_list, ws.fused_cap);
     g_launches += 1;
 }
 
-void launch_bucket(uint32_t total, const uint32_t* level_off, const WsView& ws, cudaStream_t st) {
-    if (!total) return;
-    k_bucket<<<(uint32_t)ceil_div(total, 256), 256, 0, st>>>(ws.nodes_raw, total, level_off, ws.counters, ws.nodes_lvl);
-    g_launches += 1;
+void launch_bucket(uint32_t total_bound, const WsView& ws, cudaStream_t st) {
+    k_level_offsets<<<1, 32, 0, st>>>(ws.counters, ws.level_off);
+    uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(std::max<uint32_t>(total_bound, 1), 256), 152 * 8);
+    k_bucket<<<blocks, 256, 0, st>>>(ws.nodes_raw, ws.level_off, ws.counters, ws.nodes_lvl, ws.nodes_cap);
+    g_launches += 2;
 }
 
 void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first, void* nodes, uint64_t* counts_out,

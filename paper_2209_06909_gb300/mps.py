@@ -44,11 +44,14 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("r", ctypes.c_uint64), ("merge_cost", ctypes.c_uint64),
                 ("frontier_nodes", ctypes.c_uint64), ("hbm_nodes", ctypes.c_uint64),
                 ("num_levels", ctypes.c_uint32), ("hbm_levels", ctypes.c_uint32),
-                ("bytes_fused", ctypes.c_uint64), ("bytes_levels", ctypes.c_uint64), ("launches", ctypes.c_uint64)]
+                ("bytes_fused", ctypes.c_uint64), ("bytes_levels", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("device_status", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_tree", "mps_sort_keys_host",
-           "mps_profile_enable", "mps_profile_read", "mps_last_stats", "mps_status_string", "mps_sort_keys_noalloc"]
+           "mps_profile_enable", "mps_profile_read", "mps_last_stats", "mps_status_string", "mps_sort_keys_noalloc",
+           "mps_batch_workspace_size", "mps_sort_batch", "mps_sort_batch_pairs", "mps_batch_autotune",
+           "mps_batch_graph_create", "mps_batch_graph_launch", "mps_batch_graph_destroy"]
 
 # Largest n accepted by mps_sort_keys_noalloc (its scratch is compiled into the library).
 NOALLOC_MAX_N = 1 << 20
@@ -77,6 +80,17 @@ def lib():
     L.mps_last_stats.argtypes = [P]
     L.mps_sort_keys_noalloc.argtypes = [P, P, U64, I, I, P]
     L.mps_sort_keys_noalloc.restype = I
+    U32 = ctypes.c_uint32
+    L.mps_batch_workspace_size.argtypes = [U64, U32, I, I, I, ctypes.POINTER(ctypes.c_size_t)]
+    L.mps_sort_batch.argtypes = [P, P, P, U32, U64, U64, I, I, P, ctypes.c_size_t, P]
+    L.mps_sort_batch_pairs.argtypes = [P, P, P, P, P, U32, U64, U64, I, I, P, ctypes.c_size_t, P]
+    L.mps_batch_autotune.argtypes = [P, P, P, U32, U64, U64, I, P, ctypes.c_size_t, P, ctypes.POINTER(I)]
+    L.mps_batch_graph_create.argtypes = [P, P, P, U32, U64, U64, I, I, P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    L.mps_batch_graph_launch.argtypes = [P, P, I]
+    L.mps_batch_graph_destroy.argtypes = [P]
+    for fn in ("mps_batch_workspace_size", "mps_sort_batch", "mps_sort_batch_pairs", "mps_batch_autotune",
+               "mps_batch_graph_create", "mps_batch_graph_launch", "mps_batch_graph_destroy"):
+        getattr(L, fn).restype = I
     L.mps_status_string.argtypes = [I]
     L.mps_status_string.restype = ctypes.c_char_p
     for fn in ("mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_tree", "mps_sort_keys_host",
@@ -87,6 +101,12 @@ def lib():
 
 
 def _check(fn, code):
+    if code == 7:  # device-side check: report which one
+        s = Stats()
+        lib().mps_last_stats(ctypes.byref(s))
+        err = MpsError(fn, code)
+        err.args = (f"{err.args[0]} [device status {s.device_status}]",)
+        raise err
     if code != 0:
         raise MpsError(fn, code)
 
@@ -218,6 +238,74 @@ def sort_keys_noalloc(keys: torch.Tensor, out: torch.Tensor, k: int = 4, stream=
     _check("mps_sort_keys_noalloc", lib().mps_sort_keys_noalloc(keys.data_ptr(), out.data_ptr(), keys.numel(),
                                                                 _key_type(keys), k, _stream(stream)))
     return out
+
+
+def batch_workspace(n: int, m: int, key_bytes: int, has_payload: bool = False, k: int = 0, device="cuda") -> torch.Tensor:
+    out = ctypes.c_size_t(0)
+    _check("mps_batch_workspace_size", lib().mps_batch_workspace_size(n, m, 0 if key_bytes == 4 else 1,
+                                                                      int(has_payload), k, ctypes.byref(out)))
+    return torch.empty(max(out.value, 16), dtype=torch.uint8, device=device)
+
+
+def sort_batch(keys: torch.Tensor, offsets: torch.Tensor, k: int = 0, out: torch.Tensor | None = None,
+               ws: torch.Tensor | None = None, max_len: int = 0, stream=None) -> torch.Tensor:
+    """Sorts every array of a batch (mps_sort_batch); offsets: int64 device
+    tensor of m+1 array starts."""
+    n, m = keys.numel(), offsets.numel() - 1
+    out = torch.empty_like(keys) if out is None else out
+    ws = batch_workspace(n, m, keys.element_size(), False, k, keys.device) if ws is None else ws
+    _check("mps_sort_batch", lib().mps_sort_batch(keys.data_ptr(), out.data_ptr(), offsets.data_ptr(), m, n, max_len,
+                                                  _key_type(keys), k, ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out
+
+
+def sort_batch_pairs(keys: torch.Tensor, vals: torch.Tensor, offsets: torch.Tensor, k: int = 0, out_keys=None,
+                     out_vals=None, ws=None, max_len: int = 0, stream=None):
+    n, m = keys.numel(), offsets.numel() - 1
+    out_keys = torch.empty_like(keys) if out_keys is None else out_keys
+    out_vals = torch.empty_like(vals) if out_vals is None else out_vals
+    ws = batch_workspace(n, m, keys.element_size(), True, k, keys.device) if ws is None else ws
+    _check("mps_sort_batch_pairs", lib().mps_sort_batch_pairs(keys.data_ptr(), vals.data_ptr(), out_keys.data_ptr(),
+                                                              out_vals.data_ptr(), offsets.data_ptr(), m, n, max_len,
+                                                              _key_type(keys), k, ws.data_ptr(), ws.numel(),
+                                                              _stream(stream)))
+    return out_keys, out_vals
+
+
+def batch_autotune(keys: torch.Tensor, offsets: torch.Tensor, out: torch.Tensor, ws: torch.Tensor, max_len: int = 0,
+                   stream=None) -> int:
+    best = ctypes.c_int(0)
+    n, m = keys.numel(), offsets.numel() - 1
+    _check("mps_batch_autotune", lib().mps_batch_autotune(keys.data_ptr(), out.data_ptr(), offsets.data_ptr(), m, n,
+                                                          max_len, _key_type(keys), ws.data_ptr(), ws.numel(),
+                                                          _stream(stream), ctypes.byref(best)))
+    return best.value
+
+
+class BatchGraph:
+    """A batch sort captured once in a CUDA graph (mps_batch_graph_*)."""
+
+    def __init__(self, keys, offsets, out, ws, k=0, max_len=0, stream=None):
+        self.handle = ctypes.c_void_p()
+        self.keep = (keys, offsets, out, ws)
+        n, m = keys.numel(), offsets.numel() - 1
+        _check("mps_batch_graph_create", lib().mps_batch_graph_create(
+            keys.data_ptr(), out.data_ptr(), offsets.data_ptr(), m, n, max_len, _key_type(keys), k, ws.data_ptr(),
+            ws.numel(), _stream(stream), ctypes.byref(self.handle)))
+
+    def launch(self, stream=None, check=False):
+        _check("mps_batch_graph_launch", lib().mps_batch_graph_launch(self.handle, _stream(stream), int(check)))
+
+    def close(self):
+        if self.handle:
+            lib().mps_batch_graph_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def profile_enable(on: bool = True) -> None:
