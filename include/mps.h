@@ -169,6 +169,64 @@ mps_status mps_batch_graph_create(const void* d_keys_in, void* d_keys_out, const
 mps_status mps_batch_graph_launch(mps_batch_graph* g, cudaStream_t stream, int check);
 mps_status mps_batch_graph_destroy(mps_batch_graph* g);
 
+/* ---------------------------------------------------------------- serving
+ * A request queue with continuous batching.  Clients submit sort requests on
+ * device buffers they own (inputs must stay unchanged and outputs untouched
+ * until the request completes).  A worker thread admits pending requests
+ * against a device memory budget -- the pool the caller hands over at
+ * creation -- groups consecutive requests of the same kind into a batch,
+ * stages their inputs in the pool, sorts the batch (mps_sort_batch's kernels,
+ * no host synchronisation), and copies each result to its client's output.
+ * Up to max_inflight batches run at once on separate streams, so requests
+ * that arrive while others are on the GPU are admitted as pool memory and a
+ * stream free up, and their work overlaps on the device.  Each result is
+ * exactly the sort the request would get alone. */
+typedef struct {
+    void* d_pool;           /* device memory owned by the caller, used as the budget */
+    size_t pool_bytes;      /* admission budget in bytes */
+    uint32_t max_inflight;  /* batches (streams) in flight, 0 -> 2 */
+    uint32_t max_batch;     /* requests per batch, 0 -> 256 */
+    uint32_t timeout_ms;    /* reserved for bounded waits, 0 -> 10000 */
+    int k;                  /* fan-in 2, 4 or 8; 0 -> 4 */
+} mps_queue_config;
+
+typedef struct {
+    mps_key_type kt;        /* MPS_U32 or MPS_U64 keys */
+    int has_payload;        /* 1: uint32 payload per key (stable) */
+    uint64_t n;
+    const void* d_keys_in;
+    const uint32_t* d_vals_in;
+    void* d_keys_out;
+    uint32_t* d_vals_out;
+    uint64_t tag;           /* returned in the result */
+} mps_request;
+
+typedef struct {
+    mps_status status;      /* MPS_OK, MPS_ERR_CANCELLED, MPS_ERR_DEVICE_CHECK, ... */
+    uint32_t device_status; /* device-side check code when status is MPS_ERR_DEVICE_CHECK */
+    uint64_t tag;
+    double t_submit_ms, t_admit_ms, t_done_ms;  /* milliseconds since the queue was created */
+} mps_result;
+
+typedef struct mps_queue mps_queue;
+
+/* Starts the worker thread and its streams.  MPS_ERR_INVALID_ARG if the pool
+ * is missing; the pool stays the caller's and must outlive the queue. */
+mps_status mps_queue_create(const mps_queue_config* cfg, mps_queue** q);
+/* Enqueues a request; *ticket identifies it.  MPS_ERR_BUDGET if the request
+ * alone cannot fit the budget, MPS_ERR_INVALID_ARG for missing buffers. */
+mps_status mps_queue_submit(mps_queue* q, const mps_request* req, uint64_t* ticket);
+/* MPS_ERR_NOT_READY while the request is pending or in flight; otherwise
+ * fills *res and forgets the ticket. */
+mps_status mps_queue_poll(mps_queue* q, uint64_t ticket, mps_result* res);
+/* Waits at most timeout_ms for the request (MPS_ERR_TIMEOUT otherwise). */
+mps_status mps_queue_wait(mps_queue* q, uint64_t ticket, uint32_t timeout_ms, mps_result* res);
+/* Holds (1) or resumes (0) admission of new batches; batches in flight run on. */
+mps_status mps_queue_pause(mps_queue* q, int paused);
+/* Cancels pending requests (status MPS_ERR_CANCELLED), drains batches in
+ * flight, stops the worker. */
+mps_status mps_queue_destroy(mps_queue* q);
+
 /* Sort without any device allocation by the caller or the library (no
  * counterpart in the paper: this is a deployment convenience).  Meant for
  * callers that cannot call cudaMalloc when they need a sort -- code running

@@ -1,0 +1,402 @@
+// queue.cu -- request queue with continuous batching (serving).
+//
+// Clients submit sort requests (device input and output buffers they own).
+// A worker thread admits pending requests against a device memory budget --
+// a pool the caller hands over at creation -- groups consecutive requests of
+// one kind (uint32 keys, or uint64 keys with uint32 payloads) into a batch,
+// copies their inputs into pool memory laid end to end, sorts the batch with
+// the batch path (no host synchronisation inside), copies every result to its
+// client's output buffer, and records an event.  Several batches are in
+// flight at once on separate streams, so requests that arrive while others
+// run are admitted as soon as pool memory and a stream free up, and their
+// work overlaps on the device.  A finished batch releases its pool memory.
+// Every wait is bounded; nothing spins on the device.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/mps.h"
+
+namespace mps {
+mps_status batch_dispatch(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out, uint64_t n,
+                          const uint64_t* d_off, uint32_t m, uint64_t max_len, mps_key_type kt, int k, void* d_ws,
+                          size_t ws_bytes, bool sync_at_end, cudaStream_t st);
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr size_t kPoolAlign = 256;
+
+size_t align_up(size_t x) { return (x + kPoolAlign - 1) / kPoolAlign * kPoolAlign; }
+
+// First-fit allocator over [0, size) of the pool.
+class PoolAllocator {
+public:
+    explicit PoolAllocator(size_t size) { free_[0] = size; }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = align_up(bytes ? bytes : 1);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                size_t rest = it->second - bytes;
+                size_t start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = align_up(bytes ? bytes : 1);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+
+private:
+    std::map<size_t, size_t> free_;
+    size_t used_ = 0;
+};
+
+struct Ticket {
+    mps_request req;
+    mps_result res;
+    bool done = false;
+    Clock::time_point t_submit, t_admit, t_done;
+};
+
+struct Batch {
+    std::vector<uint64_t> tickets;
+    std::vector<std::pair<size_t, size_t>> blocks;  // pool allocations (offset, bytes)
+    cudaEvent_t done = nullptr;
+    int stream = 0;
+};
+
+size_t request_footprint(const mps_request& r) {
+    const size_t kb = r.kt == MPS_U32 ? 4 : 8;
+    const size_t b = kb + (r.has_payload ? 4 : 0);
+    size_t ws = 0;
+    mps_batch_workspace_size(r.n, 1, r.kt, r.has_payload, 0, &ws);  // largest over k
+    return 2 * align_up(r.n * b) + align_up(ws) + 8 * kPoolAlign;
+}
+
+}  // namespace
+
+struct mps_queue {
+    mps_queue_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv;       // wakes the worker
+    std::condition_variable cv_done;  // wakes waiters
+    std::map<uint64_t, Ticket> tickets;
+    std::deque<uint64_t> pending;
+    std::vector<Batch> inflight;
+    std::vector<cudaStream_t> streams;
+    std::vector<int> stream_busy;
+    std::vector<uint64_t*> h_off;     // pinned offsets staging, one per stream
+    std::vector<uint32_t*> h_status;  // pinned device-status readback, one per stream
+    PoolAllocator alloc{0};
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    bool paused = false;
+    Clock::time_point t0;
+    std::thread worker;
+};
+
+namespace {
+
+double ms_since(const Clock::time_point& t0, const Clock::time_point& t) {
+    return std::chrono::duration<double, std::milli>(t - t0).count();
+}
+
+// Launches one batch of admitted tickets (lock held by the caller).
+mps_status launch_batch(mps_queue* q, std::vector<uint64_t>& ids, int sidx, Batch& B) {
+    const mps_request& r0 = q->tickets[ids[0]].req;
+    const mps_key_type kt = r0.kt;
+    const bool vals = r0.has_payload != 0;
+    const size_t kb = kt == MPS_U32 ? 4 : 8;
+    uint64_t n = 0, max_len = 0;
+    for (uint64_t id : ids) {
+        n += q->tickets[id].req.n;
+        max_len = std::max<uint64_t>(max_len, q->tickets[id].req.n);
+    }
+    const uint32_t m = (uint32_t)ids.size();
+    size_t ws = 0;
+    mps_status s = mps_batch_workspace_size(n, m, kt, vals, q->cfg.k ? q->cfg.k : 4, &ws);
+    if (s != MPS_OK) return s;
+    const size_t sizes[6] = {n * kb, n * kb, vals ? n * 4 : 0, vals ? n * 4 : 0, (size_t)(m + 1) * 8, ws};
+    size_t offs[6];
+    for (int i = 0; i < 6; i++) {
+        if (!q->alloc.alloc(sizes[i], &offs[i])) {
+            for (int j = 0; j < i; j++) q->alloc.release(offs[j], sizes[j]);
+            return MPS_ERR_BUDGET;
+        }
+    }
+    for (int i = 0; i < 6; i++) B.blocks.push_back({offs[i], sizes[i]});
+    char* pool = static_cast<char*>(q->cfg.d_pool);
+    char* kin = pool + offs[0];
+    char* kout = pool + offs[1];
+    uint32_t* vin = vals ? reinterpret_cast<uint32_t*>(pool + offs[2]) : nullptr;
+    uint32_t* vout = vals ? reinterpret_cast<uint32_t*>(pool + offs[3]) : nullptr;
+    uint64_t* d_off = reinterpret_cast<uint64_t*>(pool + offs[4]);
+    void* d_ws = pool + offs[5];
+    cudaStream_t st = q->streams[sidx];
+    uint64_t* h_off = q->h_off[sidx];
+    uint64_t acc = 0;
+    for (uint32_t i = 0; i < m; i++) {
+        const mps_request& r = q->tickets[ids[i]].req;
+        h_off[i] = acc;
+        if (r.n) {
+            cudaMemcpyAsync(kin + acc * kb, r.d_keys_in, r.n * kb, cudaMemcpyDeviceToDevice, st);
+            if (vals) cudaMemcpyAsync(vin + acc, r.d_vals_in, r.n * 4, cudaMemcpyDeviceToDevice, st);
+        }
+        acc += r.n;
+    }
+    h_off[m] = acc;
+    cudaMemcpyAsync(d_off, h_off, (size_t)(m + 1) * 8, cudaMemcpyHostToDevice, st);
+    *q->h_status[sidx] = 0;  // the stream is idle: no copy into this buffer is pending
+    if (n) {
+        s = mps::batch_dispatch(kin, vin, kout, vout, n, d_off, m, max_len, kt, q->cfg.k ? q->cfg.k : 4, d_ws, ws, false,
+                                st);
+        if (s != MPS_OK) return s;
+        // device status word: entry 5 of the workspace's leading 64-bit counter block
+        cudaMemcpyAsync(q->h_status[sidx], reinterpret_cast<char*>(d_ws) + 5 * 8, 4, cudaMemcpyDeviceToHost, st);
+    }
+    for (uint32_t i = 0; i < m; i++) {
+        const mps_request& r = q->tickets[ids[i]].req;
+        if (!r.n) continue;
+        cudaMemcpyAsync(r.d_keys_out, kout + h_off[i] * kb, r.n * kb, cudaMemcpyDeviceToDevice, st);
+        if (vals) cudaMemcpyAsync(r.d_vals_out, vout + h_off[i], r.n * 4, cudaMemcpyDeviceToDevice, st);
+    }
+    if (cudaEventCreateWithFlags(&B.done, cudaEventDisableTiming) != cudaSuccess) return MPS_ERR_CUDA;
+    if (cudaEventRecord(B.done, st) != cudaSuccess) return MPS_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return MPS_ERR_CUDA;
+    B.tickets = ids;
+    B.stream = sidx;
+    return MPS_OK;
+}
+
+void release_batch(mps_queue* q, Batch& B) {
+    for (auto& b : B.blocks) q->alloc.release(b.first, b.second);
+    B.blocks.clear();
+    if (B.done) cudaEventDestroy(B.done);
+    B.done = nullptr;
+}
+
+void finish_tickets(mps_queue* q, const std::vector<uint64_t>& ids, mps_status s, uint32_t dev_status = 0) {
+    const auto now = Clock::now();
+    for (uint64_t id : ids) {
+        Ticket& t = q->tickets[id];
+        t.done = true;
+        t.t_done = now;
+        t.res.status = s;
+        t.res.device_status = dev_status;
+        t.res.tag = t.req.tag;
+        t.res.t_submit_ms = ms_since(q->t0, t.t_submit);
+        t.res.t_admit_ms = ms_since(q->t0, t.t_admit);
+        t.res.t_done_ms = ms_since(q->t0, now);
+    }
+}
+
+void worker_main(mps_queue* q) {
+    std::unique_lock<std::mutex> lk(q->mu);
+    while (true) {
+        // 1. retire finished batches
+        bool progressed = false;
+        for (size_t i = 0; i < q->inflight.size();) {
+            Batch& B = q->inflight[i];
+            cudaError_t e = cudaEventQuery(B.done);
+            if (e == cudaErrorNotReady) { i++; continue; }
+            const uint32_t dev = *q->h_status[B.stream];
+            mps_status s = e == cudaSuccess ? (dev ? MPS_ERR_DEVICE_CHECK : MPS_OK) : MPS_ERR_CUDA;
+            finish_tickets(q, B.tickets, s, dev);
+            q->stream_busy[B.stream] = 0;
+            release_batch(q, B);
+            q->inflight.erase(q->inflight.begin() + i);
+            progressed = true;
+        }
+        if (progressed) q->cv_done.notify_all();
+        if (q->stop && q->inflight.empty()) break;
+        // 2. admit and launch: one batch per free stream
+        while (!q->stop && !q->paused && !q->pending.empty()) {
+            int sidx = -1;
+            for (size_t s = 0; s < q->streams.size(); s++)
+                if (!q->stream_busy[s]) { sidx = (int)s; break; }
+            if (sidx < 0) break;
+            const mps_request& head = q->tickets[q->pending.front()].req;
+            std::vector<uint64_t> ids;
+            size_t need = 0;
+            const size_t avail = q->cfg.pool_bytes - q->alloc.used();
+            for (auto it = q->pending.begin(); it != q->pending.end() && ids.size() < q->cfg.max_batch; ++it) {
+                const mps_request& r = q->tickets[*it].req;
+                if (r.kt != head.kt || r.has_payload != head.has_payload) break;
+                size_t f = request_footprint(r);
+                if (need + f > avail && !ids.empty()) break;
+                ids.push_back(*it);
+                need += f;
+            }
+            if (ids.empty()) break;
+            Batch B;
+            mps_status s = launch_batch(q, ids, sidx, B);
+            if (s == MPS_ERR_BUDGET) {
+                release_batch(q, B);
+                break;  // wait for memory to free up
+            }
+            const auto now = Clock::now();
+            for (size_t i = 0; i < ids.size(); i++) {
+                q->pending.pop_front();
+                q->tickets[ids[i]].t_admit = now;
+            }
+            if (s != MPS_OK) {
+                release_batch(q, B);
+                finish_tickets(q, ids, s);
+                q->cv_done.notify_all();
+                continue;
+            }
+            q->stream_busy[sidx] = 1;
+            q->inflight.push_back(B);
+        }
+        // 3. wait for work or completions (bounded; completions are polled)
+        if (q->inflight.empty())
+            q->cv.wait_for(lk, std::chrono::milliseconds(50));
+        else {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+            lk.lock();
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+mps_status mps_queue_create(const mps_queue_config* cfg, mps_queue** out) {
+    if (!cfg || !out || !cfg->d_pool || !cfg->pool_bytes) return MPS_ERR_INVALID_ARG;
+    if (cfg->k != 0 && cfg->k != 2 && cfg->k != 4 && cfg->k != 8) return MPS_ERR_UNSUPPORTED;
+    mps_queue* q = new mps_queue();
+    q->cfg = *cfg;
+    if (!q->cfg.max_inflight) q->cfg.max_inflight = 2;
+    if (!q->cfg.max_batch) q->cfg.max_batch = 256;
+    if (!q->cfg.timeout_ms) q->cfg.timeout_ms = 10000;
+    q->alloc = PoolAllocator(cfg->pool_bytes);
+    q->streams.assign(q->cfg.max_inflight, nullptr);
+    q->stream_busy.assign(q->cfg.max_inflight, 0);
+    q->h_off.assign(q->cfg.max_inflight, nullptr);
+    q->h_status.assign(q->cfg.max_inflight, nullptr);
+    for (uint32_t i = 0; i < q->cfg.max_inflight; i++) {
+        if (cudaStreamCreateWithFlags(&q->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMallocHost(&q->h_off[i], ((size_t)q->cfg.max_batch + 1) * 8) != cudaSuccess ||
+            cudaMallocHost(&q->h_status[i], 8) != cudaSuccess) {
+            for (uint32_t j = 0; j <= i; j++) {
+                if (q->streams[j]) cudaStreamDestroy(q->streams[j]);
+                if (q->h_off[j]) cudaFreeHost(q->h_off[j]);
+                if (q->h_status[j]) cudaFreeHost(q->h_status[j]);
+            }
+            delete q;
+            return MPS_ERR_CUDA;
+        }
+    }
+    q->t0 = Clock::now();
+    q->worker = std::thread(worker_main, q);
+    *out = q;
+    return MPS_OK;
+}
+
+mps_status mps_queue_submit(mps_queue* q, const mps_request* req, uint64_t* ticket) {
+    if (!q || !req || !ticket) return MPS_ERR_INVALID_ARG;
+    if (req->kt != MPS_U32 && req->kt != MPS_U64) return MPS_ERR_INVALID_ARG;
+    if (req->n && (!req->d_keys_in || !req->d_keys_out)) return MPS_ERR_INVALID_ARG;
+    if (req->n && req->has_payload && (!req->d_vals_in || !req->d_vals_out)) return MPS_ERR_INVALID_ARG;
+    if (req->n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    if (request_footprint(*req) > q->cfg.pool_bytes) return MPS_ERR_BUDGET;
+    std::lock_guard<std::mutex> lk(q->mu);
+    if (q->stop) return MPS_ERR_CANCELLED;
+    const uint64_t id = q->next_ticket++;
+    Ticket& t = q->tickets[id];
+    t.req = *req;
+    t.res = mps_result{};
+    t.t_submit = Clock::now();
+    q->pending.push_back(id);
+    *ticket = id;
+    q->cv.notify_one();
+    return MPS_OK;
+}
+
+mps_status mps_queue_poll(mps_queue* q, uint64_t ticket, mps_result* res) {
+    if (!q || !res) return MPS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(q->mu);
+    auto it = q->tickets.find(ticket);
+    if (it == q->tickets.end()) return MPS_ERR_INVALID_ARG;
+    if (!it->second.done) return MPS_ERR_NOT_READY;
+    *res = it->second.res;
+    q->tickets.erase(it);
+    return MPS_OK;
+}
+
+mps_status mps_queue_wait(mps_queue* q, uint64_t ticket, uint32_t timeout_ms, mps_result* res) {
+    if (!q || !res) return MPS_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(q->mu);
+    auto it = q->tickets.find(ticket);
+    if (it == q->tickets.end()) return MPS_ERR_INVALID_ARG;
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms);
+    while (!q->tickets[ticket].done) {
+        if (q->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !q->tickets[ticket].done)
+            return MPS_ERR_TIMEOUT;
+    }
+    *res = q->tickets[ticket].res;
+    q->tickets.erase(ticket);
+    return MPS_OK;
+}
+
+mps_status mps_queue_pause(mps_queue* q, int paused) {
+    if (!q) return MPS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(q->mu);
+    q->paused = paused != 0;
+    q->cv.notify_one();
+    return MPS_OK;
+}
+
+mps_status mps_queue_destroy(mps_queue* q) {
+    if (!q) return MPS_OK;
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        q->stop = true;
+        // pending requests are cancelled; batches in flight drain
+        std::vector<uint64_t> cancelled(q->pending.begin(), q->pending.end());
+        q->pending.clear();
+        finish_tickets(q, cancelled, MPS_ERR_CANCELLED);
+        q->cv.notify_one();
+        q->cv_done.notify_all();
+    }
+    if (q->worker.joinable()) q->worker.join();
+    for (size_t i = 0; i < q->streams.size(); i++) {
+        cudaStreamDestroy(q->streams[i]);
+        cudaFreeHost(q->h_off[i]);
+        cudaFreeHost(q->h_status[i]);
+    }
+    delete q;
+    return MPS_OK;
+}
+
+}  // extern "C"

@@ -35,6 +35,22 @@ class Tree(ctypes.Structure):
                 ("counts", ctypes.c_void_p)]
 
 
+class QueueConfig(ctypes.Structure):
+    _fields_ = [("d_pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("timeout_ms", ctypes.c_uint32), ("k", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kt", ctypes.c_int), ("has_payload", ctypes.c_int), ("n", ctypes.c_uint64),
+                ("d_keys_in", ctypes.c_void_p), ("d_vals_in", ctypes.c_void_p), ("d_keys_out", ctypes.c_void_p),
+                ("d_vals_out", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("device_status", ctypes.c_uint32), ("tag", ctypes.c_uint64),
+                ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+
+
 class ProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -51,7 +67,9 @@ class Stats(ctypes.Structure):
 EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_tree", "mps_sort_keys_host",
            "mps_profile_enable", "mps_profile_read", "mps_last_stats", "mps_status_string", "mps_sort_keys_noalloc",
            "mps_batch_workspace_size", "mps_sort_batch", "mps_sort_batch_pairs", "mps_batch_autotune",
-           "mps_batch_graph_create", "mps_batch_graph_launch", "mps_batch_graph_destroy"]
+           "mps_batch_graph_create", "mps_batch_graph_launch", "mps_batch_graph_destroy",
+           "mps_queue_create", "mps_queue_submit", "mps_queue_poll", "mps_queue_wait", "mps_queue_pause",
+           "mps_queue_destroy"]
 
 # Largest n accepted by mps_sort_keys_noalloc (its scratch is compiled into the library).
 NOALLOC_MAX_N = 1 << 20
@@ -90,6 +108,15 @@ def lib():
     L.mps_batch_graph_destroy.argtypes = [P]
     for fn in ("mps_batch_workspace_size", "mps_sort_batch", "mps_sort_batch_pairs", "mps_batch_autotune",
                "mps_batch_graph_create", "mps_batch_graph_launch", "mps_batch_graph_destroy"):
+        getattr(L, fn).restype = I
+    L.mps_queue_create.argtypes = [P, ctypes.POINTER(P)]
+    L.mps_queue_submit.argtypes = [P, P, ctypes.POINTER(U64)]
+    L.mps_queue_poll.argtypes = [P, U64, P]
+    L.mps_queue_wait.argtypes = [P, U64, U32, P]
+    L.mps_queue_pause.argtypes = [P, I]
+    L.mps_queue_destroy.argtypes = [P]
+    for fn in ("mps_queue_create", "mps_queue_submit", "mps_queue_poll", "mps_queue_wait", "mps_queue_pause",
+               "mps_queue_destroy"):
         getattr(L, fn).restype = I
     L.mps_status_string.argtypes = [I]
     L.mps_status_string.restype = ctypes.c_char_p
@@ -300,6 +327,60 @@ class BatchGraph:
         if self.handle:
             lib().mps_batch_graph_destroy(self.handle)
             self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Queue:
+    """Request queue with continuous batching (mps_queue_*).  The pool tensor is
+    the device memory budget; request buffers must stay alive until done."""
+
+    def __init__(self, pool: torch.Tensor, max_inflight: int = 2, max_batch: int = 256, k: int = 4):
+        self.pool = pool
+        cfg = QueueConfig(pool.data_ptr(), pool.numel() * pool.element_size(), max_inflight, max_batch, 0, k)
+        self.handle = ctypes.c_void_p()
+        _check("mps_queue_create", lib().mps_queue_create(ctypes.byref(cfg), ctypes.byref(self.handle)))
+        self.keep = {}
+
+    def submit(self, keys_in, keys_out, vals_in=None, vals_out=None, tag=0) -> int:
+        req = Request(_key_type(keys_in), int(vals_in is not None), keys_in.numel(), keys_in.data_ptr(),
+                      vals_in.data_ptr() if vals_in is not None else None, keys_out.data_ptr(),
+                      vals_out.data_ptr() if vals_out is not None else None, tag)
+        t = ctypes.c_uint64(0)
+        _check("mps_queue_submit", lib().mps_queue_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self.keep[t.value] = (keys_in, keys_out, vals_in, vals_out)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> dict:
+        res = Result()
+        code = lib().mps_queue_wait(self.handle, ticket, timeout_ms, ctypes.byref(res))
+        _check("mps_queue_wait", code)
+        self.keep.pop(ticket, None)
+        return {"status": res.status, "device_status": res.device_status, "tag": res.tag,
+                "t_submit_ms": res.t_submit_ms, "t_admit_ms": res.t_admit_ms, "t_done_ms": res.t_done_ms}
+
+    def poll(self, ticket: int):
+        res = Result()
+        code = lib().mps_queue_poll(self.handle, ticket, ctypes.byref(res))
+        if code == 8:
+            return None
+        _check("mps_queue_poll", code)
+        self.keep.pop(ticket, None)
+        return {"status": res.status, "tag": res.tag, "t_submit_ms": res.t_submit_ms, "t_admit_ms": res.t_admit_ms,
+                "t_done_ms": res.t_done_ms}
+
+    def pause(self, paused: bool = True):
+        _check("mps_queue_pause", lib().mps_queue_pause(self.handle, int(paused)))
+
+    def close(self):
+        if self.handle:
+            lib().mps_queue_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+            self.keep.clear()
 
     def __del__(self):
         try:
