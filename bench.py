@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--k", type=int, default=4)
     ap.add_argument("--no-variants", action="store_true", help="skip the secondary inputs and fan-ins")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-arrays section")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
+    ap.add_argument("--serve-requests", type=int, default=160)
     return ap.parse_args()
 
 
@@ -145,6 +148,191 @@ def cpu_baseline(n_sample, seed):
     return {"value": n_sample / dt / 1e9, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
             "sample": f"one sort of a random permutation of 2^{int(math.log2(n_sample))} uint32 keys, k=4, "
                       f"{dt:.1f} s on one host core (nproc={os.cpu_count()})"}
+
+
+# ------------------------------------------------------------------ sections
+
+def bench_pairs(mps, torch, dev, stream, steps=5):
+    """n = 2^27 uint64 keys from 2^16 distinct values, runs log-uniform in
+    [2, 2^16], uint32 payload = index; stable order checked on samples."""
+    from paper_2209_06909_gb300 import inputs
+    n = 1 << 27
+    a = inputs.random_runs_loguniform(n, 31)
+    v = inputs.payload_index(n)
+    dk, dv = mps.to_device(a, dev), mps.to_device(v, dev)
+    ok, ov = torch.empty_like(dk), torch.empty_like(dv)
+    ws = mps.workspace(n, 8, True, 4, dev)
+    mps.sort_pairs(dk, dv, k=4, out_keys=ok, out_vals=ov, ws=ws, stream=stream)
+    torch.cuda.synchronize()
+    # stability on a sample of positions: keys non-decreasing, equal keys keep index order
+    idx = np.random.default_rng(0).integers(0, n - 1, 1 << 16)
+    k0 = mps.to_numpy(ok, np.uint64)
+    v0 = mps.to_numpy(ov, np.uint32)
+    assert np.all(k0[idx] <= k0[idx + 1])
+    eq = k0[idx] == k0[idx + 1]
+    assert np.all(v0[idx][eq] < v0[idx + 1][eq])
+    assert np.array_equal(a[v0[idx]], k0[idx])
+    for _ in range(2):
+        mps.sort_pairs(dk, dv, k=4, out_keys=ok, out_vals=ov, ws=ws, stream=stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        mps.sort_pairs(dk, dv, k=4, out_keys=ok, out_vals=ov, ws=ws, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    st = mps.last_stats()
+    return {"workload": "n=2^27 uint64 keys (2^16 distinct) + uint32 index payload, runs log-uniform [2,2^16], k=4",
+            "ms": ms, "gkeys_s": n / (ms * 1e-3) / 1e9, "merge_cost_per_n": st["merge_cost"] / n,
+            "stable_sample_checked": int(idx.size)}
+
+
+def bench_batch(mps, torch, dev, stream, steps=5):
+    """4096 uint32 arrays, sizes log-uniform [2^4, 2^20]: one graph-captured
+    batched sort (autotuned k) against one plain mps_sort_keys per array."""
+    from paper_2209_06909_gb300 import inputs
+    stream = torch.cuda.Stream(dev)  # graph capture needs a stream other than the legacy default
+    torch.cuda.synchronize()
+    keys, offsets = inputs.batch_arrays(4096, 77)
+    n, m = keys.size, offsets.size - 1
+    sizes = np.diff(offsets.astype(np.int64))
+    d_in = mps.to_device(keys, dev)
+    d_off = torch.from_numpy(offsets.view(np.int64)).to(dev)
+    out = torch.empty_like(d_in)
+    ws = mps.batch_workspace(n, m, 4, False, 0, dev)
+    best_k = mps.batch_autotune(d_in, d_off, out, ws, max_len=int(sizes.max()), stream=stream)
+    g = mps.BatchGraph(d_in, d_off, out, ws, k=best_k, max_len=int(sizes.max()), stream=stream)
+    g.launch(stream=stream, check=True)
+    got = mps.to_numpy(out, np.uint32)
+    for a in range(0, m, 97):  # sampled arrays against numpy
+        lo, hi = int(offsets[a]), int(offsets[a + 1])
+        assert np.array_equal(got[lo:hi], np.sort(keys[lo:hi]))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        g.launch(stream=stream)
+    torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        g.launch(stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = ev0.elapsed_time(ev1) / steps
+    g.close()
+    # plain form: one mps_sort_keys per array (same k), one shared workspace
+    pws = mps.workspace(int(sizes.max()), 4, False, best_k, dev)
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a in range(m):
+            lo, hi = int(offsets[a]), int(offsets[a + 1])
+            if hi > lo:
+                mps.sort_keys(d_in[lo:hi], k=best_k, out=out[lo:hi], ws=pws, stream=stream)
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t0
+    assert np.array_equal(mps.to_numpy(out, np.uint32)[: int(offsets[64])],
+                          np.concatenate([np.sort(keys[int(offsets[a]):int(offsets[a + 1])]) for a in range(64)]))
+    return {"workload": "4096 uint32 arrays, sizes log-uniform [2^4,2^20] (permutation or sqrt-length runs)",
+            "n_keys": int(n), "k_autotuned": best_k,
+            "batched_graph_ms": batched_ms, "batched_gkeys_s": n / (batched_ms * 1e-3) / 1e9,
+            "plain_per_array_ms": plain_s * 1e3, "plain_gkeys_s": n / plain_s / 1e9,
+            "speedup_vs_plain": plain_s * 1e3 / batched_ms}
+
+
+def bench_serve(mps, torch, dev, stream, nreq=160):
+    """Poisson stream of requests (sizes log-uniform [2^10, 2^24], 50% uint32
+    keys, 50% uint64 keys + uint32 payload, runs as the pairs workload) served
+    by the queue under a 64 GB budget, against a serial plain server (one
+    mps_sort_* per request, in arrival order); arrival-rate sweep."""
+    import threading
+    from paper_2209_06909_gb300 import inputs
+    reqs = inputs.request_stream(nreq, 5, rate_per_s=1.0)
+    tmpl = []
+    for r in reqs[:24]:
+        kk, vv = inputs.request_keys(r)
+        tmpl.append((r["kind"], mps.to_device(kk, dev), mps.to_device(vv, dev) if vv is not None else None))
+    jobs = [tmpl[i % len(tmpl)] for i in range(nreq)]
+    outs = [(torch.empty_like(k), torch.empty_like(v) if v is not None else None) for (_, k, v) in jobs]
+    total_keys = sum(k.numel() for (_, k, _) in jobs)
+    ws_plain = {4: mps.workspace(1 << 24, 4, False, 4, dev), 8: mps.workspace(1 << 24, 8, True, 4, dev)}
+
+    def run_plain_one(j):
+        kind, k, v = jobs[j]
+        ok, ov = outs[j]
+        if kind == "keys":
+            mps.sort_keys(k, k=4, out=ok, ws=ws_plain[4], stream=stream)
+        else:
+            mps.sort_pairs(k, v, k=4, out_keys=ok, out_vals=ov, ws=ws_plain[8], stream=stream)
+
+    # serial service time (back to back) sets the rate scale
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(nreq):
+        run_plain_one(j)
+    torch.cuda.synchronize()
+    serial_s = time.perf_counter() - t0
+    cap = nreq / serial_s  # requests per second the serial server sustains
+    pool = torch.empty(64 << 30, dtype=torch.uint8, device=dev)
+    sweep = []
+    for factor in (0.5, 1.0, 4.0):
+        rate = cap * factor
+        gaps = np.random.default_rng(9).exponential(1.0 / rate, nreq)
+        arrive = np.cumsum(gaps)
+        # serial plain server, arrival order, real time
+        lat = []
+        start = time.perf_counter()
+        for j in range(nreq):
+            now = time.perf_counter() - start
+            if now < arrive[j]:
+                time.sleep(arrive[j] - now)
+            run_plain_one(j)
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - start - arrive[j])
+        plain_span = time.perf_counter() - start
+        # queue with continuous batching
+        q = mps.Queue(pool, max_inflight=3, max_batch=64, k=4)
+        tickets = [None] * nreq
+        start = time.perf_counter()
+
+        def submitter():
+            for j in range(nreq):
+                now = time.perf_counter() - start
+                if now < arrive[j]:
+                    time.sleep(arrive[j] - now)
+                kind, k, v = jobs[j]
+                ok, ov = outs[j]
+                tickets[j] = q.submit(k, ok, v, ov, tag=j)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        res = [q.wait(tickets[j], timeout_ms=120000) for j in range(nreq)]
+        q.close()
+        assert all(r["status"] == 0 for r in res)
+        qlat = [(r["t_done_ms"] - r["t_submit_ms"]) * 1e-3 for r in res]
+        q_span = (max(r["t_done_ms"] for r in res) - min(r["t_submit_ms"] for r in res)) * 1e-3
+        sweep.append({"rate_req_s": rate, "offered_gkeys_s": rate * total_keys / nreq / 1e9,
+                      "queue": {"gkeys_s": total_keys / q_span / 1e9, "p50_ms": float(np.percentile(qlat, 50)) * 1e3,
+                                "p99_ms": float(np.percentile(qlat, 99)) * 1e3},
+                      "serial_plain": {"gkeys_s": total_keys / plain_span / 1e9,
+                                       "p50_ms": float(np.percentile(lat, 50)) * 1e3,
+                                       "p99_ms": float(np.percentile(lat, 99)) * 1e3}})
+    del pool
+    # results of the queue equal the plain results (last sweep point): spot check
+    kind, k, v = jobs[0]
+    ok, _ = outs[0]
+    ref = torch.empty_like(k)
+    if kind == "keys":
+        mps.sort_keys(k, k=4, out=ref, stream=stream)
+    else:
+        mps.sort_pairs(k, v, k=4, out_keys=ref, stream=stream)
+    torch.cuda.synchronize()
+    assert torch.equal(ref, ok)
+    return {"workload": "Poisson requests, sizes log-uniform [2^10,2^24], 50% uint32 keys / 50% uint64+uint32 "
+                        "pairs, 64 GB admission budget, max_inflight 3, max_batch 64",
+            "requests": nreq, "serial_back_to_back_gkeys_s": total_keys / serial_s / 1e9, "sweep": sweep,
+            "throughput_ratio_at_max_rate": sweep[-1]["queue"]["gkeys_s"] / sweep[-1]["serial_plain"]["gkeys_s"]}
 
 
 # ------------------------------------------------------------------ arms
@@ -294,7 +482,7 @@ def run_mps(args):
         assert np.array_equal(h_out.numpy()[:1024].view(np.uint32), np.arange(1024, dtype=np.uint32))
         line["e2e"] = {"value": n / e2e_s / 1e9, "unit": "GKeys/s", "h2d_bytes_per_step": n * 4,
                        "d2h_bytes_per_step": n * 4, "ms_per_step": e2e_s * 1e3}
-        del h_in, h_out, d_tmp
+        del h_in, h_out
 
         if not args.no_variants:
             variants = []
@@ -315,6 +503,18 @@ def run_mps(args):
                                      "sort_frac_of_measured": ba / (vms * 1e-3) / 1e9 / peaks["hbm_gbs"]})
             line["variants"] = variants
             del d_runs
+        del d_tmp
+        for name, fn, flag in (("pairs", lambda: bench_pairs(mps, torch, dev, stream), args.no_variants),
+                               ("batch", lambda: bench_batch(mps, torch, dev, stream), args.no_batch),
+                               ("serve", lambda: bench_serve(mps, torch, dev, stream, args.serve_requests),
+                                args.no_serve)):
+            if flag:
+                continue
+            try:
+                line[name] = fn()
+            except Exception as exc:  # report, keep the headline line
+                line[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(1 << 24, 1234)
         print(json.dumps(line), flush=True)

@@ -11,6 +11,7 @@
 // run are admitted as soon as pool memory and a stream free up, and their
 // work overlaps on the device.  A finished batch releases its pool memory.
 // Every wait is bounded; nothing spins on the device.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -247,9 +248,11 @@ void worker_main(mps_queue* q) {
             std::vector<uint64_t> ids;
             size_t need = 0;
             const size_t avail = q->cfg.pool_bytes - q->alloc.used();
+            // the oldest request's kind; every pending request of that kind joins, in
+            // arrival order, while the batch fits the free budget
             for (auto it = q->pending.begin(); it != q->pending.end() && ids.size() < q->cfg.max_batch; ++it) {
                 const mps_request& r = q->tickets[*it].req;
-                if (r.kt != head.kt || r.has_payload != head.has_payload) break;
+                if (r.kt != head.kt || r.has_payload != head.has_payload) continue;
                 size_t f = request_footprint(r);
                 if (need + f > avail && !ids.empty()) break;
                 ids.push_back(*it);
@@ -263,9 +266,9 @@ void worker_main(mps_queue* q) {
                 break;  // wait for memory to free up
             }
             const auto now = Clock::now();
-            for (size_t i = 0; i < ids.size(); i++) {
-                q->pending.pop_front();
-                q->tickets[ids[i]].t_admit = now;
+            for (uint64_t id : ids) {
+                q->pending.erase(std::find(q->pending.begin(), q->pending.end(), id));
+                q->tickets[id].t_admit = now;
             }
             if (s != MPS_OK) {
                 release_batch(q, B);
