@@ -128,6 +128,7 @@ struct Plan {
         w.vals_tmp = vals ? reinterpret_cast<uint32_t*>(b + o_vtmp) : nullptr;
         w.batch_off = nullptr;
         w.batch_m = 0;
+        w.batch_max_len = 0;
         w.batch_prm = reinterpret_cast<uint2*>(b + o_bprm);
         return w;
     }
@@ -277,7 +278,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     }
     {
         ProfScope ps("node_pass", (double)r * 2.0, st);
-        launch_node_pass(r, k, g.tmax, ws, st);
+        launch_node_pass(r, k, g.tmax, n, ws, st);
     }
     MPS_CUDA(cudaGetLastError());
     MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, sizeof(h_ctr), cudaMemcpyDeviceToHost, st));
@@ -372,6 +373,7 @@ mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
     WsView ws = plan.view(d_ws);
     ws.batch_off = d_off;
     ws.batch_m = m;
+    ws.batch_max_len = max_len;
     const MergeGeom& g = plan.g;
     g_launches = 0;
     const uint32_t r_bound = (uint32_t)std::min<uint64_t>(plan.rmax, n + 1);
@@ -381,7 +383,7 @@ mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
     launch_powers(n, r_bound, k, ws, st);
     launch_mintree(r_bound, ws, st);
     launch_masks(r_bound, false, nullptr, ws, st);
-    launch_node_pass(r_bound, k, g.tmax, ws, st);
+    launch_node_pass(r_bound, k, g.tmax, n, ws, st);
     launch_copy_lone_runs<K, V>(keys_in, vals_in, keys_out, vals_out, r_bound, ws, st);
     launch_bucket(plan.nodes_cap, ws, st);
     launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, plan.fused_cap, g, ws, st);

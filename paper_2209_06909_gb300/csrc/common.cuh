@@ -20,6 +20,7 @@ enum DevError : uint32_t {
     kDevFusedRange = 13, // a fused subtree left the key range
     kDevLoneRange = 14,  // a lone run left the key range
     kDevPackNode = 15,   // packing saw an interval outside its level's nodes
+    kDevMaxLen = 16,     // a batch array was longer than the caller's max_len
 };
 
 __device__ __forceinline__ void dev_fail(uint32_t* status, uint32_t code) { atomicCAS(status, 0u, code); }

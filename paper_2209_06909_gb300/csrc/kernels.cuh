@@ -28,6 +28,8 @@ enum : int {
     kCtrFrontierElems = 200,  // elements inside fused subtrees
     kCtrSplits = 201,   // splitters of the current level
     kCtrIntervals = 202,  // splitter intervals of the current level (packed into units)
+    kCtrMaxRun = 203,   // longest run (elements)
+    kCtrMaxLen = 204,   // longest array of a batch (elements)
     kCtrWords = 256
 };
 
@@ -80,6 +82,7 @@ struct WsView {
     // batch of arrays laid end to end (nullptr for a single array)
     const uint64_t* batch_off;     // [m+1] array starts, batch_off[m] = n
     uint32_t batch_m;
+    uint64_t batch_max_len;        // caller's bound on the longest array (0: none)
     uint2* batch_prm;              // [2m] per-array power parameters
 };
 
@@ -107,7 +110,7 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
 // tree.cu
 void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st);
 void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView& ws, cudaStream_t st);
-void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st);
+void launch_node_pass(uint32_t r, int k, uint32_t tmax, uint64_t n, const WsView& ws, cudaStream_t st);
 void launch_bucket(uint32_t total_bound, const WsView& ws, cudaStream_t st);
 void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first, void* nodes,
                       uint64_t* counts_out, cudaStream_t st);

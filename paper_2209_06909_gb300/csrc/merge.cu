@@ -46,9 +46,6 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 constexpr int kFusedThreads = 256;
-// outputs per thread in a merge pass; odd, so that the lanes of a warp touch
-// 32 different shared-memory banks when they walk their outputs in step
-constexpr int kIPT = 15;
 constexpr uint32_t kNoMid = 0xFFFFu;
 // boundary-list entries one thread holds while compacting: ceil((C/2 + 8) / 256), odd
 constexpr int kKeepMax = 25;
@@ -88,6 +85,14 @@ __device__ __forceinline__ void serial_merge(const K* __restrict__ src, K* __res
     }
 }
 
+// Outputs per thread when NT threads share a merge pass of `total` outputs:
+// one chunk each, rounded up to an odd count so that the lanes of a warp,
+// walking their outputs in step, touch 32 different shared-memory banks.
+template <int NT>
+__device__ __forceinline__ uint32_t chunk_per_thread(uint32_t total) {
+    return ((total + NT - 1) / NT) | 1u;
+}
+
 // One pass of stable 2-way merges over [0, len): segment i covers
 // [seg_start[i], seg_start[i+1]) and merges its halves at seg_mid[i], or is
 // copied when seg_mid[i] == kNoMid.
@@ -95,9 +100,12 @@ template <typename K, bool V>
 __device__ __forceinline__ void merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
                                            uint32_t* __restrict__ vdst, uint32_t len, const uint16_t* __restrict__ seg_start,
                                            const uint16_t* __restrict__ seg_mid, uint32_t ns) {
-    for (uint32_t base = threadIdx.x * kIPT; base < len; base += kFusedThreads * kIPT) {
+    const uint32_t ipt = chunk_per_thread<kFusedThreads>(len);
+    {
+        const uint32_t base = threadIdx.x * ipt;
+        if (base >= len) return;
         uint32_t o = base;
-        const uint32_t oe = min(base + (uint32_t)kIPT, len);
+        const uint32_t oe = min(base + ipt, len);
         uint32_t lo = 0, hi = ns;
         while (hi - lo > 1) {
             const uint32_t m = (lo + hi) >> 1;
@@ -661,7 +669,6 @@ __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict_
 }
 
 constexpr int kLvlThreads = 256;
-constexpr int kLvlIPT = 15;  // odd: conflict-free strides
 
 template <typename K, bool V>
 __device__ __forceinline__ void issue_unit_copies(const UnitDesc& D, K* dst, uint32_t* vdst, const K* __restrict__ leaf,
@@ -689,9 +696,12 @@ __device__ __forceinline__ void unit_round(const K* __restrict__ src, K* __restr
                                            uint32_t t) {
     const uint32_t step = 1u << (t + 1), half = 1u << t;
     const uint32_t total = off[d];
-    for (uint32_t base = threadIdx.x * kLvlIPT; base < total; base += kLvlThreads * kLvlIPT) {
+    const uint32_t ipt = chunk_per_thread<kLvlThreads>(total);
+    {
+        const uint32_t base = threadIdx.x * ipt;
+        if (base >= total) return;
         uint32_t o = base;
-        const uint32_t oe = min(base + (uint32_t)kLvlIPT, total);
+        const uint32_t oe = min(base + ipt, total);
         uint32_t c0 = 0;
         for (uint32_t c = step; c < d; c += step)
             if (off[c] <= o) c0 = c;

@@ -193,11 +193,14 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
                                                 const uint2* __restrict__ arr_param,
                                                 uint8_t* __restrict__ powers, unsigned long long* __restrict__ level_bits) {
     __shared__ unsigned long long red[256 / 32 + 1];
+    __shared__ uint32_t redm[256 / 32 + 1];
     const uint32_t r = (uint32_t)counters[kCtrR];
     unsigned long long bits = 0;
+    uint32_t longest = 0;  // longest run seen by this thread
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= r; i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t si = run_starts[i];
         uint32_t sp = i >= 1 ? run_starts[i - 1] : 0u;
+        longest = max(longest, si - sp);
         // the array holding run i (a batch sorts each array on its own)
         uint64_t base = 0, nn = n;
         uint32_t ww = w;
@@ -241,15 +244,22 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
         }
     }
     bits = block_reduce<256>(bits, OpOrU64(), 0ull, red);
+    longest = block_reduce<256>(longest, OpMax32(), 0u, redm);
     if (threadIdx.x == 0 && bits) atomicOr(level_bits, bits);
+    if (threadIdx.x == 0 && longest)
+        atomicMax(reinterpret_cast<unsigned long long*>(const_cast<uint64_t*>(counters) + kCtrMaxRun), (unsigned long long)longest);
 }
 
 // Per-array power parameters of a batch: w = ceil(log2 n_a) and the 64-bit
 // reciprocal floor((2^64 - 1) / (2 n_a)), stored as prm[a] = (w, magic_hi),
-// prm[m + a].x = magic_lo.
-__global__ void k_array_params(const uint64_t* __restrict__ off, uint32_t m, uint2* __restrict__ prm) {
+// prm[m + a].x = magic_lo.  Also the longest array, checked against the
+// caller's bound max_len (0: no bound given).
+__global__ void k_array_params(const uint64_t* __restrict__ off, uint32_t m, uint64_t max_len, uint2* __restrict__ prm,
+                               uint64_t* __restrict__ counters) {
     for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x) {
         const uint64_t na = off[a + 1] - off[a];
+        if (max_len && na > max_len) dev_fail(reinterpret_cast<uint32_t*>(counters + kCtrStatus), kDevMaxLen);
+        atomicMax(reinterpret_cast<unsigned long long*>(counters + kCtrMaxLen), (unsigned long long)na);
         uint32_t w = 0;
         while ((1ull << w) < na) w++;
         const uint64_t mg = na ? ~0ull / (2 * na) : 0ull;
@@ -283,7 +293,8 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
     uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r + 1, threads), 152 * 16);
     if (ws.batch_off) {
         k_array_params<<<(uint32_t)std::min<uint64_t>(ceil_div(ws.batch_m, 256), 1024), 256, 0, st>>>(ws.batch_off, ws.batch_m,
-                                                                                                  ws.batch_prm);
+                                                                                                  ws.batch_max_len, ws.batch_prm,
+                                                                                                  ws.counters);
         g_launches += 1;
     }
     k_powers<<<blocks, threads, 0, st>>>(ws.run_starts, ws.counters, n, w, magic, log2k, ws.batch_off, ws.batch_m,

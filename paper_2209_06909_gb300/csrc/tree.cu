@@ -201,7 +201,11 @@ __global__ void __launch_bounds__(1024) k_mask_scan(const unsigned long long* __
     }
 }
 
-__global__ void __launch_bounds__(kMaskThreads) k_mask_apply(const uint8_t* __restrict__ powers, const uint64_t* __restrict__ ctr,
+// Writes node_info (depth | start << 7) for every boundary, optionally the leaf
+// depths, and adds to the counters the merge cost M = sum_i depth(run i) L_i
+// (Sec. 2.2) and the number of nodes.
+__global__ void __launch_bounds__(kMaskThreads) k_mask_apply(const uint8_t* __restrict__ powers, uint64_t* __restrict__ ctr,
+                                                             const uint32_t* __restrict__ rs,
                                                              const unsigned long long* __restrict__ fpre,
                                                              const unsigned long long* __restrict__ gsuf,
                                                              uint8_t* __restrict__ node_info, uint8_t* __restrict__ leaf_depth) {
@@ -229,6 +233,8 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask_apply(const uint8_t* __re
         gex[q] = sg;
         sg = OpG()(e[q], sg);
     }
+    unsigned long long cost = 0, nodes = 0;
+    uint32_t rs_next = b0 < nb ? rs[b0 + 1] : 0u;
 #pragma unroll
     for (int q = 0; q < kMaskItems; q++) {
         uint32_t b = b0 + q;
@@ -240,13 +246,26 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask_apply(const uint8_t* __re
             // power 0 marks an array start inside a batch: never a node boundary
             uint32_t start = (p == 0 || ((left >> p) & 1ull)) ? 0u : 1u;
             node_info[j] = (uint8_t)(depth | (start << 7));
-            if (leaf_depth) {
-                uint64_t incl = OpF()(pf, e[q]) & kBits & ~1ull;
-                leaf_depth[j] = (uint8_t)__popcll(incl | right);
-                if (j == 1) leaf_depth[0] = (uint8_t)__popcll(OpG()(e[q], gex[q]) & kBits & ~1ull);
+            nodes += start;
+            uint64_t incl = OpF()(pf, e[q]) & kBits & ~1ull;
+            const uint32_t dj = (uint32_t)__popcll(incl | right);  // depth of run j
+            const uint32_t rs_j = rs_next;
+            rs_next = rs[j + 1];
+            cost += (unsigned long long)dj * (rs_next - rs_j);
+            if (j == 1) {
+                const uint32_t d0 = (uint32_t)__popcll(OpG()(e[q], gex[q]) & kBits & ~1ull);  // depth of run 0
+                cost += (unsigned long long)d0 * (rs_j - rs[0]);
+                if (leaf_depth) leaf_depth[0] = (uint8_t)d0;
             }
+            if (leaf_depth) leaf_depth[j] = (uint8_t)dj;
         }
         pf = OpF()(pf, e[q]);
+    }
+    cost = block_reduce<kMaskThreads>(cost, OpAddU64(), 0ull, tmp);
+    nodes = block_reduce<kMaskThreads>(nodes, OpAddU64(), 0ull, tmp);
+    if (threadIdx.x == 0) {
+        if (cost) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrM), cost);
+        if (nodes) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrNodes), nodes);
     }
 }
 
@@ -277,32 +296,44 @@ __device__ __forceinline__ bool node_shape(const MinTree& T, const uint8_t* P, u
     return ok;
 }
 
-// One pass over the boundaries (grid-stride).  For every node start j: its
-// delimiters L, R (nearest smaller powers) and size.  Nodes larger than T_max
-// become level-merge records; such a node also appends each child that is an
-// inner node of at most T_max elements to the list of fused subtrees (its
-// parent is large, so it is maximal).  A small root is a fused subtree too.
-__global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tmax,
+// One pass over the boundaries (grid-stride) that finds the nodes larger than
+// T_max.  Such a node becomes a level-merge record and appends each child that
+// is an inner node of at most T_max elements to the list of fused subtrees (its
+// parent is large, so it is maximal); a small root is a fused subtree too.
+//
+// Most nodes are skipped without a nearest-smaller query.  Every interior
+// boundary of a node of power v has power >= v, i.e. P2 > (v-1) log2 k (Def. 3.1
+// with P_k = ceil(P2 / log2 k)), so consecutive runs of the node have run
+// midpoints that agree in their first (v-1) log2 k bits of a/n; all its run
+// midpoints lie in one interval of n / k^(v-1) elements, and its size is less
+// than that plus half of each end run: below n / k^(v-1) + (longest run).  An
+// inner node (depth > 0) whose bound is at most T_max is never large and never
+// a fused root.  (Batches use the longest array for n.)
+__global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tmax, uint64_t n_single,
                                                    const uint32_t* __restrict__ rs, const uint8_t* __restrict__ node_info,
                                                    uint64_t* __restrict__ ctr, LevelNode* __restrict__ nodes_raw, uint32_t nodes_cap,
                                                    uint4* __restrict__ fused_list, uint32_t fused_cap) {
-    __shared__ unsigned long long red[256 / 32 + 1];
     const uint8_t* P = T.lv[0];
     uint32_t* status = reinterpret_cast<uint32_t*>(ctr + kCtrStatus);
-    unsigned long long msize = 0, nstarts = 0;
     const uint32_t r = (uint32_t)ctr[kCtrR];
+    const uint64_t nmax = n_single ? n_single : ctr[kCtrMaxLen];
+    const uint64_t longest = ctr[kCtrMaxRun];
+    const uint32_t log2k = k == 2 ? 1u : (k == 4 ? 2u : 3u);
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x + 1; j < r; j += gridDim.x * blockDim.x) {
         uint8_t info = node_info[j];
         if (!(info & 0x80)) continue;
         const uint32_t v = P[j];
         if (v == 0) continue;
-        nstarts++;
+        const uint32_t depth = info & 0x7F;
+        if (depth != 0) {
+            const uint32_t sh = (v - 1) * log2k;
+            const uint64_t span = sh >= 63 ? 1ull : ((nmax + (1ull << sh) - 1) >> sh);
+            if (span + longest <= tmax) continue;
+        }
         const uint32_t L = nsv_left(T, j, v, true);
         const uint32_t R = nsv_right(T, j, v, true);
         const uint32_t sL = rs[L], sR = rs[R];
         const uint32_t size = sR - sL;
-        msize += size;
-        const uint32_t depth = info & 0x7F;
         if (size > tmax) {
             NodeShape s;
             if (!node_shape(T, P, j, v, k, s)) dev_fail(status, kDevDegree);
@@ -339,12 +370,6 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tm
             else dev_fail(status, kDevCapacity);
             atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), (unsigned long long)size);
         }
-    }
-    msize = block_reduce<256>(msize, OpAddU64(), 0ull, red);
-    nstarts = block_reduce<256>(nstarts, OpAddU64(), 0ull, red);
-    if (threadIdx.x == 0) {
-        if (msize) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrM), msize);
-        if (nstarts) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrNodes), nstarts);
     }
 }
 
@@ -498,15 +523,15 @@ void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView&
     uint32_t tiles = (uint32_t)ceil_div(nb, kMaskTile);
     k_mask_reduce<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.mt_f, ws.mt_g);
     k_mask_scan<<<1, 1024, 0, st>>>(ws.mt_f, ws.mt_g, tiles, ws.mt_fpre, ws.mt_gsuf);
-    k_mask_apply<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.mt_fpre, ws.mt_gsuf, ws.node_info,
+    k_mask_apply<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.run_starts, ws.mt_fpre, ws.mt_gsuf, ws.node_info,
                                                   dump_leaf ? leaf_depth : nullptr);
     g_launches += 3;
 }
 
-void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st) {
+void launch_node_pass(uint32_t r, int k, uint32_t tmax, uint64_t n, const WsView& ws, cudaStream_t st) {
     uint32_t nb = r - 1;
     uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(nb, 256), 152 * 16);
-    k_node_pass<<<blocks, 256, 0, st>>>(make_mintree(ws), k, tmax, ws.run_starts, ws.node_info,
+    k_node_pass<<<blocks, 256, 0, st>>>(make_mintree(ws), k, tmax, ws.batch_off ? 0ull : n, ws.run_starts, ws.node_info,
                                                               ws.counters, ws.nodes_raw, ws.nodes_cap, ws.fused_list, ws.fused_cap);
     g_launches += 1;
 }
