@@ -268,7 +268,10 @@ typedef struct {
     uint32_t num_levels, hbm_levels;
     uint64_t bytes_fused, bytes_levels; /* algorithmic bytes of the merge kernels */
     uint64_t launches;                  /* CUDA kernels launched by the call */
-    uint32_t device_status;             /* device-side check code (0 = none) */
+    uint32_t device_status;             /* device-side check code (0 = none): 1 node degree > k,
+                                           2 capacity, 3 tile overflow, 11-15 work-unit / fused /
+                                           lone-run ranges, 16 array longer than max_len, 17 a
+                                           bounded wait ran out (returned as MPS_ERR_TIMEOUT) */
     uint32_t pad;
 } mps_stats;
 

@@ -32,6 +32,10 @@ constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// A device status word as a return code: a bounded wait that ran out is a
+// timeout, anything else a failed invariant check.
+inline mps_status device_error(uint32_t code) { return code == kDevSpin ? MPS_ERR_TIMEOUT : MPS_ERR_DEVICE_CHECK; }
+
 // Byte layout of the workspace for one (n, key bytes, payload, k).
 struct Plan {
     uint64_t n = 0;
@@ -44,7 +48,7 @@ struct Plan {
     uint64_t lv_cap[kMinTreeLevels] = {};
     int nlv_max = 0;
     // offsets
-    size_t o_ctr, o_lvloff, o_det_sum, o_det_pref, o_rs, o_rdesc, o_fused, o_canon, o_lv[kMinTreeLevels], o_info,
+    size_t o_ctr, o_lvloff, o_det_state, o_rs, o_rdesc, o_fused, o_canon, o_lv[kMinTreeLevels], o_info,
         o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_ufirst, o_ptiles, o_hist, o_ktmp, o_vtmp, total;
 
     uint32_t m = 0;  // arrays of a batch (0: a single array)
@@ -70,14 +74,13 @@ struct Plan {
         auto take = [&](size_t bytes) { size_t at = o; o += align_up(bytes); return at; };
         o_ctr = take(kCtrWords * 8);
         o_lvloff = take(kMaxLevels * 4);
-        o_det_sum = take(det_tiles * 16);
-        o_det_pref = take(det_tiles * 8);
-        o_rs = take((rmax + 2) * 4);
+        o_det_state = take(det_tiles * 8);
+        o_rs = take((rmax + 2 + 32) * 4);  // padded for 16-byte loads past r
         o_rdesc = take(rmax + 1);
         o_fused = take((size_t)fused_cap * 16);
         o_canon = take((rmax + 1) * 4);
         for (int t = 0; t < kMinTreeLevels; t++) o_lv[t] = t < nlv_max ? take(lv_cap[t]) : 0;
-        o_info = take(rmax + 1);
+        o_info = take(rmax + 1 + 16);
         o_mt = take(mask_tiles * 8 * 4);
         o_nodes_raw = take((size_t)nodes_cap * sizeof(LevelNode));
         o_nodes_lvl = take((size_t)nodes_cap * sizeof(LevelNode));
@@ -98,8 +101,7 @@ struct Plan {
         WsView w{};
         w.n = n;
         w.counters = reinterpret_cast<uint64_t*>(b + o_ctr);
-        w.det_sum = reinterpret_cast<uint4*>(b + o_det_sum);
-        w.det_pref = reinterpret_cast<uint2*>(b + o_det_pref);
+        w.det_state = reinterpret_cast<uint64_t*>(b + o_det_state);
         w.run_starts = reinterpret_cast<uint32_t*>(b + o_rs);
         w.run_desc = reinterpret_cast<uint8_t*>(b + o_rdesc);
         w.fused_list = reinterpret_cast<uint4*>(b + o_fused);
@@ -239,8 +241,12 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
         launch_detect<K>(keys_in, n, ws, st);
     }
     MPS_CUDA(cudaGetLastError());
-    MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, 8, cudaMemcpyDeviceToHost, st));
+    MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, (kCtrStatus + 1) * 8, cudaMemcpyDeviceToHost, st));
     MPS_CUDA(cudaStreamSynchronize(st));
+    if ((uint32_t)h_ctr[kCtrStatus]) {
+        g_last.device_status = (uint32_t)h_ctr[kCtrStatus];
+        return device_error((uint32_t)h_ctr[kCtrStatus]);
+    }
     const uint32_t r = (uint32_t)h_ctr[kCtrR];
     g_last.r = r;
 
@@ -274,17 +280,17 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     {
         ProfScope ps("tree_scans", (double)r * 4.0, st);
         launch_mintree(r, ws, st);
-        launch_masks(r, tree && tree->leaf_depth, tree ? tree->leaf_depth : nullptr, ws, st);
+        launch_masks(r, tree && tree->leaf_depth, tree ? tree->leaf_depth : nullptr, n, k, g.tmax, ws, st);
     }
     {
         ProfScope ps("node_pass", (double)r * 2.0, st);
-        launch_node_pass(r, k, g.tmax, n, ws, st);
+        launch_node_pass(r, k, g.tmax, ws, st);
     }
     MPS_CUDA(cudaGetLastError());
     MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, sizeof(h_ctr), cudaMemcpyDeviceToHost, st));
     MPS_CUDA(cudaStreamSynchronize(st));
     g_last.device_status = (uint32_t)h_ctr[kCtrStatus];
-    if ((uint32_t)h_ctr[kCtrStatus]) return MPS_ERR_DEVICE_CHECK;
+    if ((uint32_t)h_ctr[kCtrStatus]) return device_error((uint32_t)h_ctr[kCtrStatus]);
     const uint64_t hbm_total = h_ctr[kCtrHbmTotal];
     if (hbm_total > plan.nodes_cap || h_ctr[kCtrFrontier] > plan.fused_cap) return MPS_ERR_DEVICE_CHECK;
     g_last.merge_cost = h_ctr[kCtrM];
@@ -336,7 +342,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     MPS_CUDA(cudaMemcpyAsync(&status, ws.counters + kCtrStatus, 4, cudaMemcpyDeviceToHost, st));
     MPS_CUDA(cudaStreamSynchronize(st));
     g_last.device_status = status;
-    if (status) return MPS_ERR_DEVICE_CHECK;
+    if (status) return device_error(status);
     g_last.bytes_fused = (uint64_t)(2 * b * (double)h_ctr[kCtrFrontierElems]);
     g_last.launches = g_launches;
     return MPS_OK;
@@ -382,8 +388,8 @@ mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
     launch_detect<K>(keys_in, n, ws, st);
     launch_powers(n, r_bound, k, ws, st);
     launch_mintree(r_bound, ws, st);
-    launch_masks(r_bound, false, nullptr, ws, st);
-    launch_node_pass(r_bound, k, g.tmax, n, ws, st);
+    launch_masks(r_bound, false, nullptr, n, k, g.tmax, ws, st);
+    launch_node_pass(r_bound, k, g.tmax, ws, st);
     launch_copy_lone_runs<K, V>(keys_in, vals_in, keys_out, vals_out, r_bound, ws, st);
     launch_bucket(plan.nodes_cap, ws, st);
     launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, plan.fused_cap, g, ws, st);
@@ -400,7 +406,7 @@ mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
         g_last = mps_stats{};
         g_last.n = n;
         g_last.device_status = (uint32_t)h_ctr[kCtrStatus];
-        if ((uint32_t)h_ctr[kCtrStatus]) return MPS_ERR_DEVICE_CHECK;
+        if ((uint32_t)h_ctr[kCtrStatus]) return device_error((uint32_t)h_ctr[kCtrStatus]);
         g_last.r = h_ctr[kCtrR];
         g_last.merge_cost = h_ctr[kCtrM];
         g_last.frontier_nodes = h_ctr[kCtrFrontier];
@@ -636,7 +642,7 @@ mps_status mps_batch_graph_launch(mps_batch_graph* g, cudaStream_t stream, int c
         if (cudaMemcpyAsync(&status, g->counters + kCtrStatus, 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
             return MPS_ERR_CUDA;
         if (cudaStreamSynchronize(stream) != cudaSuccess) return MPS_ERR_CUDA;
-        if (status) return MPS_ERR_DEVICE_CHECK;
+        if (status) return device_error(status);
     }
     return MPS_OK;
 }

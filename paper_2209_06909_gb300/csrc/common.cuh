@@ -21,6 +21,7 @@ enum DevError : uint32_t {
     kDevLoneRange = 14,  // a lone run left the key range
     kDevPackNode = 15,   // packing saw an interval outside its level's nodes
     kDevMaxLen = 16,     // a batch array was longer than the caller's max_len
+    kDevSpin = 17,       // a bounded wait on another block ran out
 };
 
 __device__ __forceinline__ void dev_fail(uint32_t* status, uint32_t code) { atomicCAS(status, 0u, code); }

@@ -30,6 +30,7 @@ enum : int {
     kCtrIntervals = 202,  // splitter intervals of the current level (packed into units)
     kCtrMaxRun = 203,   // longest run (elements)
     kCtrMaxLen = 204,   // longest array of a batch (elements)
+    kCtrDetTile = 205,  // next run-detection tile to take
     kCtrWords = 256
 };
 
@@ -50,15 +51,14 @@ static_assert(sizeof(LevelNode) == 64, "LevelNode layout");
 struct WsView {
     uint64_t n;                    // keys being sorted (all arrays of a batch)
     uint64_t* counters;
-    uint4* det_sum;
-    uint2* det_pref;
+    uint64_t* det_state;           // [tiles] run-detection tile words (look-back)
     uint32_t* run_starts;
     uint8_t* run_desc;
     uint8_t* lv[kMinTreeLevels];   // lv[0] = powers[0..r] (+ padding)
     uint32_t lv_len[kMinTreeLevels];
     int nlv;
     uint8_t* powers;               // == lv[0]
-    uint8_t* node_info;            // per boundary: depth | (is_start << 7)
+    uint8_t* node_info;            // [b] for boundary j = b + 1: depth | needs_query << 6 | is_start << 7
     unsigned long long* mt_f;      // mask-scan tile aggregates
     unsigned long long* mt_g;
     unsigned long long* mt_fpre;
@@ -109,8 +109,9 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
 
 // tree.cu
 void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st);
-void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView& ws, cudaStream_t st);
-void launch_node_pass(uint32_t r, int k, uint32_t tmax, uint64_t n, const WsView& ws, cudaStream_t st);
+void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, uint64_t n, int k, uint32_t tmax, const WsView& ws,
+                  cudaStream_t st);
+void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st);
 void launch_bucket(uint32_t total_bound, const WsView& ws, cudaStream_t st);
 void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first, void* nodes,
                       uint64_t* counts_out, cudaStream_t st);

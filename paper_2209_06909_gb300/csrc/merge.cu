@@ -93,39 +93,78 @@ __device__ __forceinline__ uint32_t chunk_per_thread(uint32_t total) {
     return ((total + NT - 1) / NT) | 1u;
 }
 
-// One pass of stable 2-way merges over [0, len): segment i covers
-// [seg_start[i], seg_start[i+1]) and merges its halves at seg_mid[i], or is
-// copied when seg_mid[i] == kNoMid.
+// Entry of the shared-memory boundary list: bits 0..15 element offset,
+// 16..23 power, 24..31 the tournament round in which its two sides meet.
+__device__ __forceinline__ uint32_t be_off(uint32_t e) { return e & 0xFFFFu; }
+__device__ __forceinline__ uint32_t be_pow(uint32_t e) { return (e >> 16) & 0xFFu; }
+__device__ __forceinline__ uint32_t be_rnd(uint32_t e) { return e >> 24; }
+
+// Round t of the current level over [0, len), read straight from the sorted
+// boundary list bl[0..na): entries with round < t lie inside runs merged by
+// earlier rounds, an entry with round t is the midpoint of a merge, and an
+// entry with a later round delimits segments.  Between two delimiters there
+// is at most one midpoint (the tournament brackets of a node), so the segment
+// holding output o is found by a binary search for o and a walk over at most
+// 2^t - 1 skipped entries on either side; a segment without a midpoint is
+// copied.
+// Index of the first boundary-list entry with an offset above this thread's
+// first output of a merge round (the same for every round of a level).
+__device__ __forceinline__ int round_entry(uint32_t len, const uint32_t* __restrict__ bl, int na) {
+    const uint32_t o = threadIdx.x * chunk_per_thread<kFusedThreads>(len);
+    int lo = 0, hi = na;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (be_off(bl[mid]) <= o) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 template <typename K, bool V>
-__device__ __forceinline__ void merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
-                                           uint32_t* __restrict__ vdst, uint32_t len, const uint16_t* __restrict__ seg_start,
-                                           const uint16_t* __restrict__ seg_mid, uint32_t ns) {
+__device__ __forceinline__ void merge_round(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
+                                            uint32_t* __restrict__ vdst, uint32_t len, const uint32_t* __restrict__ bl,
+                                            int na, int first, uint32_t t) {
     const uint32_t ipt = chunk_per_thread<kFusedThreads>(len);
-    {
-        const uint32_t base = threadIdx.x * ipt;
-        if (base >= len) return;
-        uint32_t o = base;
-        const uint32_t oe = min(base + ipt, len);
-        uint32_t lo = 0, hi = ns;
-        while (hi - lo > 1) {
-            const uint32_t m = (lo + hi) >> 1;
-            if (seg_start[m] <= o) lo = m; else hi = m;
-        }
-        uint32_t i = lo;
-        while (o < oe) {
-            const uint32_t s = seg_start[i], e = seg_start[i + 1], m = seg_mid[i];
-            const uint32_t stop = min(e, oe);
-            if (m == kNoMid) {
-                for (; o < stop; o++) {
-                    dst[o] = src[o];
-                    if (V) vdst[o] = vsrc[o];
-                }
+    const uint32_t base = threadIdx.x * ipt;
+    if (base >= len) return;
+    uint32_t o = base;
+    const uint32_t oe = min(base + ipt, len);
+    int j = first - 1;  // nearest entry at or left of o that this round sees (-1: the start)
+    while (j >= 0 && be_rnd(bl[j]) < t) j--;
+    while (o < oe) {
+        int nx = j + 1;
+        while (nx < na && be_rnd(bl[nx]) < t) nx++;
+        uint32_t s, m = kNoMid, e;
+        if (j >= 0 && be_rnd(bl[j]) == t) {
+            // o lies in the right half of a merge whose left delimiter precedes j
+            m = be_off(bl[j]);
+            int jl = j - 1;
+            while (jl >= 0 && be_rnd(bl[jl]) < t) jl--;
+            s = jl >= 0 ? be_off(bl[jl]) : 0u;
+            e = nx < na ? be_off(bl[nx]) : len;
+            j = nx;
+        } else {
+            s = j >= 0 ? be_off(bl[j]) : 0u;
+            if (nx < na && be_rnd(bl[nx]) == t) {
+                m = be_off(bl[nx]);
+                int n2 = nx + 1;
+                while (n2 < na && be_rnd(bl[n2]) < t) n2++;
+                e = n2 < na ? be_off(bl[n2]) : len;
+                j = n2;
             } else {
-                const uint32_t l = merge_path(src, s, m, e, o - s);
-                serial_merge<K, V>(src, dst, vsrc, vdst, s + l, m, m + (o - s) - l, e, o, stop);
-                o = stop;
+                e = nx < na ? be_off(bl[nx]) : len;
+                j = nx;
             }
-            i++;
+        }
+        const uint32_t stop = min(e, oe);
+        if (m == kNoMid || m >= e || m <= s) {
+            for (; o < stop; o++) {
+                dst[o] = src[o];
+                if (V) vdst[o] = vsrc[o];
+            }
+        } else {
+            const uint32_t l = merge_path(src, s, m, e, o - s);
+            serial_merge<K, V>(src, dst, vsrc, vdst, s + l, m, m + (o - s) - l, e, o, stop);
+            o = stop;
         }
     }
 }
@@ -137,21 +176,15 @@ __device__ __forceinline__ uint32_t odd_chunk(uint32_t m) {
     return per | 1u;
 }
 
-// Entry of the shared-memory boundary list: bits 0..15 element offset,
-// 16..23 power, 24..31 index q within its group of equal powers.
-__device__ __forceinline__ uint32_t be_off(uint32_t e) { return e & 0xFFFFu; }
-__device__ __forceinline__ uint32_t be_pow(uint32_t e) { return (e >> 16) & 0xFFu; }
-__device__ __forceinline__ uint32_t be_q(uint32_t e) { return e >> 24; }
-
-// Segmented count: bit 31 = group reset, low bits = equal-power boundaries seen.
-struct OpSegCount {
+// Scan element of a level: bit 31 = a smaller power was seen (the group of
+// equal powers restarts), bits 16..30 = power-p boundaries in the current
+// group (so far), bits 0..15 = smaller-power boundaries (kept for later levels).
+struct OpLevel {
     __device__ uint32_t operator()(uint32_t X, uint32_t Y) const {
-        return (Y & 0x80000000u) ? Y : ((X & 0x80000000u) | ((X & 0x7FFFFFFFu) + Y));
+        const uint32_t kept = (X + Y) & 0xFFFFu;
+        return (Y & 0x80000000u) ? ((Y & 0xFFFF0000u) | kept)
+                                 : (((X & 0xFFFF0000u) + (Y & 0x7FFF0000u)) | kept);
     }
-};
-// (segmented count, plain count)
-struct OpQ {
-    __device__ uint4 operator()(uint4 X, uint4 Y) const { return make_uint4(OpSegCount()(X.x, Y.x), X.y + Y.y, 0u, 0u); }
 };
 struct OpMax2 {
     __device__ uint4 operator()(uint4 X, uint4 Y) const { return make_uint4(max(X.x, Y.x), max(X.y, Y.y), 0u, 0u); }
@@ -281,84 +314,62 @@ __global__ void __launch_bounds__(kFusedThreads)
         uint32_t* vcur = vB;
         uint32_t* voth = vA;
         uint32_t na = nb;
-        uint16_t* seg_start = reinterpret_cast<uint16_t*>(bl1);
-        uint16_t* seg_mid = seg_start + BMAX + 2;
+        uint32_t T = 0;  // tournament rounds per node: log2 k
+        while ((1u << T) < (uint32_t)k) T++;
+        __shared__ uint32_t s_rmask;
 
         for (uint32_t p = pmax; p >= pmin && p >= 1; p--) {
             per = odd_chunk(na);
             e0 = min(na, tid * per);
             e1 = min(na, e0 + per);
-            // group index q of every power-p boundary (segmented count), and their number
-            uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+            // group index q of every power-p boundary (segmented count) and the
+            // positions of the smaller powers that stay for later levels
+            uint32_t acc = 0;
             for (uint32_t e = e0; e < e1; e++) {
                 const uint32_t pw = be_pow(bl0[e]);
-                acc = OpQ()(acc, make_uint4(pw < p ? 0x80000000u : (pw == p ? 1u : 0u), pw == p ? 1u : 0u, 0u, 0u));
+                acc = OpLevel()(acc, pw < p ? 0x80000001u : (pw == p ? 0x00010000u : 0u));
             }
-            uint4 tot;
-            const uint4 pre = block_scan_excl<kFusedThreads, false>(acc, OpQ(), make_uint4(0u, 0u, 0u, 0u), stmp4, &tot);
-            if (tot.y == 0) continue;
-            {
-                uint32_t run = pre.x;
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t v = bl0[e];
-                    const uint32_t pw = be_pow(v);
-                    run = OpSegCount()(run, pw < p ? 0x80000000u : (pw == p ? 1u : 0u));
-                    if (pw == p) bl0[e] = (v & 0x00FFFFFFu) | ((run & 0x7FFFFFFFu) << 24);
+            if (tid == 0) s_rmask = 0;
+            uint32_t tot;
+            const uint32_t pre = block_scan_excl<kFusedThreads, false>(acc, OpLevel(), 0u, stmp, &tot);
+            const uint32_t nkeep = tot & 0xFFFFu;
+            if (nkeep == na) continue;  // no boundary of power p in this subtree
+            // round of each boundary: ctz(q) for power p (the bracket round of
+            // the node's tournament), T for smaller powers (a delimiter); the
+            // kept boundaries wait in registers until the level is merged
+            uint32_t keep[kKeepMax];
+            uint32_t nk = 0, rmask = 0;
+            uint32_t run = pre;
+            for (uint32_t e = e0; e < e1; e++) {
+                const uint32_t v = bl0[e];
+                const uint32_t pw = be_pow(v);
+                run = OpLevel()(run, pw < p ? 0x80000001u : (pw == p ? 0x00010000u : 0u));
+                if (pw == p) {
+                    const uint32_t q = (run >> 16) & 0x7FFFu;
+                    const uint32_t rd = min((uint32_t)__ffs(q) - 1u, T - 1u);
+                    bl0[e] = (v & 0x00FFFFFFu) | (rd << 24);
+                    rmask |= 1u << rd;
+                } else {
+                    bl0[e] = (v & 0x00FFFFFFu) | (T << 24);
+                    keep[nk++] = v & 0x00FFFFFFu;
                 }
             }
+            const uint32_t kpos = pre & 0xFFFFu;
+            if (rmask) atomicOr(&s_rmask, rmask);
+            __syncthreads();
+            const uint32_t rounds = s_rmask;
+            const int first = round_entry(len, bl0, (int)na);
             // tournament rounds
-            for (uint32_t t = 0; (1u << t) < (uint32_t)k; t++) {
-                uint32_t nd = 0, nm = 0;
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t v = bl0[e];
-                    const uint32_t pw = be_pow(v);
-                    const uint32_t cz = pw == p ? (uint32_t)__ffs(be_q(v)) - 1 : 0u;
-                    nd += (pw < p) || (pw == p && cz > t);
-                    nm += (pw == p && cz == t);
-                }
-                uint32_t tot2;
-                const uint32_t dp = block_sum_excl<kFusedThreads>(nd | (nm << 16), stmp, &tot2);
-                if ((tot2 >> 16) == 0) break;
-                const uint32_t ns = (tot2 & 0xFFFFu) + 1;
-                for (uint32_t i = tid; i < ns; i += kFusedThreads) seg_mid[i] = (uint16_t)kNoMid;
-                if (tid == 0) {
-                    seg_start[0] = 0;
-                    seg_start[ns] = (uint16_t)len;
-                }
-                uint32_t dpos = dp & 0xFFFFu;
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t v = bl0[e];
-                    const uint32_t pw = be_pow(v);
-                    const uint32_t cz = pw == p ? (uint32_t)__ffs(be_q(v)) - 1 : 0u;
-                    if ((pw < p) || (pw == p && cz > t)) seg_start[1 + dpos++] = (uint16_t)be_off(v);
-                }
-                __syncthreads();
-                dpos = dp & 0xFFFFu;
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t v = bl0[e];
-                    const uint32_t pw = be_pow(v);
-                    const uint32_t cz = pw == p ? (uint32_t)__ffs(be_q(v)) - 1 : 0u;
-                    const bool del = (pw < p) || (pw == p && cz > t);
-                    if (pw == p && cz == t) seg_mid[dpos] = (uint16_t)be_off(v);
-                    dpos += del;
-                }
-                __syncthreads();
-                merge_pass<K, V>(cur, oth, vcur, voth, len, seg_start, seg_mid, ns);
+            for (uint32_t t = 0; t < T; t++) {
+                if (!((rounds >> t) & 1u)) continue;
+                merge_round<K, V>(cur, oth, vcur, voth, len, bl0, (int)na, first, t);
                 __syncthreads();
                 K* tk = cur; cur = oth; oth = tk;
                 uint32_t* tv = vcur; vcur = voth; voth = tv;
             }
             // drop the boundaries consumed at this level
-            uint32_t keep[kKeepMax];
-            uint32_t nk = 0;
-            for (uint32_t e = e0; e < e1; e++) {
-                const uint32_t v = bl0[e];
-                if (be_pow(v) < p) keep[nk++] = v & 0x00FFFFFFu;
-            }
-            uint32_t ntot;
-            const uint32_t kpos = block_sum_excl<kFusedThreads>(nk, stmp, &ntot);
             for (uint32_t q = 0; q < nk; q++) bl0[kpos + q] = keep[q];
-            na = ntot;
+            na = nkeep;
             __syncthreads();
         }
 
@@ -669,6 +680,23 @@ __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict_
 }
 
 constexpr int kLvlThreads = 256;
+constexpr uint32_t kLvlPad = 16;  // elements of slack per level-merge buffer
+
+// Block-wide copy of src[0..total) (shared memory) to dst[0..total) (global),
+// where src + q and dst + q share their offset within 16 bytes (src sits
+// `shift` elements past a 16-byte boundary): scalar head and tail, 16-byte
+// vectors in between.
+template <typename T>
+__device__ __forceinline__ void store_vec(T* __restrict__ dst, const T* __restrict__ src, uint32_t total, uint32_t shift) {
+    constexpr uint32_t VE = 16 / sizeof(T);
+    const uint32_t head = min(total, (VE - shift) & (VE - 1u));
+    const uint32_t nvec = (total - head) / VE;
+    for (uint32_t q = threadIdx.x; q < head; q += kLvlThreads) dst[q] = src[q];
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + head);
+    uint4* d4 = reinterpret_cast<uint4*>(dst + head);
+    for (uint32_t q = threadIdx.x; q < nvec; q += kLvlThreads) d4[q] = s4[q];
+    for (uint32_t q = head + nvec * VE + threadIdx.x; q < total; q += kLvlThreads) dst[q] = src[q];
+}
 
 template <typename K, bool V>
 __device__ __forceinline__ void issue_unit_copies(const UnitDesc& D, K* dst, uint32_t* vdst, const K* __restrict__ leaf,
@@ -736,10 +764,13 @@ __global__ void __launch_bounds__(kLvlThreads)
                   const uint32_t* __restrict__ vleaf, K* __restrict__ buf0, K* __restrict__ buf1, uint32_t* __restrict__ vbuf0,
                   uint32_t* __restrict__ vbuf1, uint32_t C, uint64_t n, uint32_t* __restrict__ status) {
     extern __shared__ uint4 smem_raw[];
+    // two buffers of C elements plus room to shift the last round's output
+    // onto the 16-byte grid of its destination
+    const uint32_t CP = C + kLvlPad;
     K* La = reinterpret_cast<K*>(smem_raw);
-    K* Lb = La + C;
-    uint32_t* vLa = V ? reinterpret_cast<uint32_t*>(Lb + C) : nullptr;
-    uint32_t* vLb = V ? vLa + C : nullptr;
+    K* Lb = La + CP;
+    uint32_t* vLa = V ? reinterpret_cast<uint32_t*>(Lb + CP) : nullptr;
+    uint32_t* vLb = V ? vLa + CP : nullptr;
     __shared__ UnitDesc ring[2];
 
     const uint32_t total_units = (uint32_t)ctr[kCtrUnits];
@@ -788,22 +819,37 @@ __global__ void __launch_bounds__(kLvlThreads)
         cp_async_commit();
         cp_async_wait<0>();
         __syncthreads();
+        K* out = odd ? buf1 : buf0;
+        uint32_t* vout = odd ? vbuf1 : vbuf0;
+        const uint32_t ob = D.out_base;
+        // the last round writes element q at shift + q, where shift puts it on
+        // the 16-byte grid of out[ob + q] (16-byte stores below)
+        constexpr uint32_t VK = 16 / sizeof(K);
+        const uint32_t shk = (uint32_t)((reinterpret_cast<uintptr_t>(out + ob) & 15u) / sizeof(K));
+        const uint32_t shv = V ? (uint32_t)((reinterpret_cast<uintptr_t>(vout + ob) & 15u) / 4u) : 0u;
+        uint32_t nr = 0;
+        while ((1u << nr) < d) nr++;
         K* cur = La;
         K* oth = Lb;
         uint32_t* vcur = vLa;
         uint32_t* voth = vLb;
-        for (uint32_t t = 0; (1u << t) < d; t++) {
-            unit_round<K, V>(cur, oth, vcur, voth, D.off, d, t);
+        for (uint32_t t = 0; t < nr; t++) {
+            const bool last = t + 1 == nr;
+            K* dk = oth + (last ? shk : 0u);
+            uint32_t* dv = V ? voth + (last ? shv : 0u) : nullptr;
+            unit_round<K, V>(cur, dk, vcur, dv, D.off, d, t);
             __syncthreads();
-            K* tk = cur; cur = oth; oth = tk;
-            uint32_t* tv = vcur; vcur = voth; voth = tv;
+            oth = cur; cur = dk;
+            voth = vcur; vcur = dv;
         }
-        K* out = odd ? buf1 : buf0;
-        uint32_t* vout = odd ? vbuf1 : vbuf0;
-        const uint32_t ob = D.out_base;
-        for (uint32_t q = threadIdx.x; q < total; q += kLvlThreads) {
-            out[ob + q] = cur[q];
-            if (V) vout[ob + q] = vcur[q];
+        if (nr) {
+            store_vec<K>(out + ob, cur, total, shk);
+            if (V) store_vec<uint32_t>(vout + ob, vcur, total, shv);
+        } else {
+            for (uint32_t q = threadIdx.x; q < total; q += kLvlThreads) {
+                out[ob + q] = cur[q];
+                if (V) vout[ob + q] = vcur[q];
+            }
         }
         if (u + 1 < u1 && threadIdx.x < 8) reinterpret_cast<uint4*>(&ring[(u + 1 - u0) & 1])[threadIdx.x] = nxt;
         __syncthreads();
@@ -861,7 +907,7 @@ MergeGeom merge_geom(int key_bytes, bool vals, int k) {
     g.q = g.c_level / 2;
     g.k = k;
     // persistent level merge: two buffers of c_level elements per block
-    size_t lvl_smem = (size_t)2 * g.c_level * ((size_t)key_bytes + (vals ? 4 : 0)) + 256;
+    size_t lvl_smem = (size_t)2 * (g.c_level + kLvlPad) * ((size_t)key_bytes + (vals ? 4 : 0)) + 256;
     g.level_grid = 152 * (uint32_t)std::min<size_t>(16, (220 * 1024) / lvl_smem);
     size_t fz_smem = (size_t)2 * g.c_fused * ((size_t)key_bytes + (vals ? 4 : 0)) + (size_t)2 * (g.c_fused / 2 + 8) * 4 + 1024;
     g.fused_grid = 152 * (uint32_t)std::max<size_t>(1, std::min<size_t>(8, (220 * 1024) / fz_smem));
@@ -909,7 +955,7 @@ void launch_level_merge(uint32_t nn_bound, uint64_t elems_bound, const K* leaf_k
                         uint32_t* vout, const MergeGeom& g, const WsView& ws, cudaStream_t st) {
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
     const uint64_t bound = elems_bound / g.ts + nn_bound + 1;
-    size_t smem = (size_t)2 * g.c_level * (sizeof(K) + (V ? 4 : 0));
+    size_t smem = (size_t)2 * (g.c_level + kLvlPad) * (sizeof(K) + (V ? 4 : 0));
     cudaFuncSetAttribute(k_level_merge<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     uint32_t grid = (uint32_t)std::min<uint64_t>(bound, (uint64_t)g.level_grid);
     k_level_merge<K, V><<<grid, kLvlThreads, smem, st>>>(reinterpret_cast<const UnitDesc*>(ws.unit_desc), ws.counters,

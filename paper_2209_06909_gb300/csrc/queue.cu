@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/mps.h"
+#include "common.cuh"
 
 namespace mps {
 mps_status batch_dispatch(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out, uint64_t n,
@@ -229,7 +230,7 @@ void worker_main(mps_queue* q) {
             cudaError_t e = cudaEventQuery(B.done);
             if (e == cudaErrorNotReady) { i++; continue; }
             const uint32_t dev = *q->h_status[B.stream];
-            mps_status s = e == cudaSuccess ? (dev ? MPS_ERR_DEVICE_CHECK : MPS_OK) : MPS_ERR_CUDA;
+            mps_status s = e == cudaSuccess ? (dev ? (dev == mps::kDevSpin ? MPS_ERR_TIMEOUT : MPS_ERR_DEVICE_CHECK) : MPS_OK) : MPS_ERR_CUDA;
             finish_tickets(q, B.tickets, s, dev);
             q->stream_busy[B.stream] = 0;
             release_batch(q, B);

@@ -94,9 +94,19 @@ __device__ __forceinline__ void load_window(const K* __restrict__ keys, uint64_t
     v[kDetItems + 1] = (i0 + kDetItems < n) ? keys[i0 + kDetItems] : K(0);
 }
 
+// Bit j (j = 0..16) = key[i0 + j] < key[i0 + j - 1]: the comparisons that
+// drive the automaton for the thread's 16 elements, plus one more for the
+// direction of a run that starts at its last element.
 template <typename K>
-__device__ __forceinline__ uint4 thread_runsum(const K (&v)[kDetItems + 2], uint64_t n, uint64_t i0,
-                                              const uint64_t* __restrict__ off, uint32_t m) {
+__device__ __forceinline__ uint32_t lt_mask(const K (&v)[kDetItems + 2]) {
+    uint32_t msk = 0;
+#pragma unroll
+    for (int j = 0; j <= kDetItems; j++) msk |= (v[1 + j] < v[j] ? 1u : 0u) << j;
+    return msk;
+}
+
+__device__ __forceinline__ uint4 thread_runsum(uint32_t lt, uint64_t n, uint64_t i0, const uint64_t* __restrict__ off,
+                                              uint32_t m) {
     uint32_t s0 = 0, s1 = 1, s2 = 2, c0 = 0, c1 = 0, c2 = 0;
     uint64_t nx = next_start(off, m, i0);
 #pragma unroll
@@ -107,8 +117,8 @@ __device__ __forceinline__ uint4 thread_runsum(const K (&v)[kDetItems + 2], uint
                 nx = next_start(off, m, i + 1);
                 s0 = s1 = s2 = 0;
             } else {
-                bool lt = v[1 + j] < v[j];
-                s0 = step_state(s0, lt); s1 = step_state(s1, lt); s2 = step_state(s2, lt);
+                const bool l = (lt >> j) & 1u;
+                s0 = step_state(s0, l); s1 = step_state(s1, l); s2 = step_state(s2, l);
             }
             c0 += (s0 == 0); c1 += (s1 == 0); c2 += (s2 == 0);
         }
@@ -116,78 +126,166 @@ __device__ __forceinline__ uint4 thread_runsum(const K (&v)[kDetItems + 2], uint
     return make_uint4(s0 | (s1 << 2) | (s2 << 4), c0, c1, c2);
 }
 
-template <typename K>
-__global__ void __launch_bounds__(kDetThreads) k_det_reduce(const K* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
-                                                            uint32_t m, uint4* __restrict__ tile_sum) {
-    __shared__ uint4 tmp[kDetThreads / 32 + 1];
-    uint64_t i0 = (uint64_t)blockIdx.x * kDetTile + (uint64_t)threadIdx.x * kDetItems;
-    K v[kDetItems + 2];
-    load_window(keys, n, i0, v);
-    uint4 s = thread_runsum(v, n, i0, off, m);
-    uint4 tot;
-    block_scan_excl<kDetThreads, false>(s, OpRunSum(), runsum_identity(), tmp, &tot);
-    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
-}
+// ---- single-pass tile scan with decoupled look-back
+// Each tile publishes a 64-bit word: flag (bits 62-63) and either its own
+// summary (flag 1: map in bits 0-5, B-counts per entry state in 13-bit fields
+// at 6, 19, 32) or its inclusive prefix (flag 2: state after the tile in bits
+// 0-1, runs up to and including the tile in bits 2-33).  Tile 0 starts in
+// state B, so a prefix needs only the one state and count.
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPre = 2ull << 62;
+constexpr uint64_t kFlagMask = 3ull << 62;
+constexpr uint32_t kSpinLimit = 1u << 22;
 
-// Exclusive scan over tile summaries; writes per tile (entry state, runs before)
-// and the run count r.  One block.
-__global__ void __launch_bounds__(1024) k_det_scan(const uint4* __restrict__ tile_sum, uint32_t tiles, uint2* __restrict__ tile_pref,
-                                                   uint64_t* __restrict__ counters, uint32_t* __restrict__ run_starts, uint64_t n) {
-    __shared__ uint4 tmp[1024 / 32 + 1];
-    uint32_t per = (tiles + 1023) / 1024;
-    uint32_t b = threadIdx.x * per, e = min(tiles, b + per);
-    uint4 acc = runsum_identity();
-    OpRunSum op;
-    for (uint32_t t = b; t < e; t++) acc = op(acc, tile_sum[t]);
-    uint4 tot;
-    uint4 pre = block_scan_excl<1024, false>(acc, op, runsum_identity(), tmp, &tot);
-    for (uint32_t t = b; t < e; t++) {
-        // the state before element 0 is irrelevant (element 0 resets to B); use B
-        tile_pref[t] = make_uint2(map_get(pre.x, 0), pre.y);
-        pre = op(pre, tile_sum[t]);
-    }
-    if (threadIdx.x == 0) {
-        uint64_t r = tot.y;
-        counters[kCtrR] = r;
-        run_starts[r] = (uint32_t)n;
-    }
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t pack_agg(uint4 a) {
+    return kFlagAgg | (uint64_t)a.x | ((uint64_t)a.y << 6) | ((uint64_t)a.z << 19) | ((uint64_t)a.w << 32);
+}
+__device__ __forceinline__ uint4 unpack_agg(uint64_t w) {
+    return make_uint4((uint32_t)(w & 63u), (uint32_t)((w >> 6) & 0x1FFFu), (uint32_t)((w >> 19) & 0x1FFFu),
+                      (uint32_t)((w >> 32) & 0x1FFFu));
+}
+__device__ __forceinline__ uint32_t runsum_count(uint4 a, uint32_t st) { return st == 0 ? a.y : (st == 1 ? a.z : a.w); }
 
+// Run detection in one pass over the keys.  Tiles take their index from a
+// counter in launch order, so every tile a block waits for is already
+// running; the block scans its tile, publishes the tile summary, walks back
+// over earlier tiles until it meets a published prefix (bounded waits; a wait
+// that runs out sets the status word), publishes its own prefix, and writes
+// its run starts and directions, staged in shared memory, as one contiguous
+// coalesced range.
 template <typename K>
-__global__ void __launch_bounds__(kDetThreads) k_det_write(const K* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
-                                                           uint32_t m, const uint2* __restrict__ tile_pref,
-                                                           uint32_t* __restrict__ run_starts, uint8_t* __restrict__ run_desc) {
+__global__ void __launch_bounds__(kDetThreads, 5) k_detect(const K* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
+                                                        uint32_t m, uint64_t* __restrict__ tile_state,
+                                                        uint64_t* __restrict__ counters, uint32_t* __restrict__ run_starts,
+                                                        uint8_t* __restrict__ run_desc) {
     __shared__ uint4 tmp[kDetThreads / 32 + 1];
-    uint64_t i0 = (uint64_t)blockIdx.x * kDetTile + (uint64_t)threadIdx.x * kDetItems;
-    K v[kDetItems + 2];
-    load_window(keys, n, i0, v);
-    uint4 s = thread_runsum(v, n, i0, off, m);
-    uint4 pre = block_scan_excl<kDetThreads, false>(s, OpRunSum(), runsum_identity(), tmp, nullptr);
-    uint2 tp = tile_pref[blockIdx.x];
-    uint32_t st = map_get(pre.x, tp.x);
-    uint32_t cnts[3] = {pre.y, pre.z, pre.w};
-    uint32_t idx = tp.y + cnts[tp.x];
+    __shared__ uint32_t s_tile, s_state, s_base, s_count;
+    __shared__ uint32_t s_rs[kDetTile];
+    __shared__ uint8_t s_rd[kDetTile];
+    if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(counters + kCtrDetTile), 1ull);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t tiles = (uint32_t)ceil_div(n, kDetTile);
+    const uint64_t i0 = (uint64_t)tile * kDetTile + (uint64_t)threadIdx.x * kDetItems;
+    uint32_t lt;
+    {
+        K v[kDetItems + 2];
+        load_window(keys, n, i0, v);
+        lt = lt_mask(v);
+    }
+    const uint4 s = thread_runsum(lt, n, i0, off, m);
+    uint4 tot;
+    const uint4 pre = block_scan_excl<kDetThreads, false>(s, OpRunSum(), runsum_identity(), tmp, &tot);
+    if (threadIdx.x < 32) {
+        // Look-back by warp 0: lane i reads the word of tile (window end - i).
+        // The nearest published prefix ends the walk; the summaries of the
+        // tiles after it compose (earlier tile first) into `comp`.
+        const uint32_t lane = threadIdx.x;
+        // element 0 always starts a run, so tile 0's entry state is irrelevant (B)
+        uint32_t st_in = 0, base = 0;
+        if (tile > 0) {
+            if (lane == 0) st_release(tile_state + tile, pack_agg(tot));
+            uint4 comp = runsum_identity();
+            int64_t win_end = (int64_t)tile - 1;
+            bool failed = false;
+            while (true) {
+                const int64_t t = win_end - (int64_t)lane;
+                uint64_t w = 0;
+                uint32_t pmask = 0;
+                int jp = 32;
+                for (uint32_t spins = 0;; spins++) {
+                    w = t >= 0 ? ld_acquire(tile_state + t) : kFlagPre;  // tile 0 always holds a prefix
+                    pmask = __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagPre);
+                    jp = pmask ? __ffs(pmask) - 1 : 32;
+                    const uint32_t before = jp == 32 ? 0xffffffffu : ((1u << jp) - 1u);
+                    const uint32_t waiting = __ballot_sync(0xffffffffu, (w & kFlagMask) == 0) & before;
+                    if (!waiting) break;
+                    if (spins >= kSpinLimit) {
+                        failed = true;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                if (failed) {
+                    if (lane == 0) dev_fail(reinterpret_cast<uint32_t*>(counters + kCtrStatus), kDevSpin);
+                    break;
+                }
+                // compose the summaries of lanes 0 .. jp-1 (lane jp-1 is the earliest tile)
+                uint4 x = (int)lane < jp ? unpack_agg(w) : runsum_identity();
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint4 y = shfl_down(x, o);
+                    if (lane + o < 32) x = OpRunSum()(y, x);
+                }
+                x.x = __shfl_sync(0xffffffffu, x.x, 0);
+                x.y = __shfl_sync(0xffffffffu, x.y, 0);
+                x.z = __shfl_sync(0xffffffffu, x.z, 0);
+                x.w = __shfl_sync(0xffffffffu, x.w, 0);
+                comp = OpRunSum()(x, comp);
+                if (jp < 32) {
+                    const uint64_t wp = __shfl_sync(0xffffffffu, w, jp);
+                    const uint32_t sp = (uint32_t)(wp & 3u), cp = (uint32_t)((wp >> 2) & 0xFFFFFFFFu);
+                    st_in = map_get(comp.x, sp);
+                    base = cp + runsum_count(comp, sp);
+                    break;
+                }
+                win_end -= 32;
+            }
+        }
+        if (lane == 0) {
+            const uint32_t cnt = runsum_count(tot, st_in);
+            const uint32_t st_out = map_get(tot.x, st_in);
+            st_release(tile_state + tile, kFlagPre | ((uint64_t)(base + cnt) << 2) | st_out);
+            s_state = st_in;
+            s_base = base;
+            s_count = cnt;
+            if (tile == tiles - 1) {
+                counters[kCtrR] = base + cnt;
+                run_starts[base + cnt] = (uint32_t)n;
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t st_in = s_state;
+    uint32_t st = map_get(pre.x, st_in);
+    uint32_t idx = runsum_count(pre, st_in);
     uint64_t nx = next_start(off, m, i0);
 #pragma unroll
     for (int j = 0; j < kDetItems; j++) {
-        uint64_t i = i0 + j;
+        const uint64_t i = i0 + j;
         if (i < n) {
             const bool reset = (i == nx);
             if (reset) nx = next_start(off, m, i + 1);
-            st = reset ? 0u : step_state(st, v[1 + j] < v[j]);
+            st = reset ? 0u : step_state(st, (lt >> j) & 1u);
             if (st == 0) {
-                run_starts[idx] = (uint32_t)i;
+                s_rs[idx] = (uint32_t)i;
                 // descending iff the next element is in the same array and smaller
-                run_desc[idx] = (i + 1 < n && i + 1 != nx && v[2 + j] < v[1 + j]) ? 1 : 0;
+                s_rd[idx] = (i + 1 < n && i + 1 != nx && ((lt >> (j + 1)) & 1u)) ? 1 : 0;
                 idx++;
             }
         }
     }
+    __syncthreads();
+    const uint32_t base = s_base, cnt = s_count;
+    for (uint32_t q = threadIdx.x; q < cnt; q += kDetThreads) {
+        run_starts[base + q] = s_rs[q];
+        run_desc[base + q] = s_rd[q];
+    }
 }
 
 // Powers of boundaries 1..r-1, sentinels powers[0] = powers[r] = 0, padding
-// of 255 up to the next multiple of 32, and the bit set of powers that occur.
-__global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run_starts, const uint64_t* __restrict__ counters,
+// of 255 up to the next multiple of 32, the bit set of powers that occur and
+// the longest run.  Each thread takes 16 boundaries: 16-byte loads of run
+// starts (the array is padded past r) and one 16-byte store of powers.
+__global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run_starts, uint64_t* __restrict__ counters,
                                                 uint64_t n, uint32_t w, uint64_t magic, uint32_t log2k,
                                                 const uint64_t* __restrict__ off, uint32_t m,
                                                 const uint2* __restrict__ arr_param,
@@ -195,59 +293,79 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
     __shared__ unsigned long long red[256 / 32 + 1];
     __shared__ uint32_t redm[256 / 32 + 1];
     const uint32_t r = (uint32_t)counters[kCtrR];
+    const uint32_t groups = (r + 1 + 15) / 16;  // boundaries 0..r
+    const uint32_t pad_end = (r + 1 + 31) / 32 * 32;
     unsigned long long bits = 0;
     uint32_t longest = 0;  // longest run seen by this thread
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= r; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t si = run_starts[i];
-        uint32_t sp = i >= 1 ? run_starts[i - 1] : 0u;
-        longest = max(longest, si - sp);
-        // the array holding run i (a batch sorts each array on its own)
-        uint64_t base = 0, nn = n;
-        uint32_t ww = w;
-        uint64_t mg = magic;
-        bool arr_start = false;
-        if (off != nullptr && i >= 1 && i < r) {
-            uint32_t lo = 0, hi = m + 1;  // last a with off[a] <= si
+    for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < groups; gi += gridDim.x * blockDim.x) {
+        const uint32_t i0 = gi * 16;
+        uint32_t rv[20];
+        const uint4* r4 = reinterpret_cast<const uint4*>(run_starts + i0);
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+            const uint4 x = r4[q];
+            rv[4 * q] = x.x; rv[4 * q + 1] = x.y; rv[4 * q + 2] = x.z; rv[4 * q + 3] = x.w;
+        }
+        const uint32_t prev = i0 ? run_starts[i0 - 1] : 0u;
+        // the array holding run i0 (a batch sorts each array on its own): last a with off[a] <= s
+        uint32_t arr = 0;
+        if (off != nullptr) {
+            uint32_t lo = 0, hi = m + 1;
+            const uint32_t s0 = rv[0];
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (off[mid] <= si) lo = mid; else hi = mid;
+                if (off[mid] <= s0) lo = mid; else hi = mid;
             }
-            base = off[lo];
-            nn = off[lo + 1] - base;
-            arr_start = (base == si);
-            const uint2 prm = arr_param[lo];
-            ww = prm.x;
-            mg = ((uint64_t)prm.y << 32) | arr_param[m + lo].x;
+            arr = lo;
         }
-        const uint64_t d = 2 * nn;
-        if (i >= 1 && i < r && !arr_start) {
-            uint64_t a2 = (uint64_t)(sp - base) + (si - base);                 // 2n * a
-            uint64_t b2 = (uint64_t)(si - base) + (run_starts[i + 1] - base);  // 2n * b
-            const uint32_t w = ww;
-            const uint64_t magic = mg;
-            uint64_t X = a2 << w, Y = b2 << w;
-            uint64_t x = __umul64hi(X, magic), y = __umul64hi(Y, magic);
-            uint64_t rx = X - x * d, ry = Y - y * d;
-            while (rx >= d) { x++; rx -= d; }
-            while (ry >= d) { y++; ry -= d; }
-            uint32_t h = 63u - (uint32_t)__clzll((long long)(x ^ y));
-            uint32_t p2 = w - h;
-            uint32_t pk = (p2 + log2k - 1) / log2k;
-            powers[i] = (uint8_t)pk;
-            bits |= 1ull << pk;
-        } else {
-            powers[i] = 0;
+        uint32_t word[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            const uint32_t i = i0 + q;
+            uint32_t pk = 255u;  // padding past r
+            if (i <= r) {
+                const uint32_t si = rv[q];
+                const uint32_t sp = q ? rv[q - 1] : prev;
+                if (i >= 1) longest = max(longest, si - sp);
+                pk = 0;
+                uint64_t base = 0, nn = n;
+                uint32_t ww = w;
+                uint64_t mg = magic;
+                bool arr_start = false;
+                if (off != nullptr && i >= 1 && i < r) {
+                    while (arr < m && off[arr + 1] <= si) arr++;
+                    base = off[arr];
+                    nn = off[arr + 1] - base;
+                    arr_start = (base == si);
+                    const uint2 prm = arr_param[arr];
+                    ww = prm.x;
+                    mg = ((uint64_t)prm.y << 32) | arr_param[m + arr].x;
+                }
+                if (i >= 1 && i < r && !arr_start) {
+                    const uint64_t d = 2 * nn;
+                    const uint64_t a2 = (uint64_t)(sp - base) + (si - base);         // 2n * a
+                    const uint64_t b2 = (uint64_t)(si - base) + (rv[q + 1] - base);  // 2n * b
+                    const uint64_t X = a2 << ww, Y = b2 << ww;
+                    uint64_t x = __umul64hi(X, mg), y = __umul64hi(Y, mg);
+                    uint64_t rx = X - x * d, ry = Y - y * d;
+                    while (rx >= d) { x++; rx -= d; }
+                    while (ry >= d) { y++; ry -= d; }
+                    const uint32_t h = 63u - (uint32_t)__clzll((long long)(x ^ y));
+                    const uint32_t p2 = ww - h;
+                    pk = (p2 + log2k - 1) / log2k;
+                    bits |= 1ull << pk;
+                }
+            }
+            word[q >> 2] |= pk << (8 * (q & 3));
         }
-        if (i == r) {
-            uint64_t pad_end = (r + 1 + 31) / 32 * 32;
-            for (uint64_t q = r + 1; q < pad_end; q++) powers[q] = 255;
-        }
+        *reinterpret_cast<uint4*>(powers + i0) = make_uint4(word[0], word[1], word[2], word[3]);
+        if (i0 <= r && r < i0 + 16 && pad_end > i0 + 16)
+            *reinterpret_cast<uint4*>(powers + i0 + 16) = make_uint4(~0u, ~0u, ~0u, ~0u);
     }
     bits = block_reduce<256>(bits, OpOrU64(), 0ull, red);
     longest = block_reduce<256>(longest, OpMax32(), 0u, redm);
     if (threadIdx.x == 0 && bits) atomicOr(level_bits, bits);
-    if (threadIdx.x == 0 && longest)
-        atomicMax(reinterpret_cast<unsigned long long*>(const_cast<uint64_t*>(counters) + kCtrMaxRun), (unsigned long long)longest);
+    if (threadIdx.x == 0 && longest) atomicMax(reinterpret_cast<unsigned long long*>(counters + kCtrMaxRun), (unsigned long long)longest);
 }
 
 // Per-array power parameters of a batch: w = ceil(log2 n_a) and the 64-bit
@@ -275,10 +393,10 @@ __global__ void k_array_params(const uint64_t* __restrict__ off, uint32_t m, uin
 template <typename K>
 void launch_detect(const K* keys, uint64_t n, const WsView& ws, cudaStream_t st) {
     uint32_t tiles = (uint32_t)ceil_div(n, kDetTile);
-    k_det_reduce<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.batch_off, ws.batch_m, ws.det_sum);
-    k_det_scan<<<1, 1024, 0, st>>>(ws.det_sum, tiles, ws.det_pref, ws.counters, ws.run_starts, n);
-    k_det_write<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.batch_off, ws.batch_m, ws.det_pref, ws.run_starts, ws.run_desc);
-    g_launches += 3;
+    cudaMemsetAsync(ws.det_state, 0, (size_t)tiles * 8, st);
+    k_detect<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.batch_off, ws.batch_m, ws.det_state, ws.counters, ws.run_starts,
+                                               ws.run_desc);
+    g_launches += 1;
 }
 
 template void launch_detect<uint32_t>(const uint32_t*, uint64_t, const WsView&, cudaStream_t);
@@ -290,7 +408,7 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
     uint64_t magic = ~0ull / (2 * n);
     uint32_t log2k = k == 2 ? 1 : (k == 4 ? 2 : 3);
     uint32_t threads = 256;
-    uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r + 1, threads), 152 * 16);
+    uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(ceil_div((uint64_t)r + 1, 16), threads), 152 * 16);
     if (ws.batch_off) {
         k_array_params<<<(uint32_t)std::min<uint64_t>(ceil_div(ws.batch_m, 256), 1024), 256, 0, st>>>(ws.batch_off, ws.batch_m,
                                                                                                   ws.batch_max_len, ws.batch_prm,

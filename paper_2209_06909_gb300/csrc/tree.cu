@@ -161,16 +161,21 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask_reduce(const uint8_t* __r
                                                               unsigned long long* __restrict__ tf, unsigned long long* __restrict__ tg) {
     __shared__ unsigned long long tmp[kMaskThreads / 32 + 1];
     const uint32_t r = (uint32_t)ctr[kCtrR];
-    uint32_t nb = r - 1;
-    uint32_t b0 = blockIdx.x * kMaskTile + threadIdx.x * kMaskItems;
+    const uint32_t nb = r - 1;
+    const uint32_t b0 = blockIdx.x * kMaskTile + threadIdx.x * kMaskItems;
     unsigned long long f = kMaskIdentity, g = kMaskIdentity;
+    if (b0 < nb) {
+        // powers[b0 .. b0+31] (padded past r); boundary b is j = b + 1
+        const uint4* p4 = reinterpret_cast<const uint4*>(powers + b0);
+        const uint4 a = p4[0], c = p4[1];
+        const uint32_t pw[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
 #pragma unroll
-    for (int q = 0; q < kMaskItems; q++) {
-        uint32_t b = b0 + q;
-        if (b < nb) {
-            uint64_t e = melem(powers[b + 1]);
-            f = OpF()(f, e);
-            g = OpG()(g, e);
+        for (int q = 0; q < kMaskItems; q++) {
+            if (b0 + q < nb) {
+                const uint64_t e = melem((pw[(q + 1) >> 2] >> (8 * ((q + 1) & 3))) & 0xFFu);
+                f = OpF()(f, e);
+                g = OpG()(g, e);
+            }
         }
     }
     unsigned long long tot;
@@ -201,66 +206,115 @@ __global__ void __launch_bounds__(1024) k_mask_scan(const unsigned long long* __
     }
 }
 
-// Writes node_info (depth | start << 7) for every boundary, optionally the leaf
-// depths, and adds to the counters the merge cost M = sum_i depth(run i) L_i
-// (Sec. 2.2) and the number of nodes.
-__global__ void __launch_bounds__(kMaskThreads) k_mask_apply(const uint8_t* __restrict__ powers, uint64_t* __restrict__ ctr,
+// Smallest power v >= 1 whose inner nodes are provably at most T_max elements
+// (255 if none).  Every interior boundary of a node of power v has power >= v,
+// i.e. P2 > (v-1) log2 k (Def. 3.1 with P_k = ceil(P2 / log2 k)), so adjacent
+// runs of the node have midpoints a/n that agree in their first (v-1) log2 k
+// bits: all run midpoints of the node lie in one interval of n / k^(v-1)
+// elements, and the node is smaller than that plus half of each end run, i.e.
+// than n / k^(v-1) + (longest run).  (A batch takes its longest array for n.)
+__device__ __forceinline__ uint32_t small_power(uint64_t nmax, uint64_t longest, uint32_t log2k, uint32_t tmax) {
+    for (uint32_t v = 1; v < 64; v++) {
+        const uint32_t sh = (v - 1) * log2k;
+        const uint64_t span = sh >= 63 ? 1ull : ((nmax + (1ull << sh) - 1) >> sh);
+        if (span + longest <= tmax) return v;
+    }
+    return 255u;
+}
+
+// Per boundary j = b + 1, node_info[b] = depth | query << 6 | start << 7, where
+// start marks the first boundary of a node and query marks the starts the
+// node pass must examine: roots (depth 0) and nodes of power below
+// small_power().  Optionally writes the leaf depths, and adds to the counters
+// the merge cost M = sum_i depth(run i) L_i (Sec. 2.2) and the number of nodes.
+// Each thread holds 16 boundaries: 16-byte loads of powers and run starts and
+// one 16-byte store of node_info.
+__global__ void __launch_bounds__(kMaskThreads, 3) k_mask_apply(const uint8_t* __restrict__ powers, uint64_t* __restrict__ ctr,
                                                              const uint32_t* __restrict__ rs,
                                                              const unsigned long long* __restrict__ fpre,
                                                              const unsigned long long* __restrict__ gsuf,
-                                                             uint8_t* __restrict__ node_info, uint8_t* __restrict__ leaf_depth) {
+                                                             uint8_t* __restrict__ node_info, uint8_t* __restrict__ leaf_depth,
+                                                             uint64_t n_single, uint32_t log2k, uint32_t tmax) {
+    static_assert(kMaskItems == 16, "one 16-byte word of node_info per thread");
     __shared__ unsigned long long tmp[kMaskThreads / 32 + 1];
     const uint32_t r = (uint32_t)ctr[kCtrR];
-    uint32_t nb = r - 1;
-    uint32_t b0 = blockIdx.x * kMaskTile + threadIdx.x * kMaskItems;
-    uint64_t e[kMaskItems];
+    const uint32_t nb = r - 1;
+    const uint32_t b0 = blockIdx.x * kMaskTile + threadIdx.x * kMaskItems;
+    const bool live = b0 < nb;
+    const uint32_t vskip = small_power(n_single ? n_single : ctr[kCtrMaxLen], ctr[kCtrMaxRun], log2k, tmax);
+    // powers[b0 .. b0+31] and rs[b0 .. b0+19] (both arrays are padded past r)
+    uint32_t pw[8], rv[20];
+    if (live) {
+        const uint4* p4 = reinterpret_cast<const uint4*>(powers + b0);
+        const uint4 a = p4[0], c = p4[1];
+        pw[0] = a.x; pw[1] = a.y; pw[2] = a.z; pw[3] = a.w; pw[4] = c.x; pw[5] = c.y; pw[6] = c.z; pw[7] = c.w;
+        const uint4* r4 = reinterpret_cast<const uint4*>(rs + b0);
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+            const uint4 x = r4[q];
+            rv[4 * q] = x.x; rv[4 * q + 1] = x.y; rv[4 * q + 2] = x.z; rv[4 * q + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; q++) pw[q] = 0;
+#pragma unroll
+        for (int q = 0; q < 20; q++) rv[q] = 0;
+    }
+    // element of boundary b0 + q (the power of j = b0 + q + 1), identity past the end
+    auto elem = [&](int q) -> unsigned long long {
+        const uint32_t p = (pw[(q + 1) >> 2] >> (8 * ((q + 1) & 3))) & 0xFFu;
+        return b0 + q < nb ? melem(p) : kMaskIdentity;
+    };
     unsigned long long f = kMaskIdentity, g = kMaskIdentity;
 #pragma unroll
     for (int q = 0; q < kMaskItems; q++) {
-        uint32_t b = b0 + q;
-        e[q] = b < nb ? melem(powers[b + 1]) : kMaskIdentity;
-        f = OpF()(f, e[q]);
-        g = OpG()(g, e[q]);
+        const unsigned long long e = elem(q);
+        f = OpF()(f, e);
+        g = OpG()(g, e);
     }
     unsigned long long pf = block_scan_excl<kMaskThreads, false>(f, OpF(), kMaskIdentity, tmp, nullptr);
     unsigned long long sg = block_scan_excl<kMaskThreads, true>(g, OpGRev(), kMaskIdentity, tmp, nullptr);
     pf = OpF()(fpre[blockIdx.x], pf);
     sg = OpG()(sg, gsuf[blockIdx.x]);
-    // right-side summaries per item, right to left
-    uint64_t gex[kMaskItems];
+    // bit sets of the right-side summaries per item (right to left); powers are
+    // at most 32, so bits 1..32 of a summary fit in 32 bits
+    uint32_t rb[kMaskItems];
+    uint32_t d0 = 0;  // depth of run 0 (thread holding boundary 1 only)
 #pragma unroll
     for (int q = kMaskItems - 1; q >= 0; q--) {
-        gex[q] = sg;
-        sg = OpG()(e[q], sg);
+        rb[q] = (uint32_t)((sg & kBits) >> 1);
+        const unsigned long long e = elem(q);
+        if (q == 0 && b0 == 0) d0 = (uint32_t)__popcll(OpG()(e, sg) & kBits & ~1ull);
+        sg = OpG()(e, sg);
     }
     unsigned long long cost = 0, nodes = 0;
-    uint32_t rs_next = b0 < nb ? rs[b0 + 1] : 0u;
+    uint32_t word[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int q = 0; q < kMaskItems; q++) {
-        uint32_t b = b0 + q;
+        const uint32_t b = b0 + q;
+        const unsigned long long e = elem(q);
         if (b < nb) {
-            uint32_t j = b + 1;
-            uint32_t p = mmin(e[q]);
-            uint64_t left = pf & kBits & ~1ull, right = gex[q] & kBits & ~1ull;
-            uint32_t depth = __popcll((left | right) & below(p));
+            const uint32_t j = b + 1;
+            const uint32_t p = mmin(e);
+            const uint64_t left = pf & kBits & ~1ull, right = (uint64_t)rb[q] << 1;
+            const uint32_t depth = __popcll((left | right) & below(p));
             // power 0 marks an array start inside a batch: never a node boundary
-            uint32_t start = (p == 0 || ((left >> p) & 1ull)) ? 0u : 1u;
-            node_info[j] = (uint8_t)(depth | (start << 7));
+            const uint32_t start = (p == 0 || ((left >> p) & 1ull)) ? 0u : 1u;
+            const uint32_t query = start && (depth == 0 || p < vskip) ? 1u : 0u;
+            word[q >> 2] |= (depth | (query << 6) | (start << 7)) << (8 * (q & 3));
             nodes += start;
-            uint64_t incl = OpF()(pf, e[q]) & kBits & ~1ull;
+            const uint64_t incl = OpF()(pf, e) & kBits & ~1ull;
             const uint32_t dj = (uint32_t)__popcll(incl | right);  // depth of run j
-            const uint32_t rs_j = rs_next;
-            rs_next = rs[j + 1];
-            cost += (unsigned long long)dj * (rs_next - rs_j);
+            cost += (unsigned long long)dj * (rv[q + 2] - rv[q + 1]);
             if (j == 1) {
-                const uint32_t d0 = (uint32_t)__popcll(OpG()(e[q], gex[q]) & kBits & ~1ull);  // depth of run 0
-                cost += (unsigned long long)d0 * (rs_j - rs[0]);
+                cost += (unsigned long long)d0 * (rv[1] - rv[0]);
                 if (leaf_depth) leaf_depth[0] = (uint8_t)d0;
             }
             if (leaf_depth) leaf_depth[j] = (uint8_t)dj;
         }
-        pf = OpF()(pf, e[q]);
+        pf = OpF()(pf, e);
     }
+    if (live) *reinterpret_cast<uint4*>(node_info + b0) = make_uint4(word[0], word[1], word[2], word[3]);
     cost = block_reduce<kMaskThreads>(cost, OpAddU64(), 0ull, tmp);
     nodes = block_reduce<kMaskThreads>(nodes, OpAddU64(), 0ull, tmp);
     if (threadIdx.x == 0) {
@@ -296,79 +350,72 @@ __device__ __forceinline__ bool node_shape(const MinTree& T, const uint8_t* P, u
     return ok;
 }
 
-// One pass over the boundaries (grid-stride) that finds the nodes larger than
-// T_max.  Such a node becomes a level-merge record and appends each child that
-// is an inner node of at most T_max elements to the list of fused subtrees (its
-// parent is large, so it is maximal); a small root is a fused subtree too.
-//
-// Most nodes are skipped without a nearest-smaller query.  Every interior
-// boundary of a node of power v has power >= v, i.e. P2 > (v-1) log2 k (Def. 3.1
-// with P_k = ceil(P2 / log2 k)), so consecutive runs of the node have run
-// midpoints that agree in their first (v-1) log2 k bits of a/n; all its run
-// midpoints lie in one interval of n / k^(v-1) elements, and its size is less
-// than that plus half of each end run: below n / k^(v-1) + (longest run).  An
-// inner node (depth > 0) whose bound is at most T_max is never large and never
-// a fused root.  (Batches use the longest array for n.)
-__global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tmax, uint64_t n_single,
+// Finds the nodes larger than T_max among the node starts that k_mask_apply
+// marked for a query (16 boundaries per 16-byte load; unmarked words are
+// skipped whole).  A large node becomes a level-merge record and appends each
+// child that is an inner node of at most T_max elements to the list of fused
+// subtrees (its parent is large, so it is maximal); a small root is a fused
+// subtree too.
+__global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tmax,
                                                    const uint32_t* __restrict__ rs, const uint8_t* __restrict__ node_info,
                                                    uint64_t* __restrict__ ctr, LevelNode* __restrict__ nodes_raw, uint32_t nodes_cap,
                                                    uint4* __restrict__ fused_list, uint32_t fused_cap) {
     const uint8_t* P = T.lv[0];
     uint32_t* status = reinterpret_cast<uint32_t*>(ctr + kCtrStatus);
     const uint32_t r = (uint32_t)ctr[kCtrR];
-    const uint64_t nmax = n_single ? n_single : ctr[kCtrMaxLen];
-    const uint64_t longest = ctr[kCtrMaxRun];
-    const uint32_t log2k = k == 2 ? 1u : (k == 4 ? 2u : 3u);
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x + 1; j < r; j += gridDim.x * blockDim.x) {
-        uint8_t info = node_info[j];
-        if (!(info & 0x80)) continue;
-        const uint32_t v = P[j];
-        if (v == 0) continue;
-        const uint32_t depth = info & 0x7F;
-        if (depth != 0) {
-            const uint32_t sh = (v - 1) * log2k;
-            const uint64_t span = sh >= 63 ? 1ull : ((nmax + (1ull << sh) - 1) >> sh);
-            if (span + longest <= tmax) continue;
-        }
-        const uint32_t L = nsv_left(T, j, v, true);
-        const uint32_t R = nsv_right(T, j, v, true);
-        const uint32_t sL = rs[L], sR = rs[R];
-        const uint32_t size = sR - sL;
-        if (size > tmax) {
-            NodeShape s;
-            if (!node_shape(T, P, j, v, k, s)) dev_fail(status, kDevDegree);
-            uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmTotal), 1ull);
-            if (slot < nodes_cap) {
-                LevelNode nd;
-                nd.sL = sL; nd.sR = sR; nd.unit_off = 0; nd.nunits = 0;
+    const uint32_t nb = r - 1;
+    const uint32_t words = (nb + 15) >> 4;
+    for (uint32_t wi = blockIdx.x * blockDim.x + threadIdx.x; wi < words; wi += gridDim.x * blockDim.x) {
+        const uint4 w4 = reinterpret_cast<const uint4*>(node_info)[wi];
+        if (!((w4.x | w4.y | w4.z | w4.w) & 0x40404040u)) continue;
+        const uint32_t wd[4] = {w4.x, w4.y, w4.z, w4.w};
+        for (uint32_t q = 0; q < 16; q++) {
+            const uint32_t info = (wd[q >> 2] >> (8 * (q & 3))) & 0xFFu;
+            const uint32_t b = wi * 16 + q;
+            if (!(info & 0x40) || b >= nb) continue;
+            const uint32_t j = b + 1;
+            const uint32_t v = P[j];
+            const uint32_t depth = info & 0x3F;
+            const uint32_t L = nsv_left(T, j, v, true);
+            const uint32_t R = nsv_right(T, j, v, true);
+            const uint32_t sL = rs[L], sR = rs[R];
+            const uint32_t size = sR - sL;
+            if (size > tmax) {
+                NodeShape s;
+                if (!node_shape(T, P, j, v, k, s)) dev_fail(status, kDevDegree);
+                uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmTotal), 1ull);
+                if (slot < nodes_cap) {
+                    LevelNode nd;
+                    nd.sL = sL; nd.sR = sR; nd.unit_off = 0; nd.nunits = 0;
 #pragma unroll
-                for (int q = 0; q < 9; q++) nd.b[q] = q <= (int)s.d ? s.b[q] : 0u;
-                nd.power = (uint8_t)v; nd.depth = (uint8_t)depth; nd.degree = (uint8_t)s.d; nd.pad = 0;
-                nd.split_off = nd.nsplit = 0;
-                nodes_raw[slot] = nd;
-            } else {
-                dev_fail(status, kDevCapacity);
-            }
-            atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmCount + v), 1ull);
-            atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmSize + v), (unsigned long long)size);
-            unsigned long long fe = 0;
-            for (uint32_t c = 0; c < s.d; c++) {
-                uint32_t a = s.b[c], e = s.b[c + 1];
-                uint32_t cs = rs[e] - rs[a];
-                if (e - a >= 2 && cs <= tmax) {
-                    uint32_t fs = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
-                    if (fs < fused_cap) fused_list[fs] = make_uint4(a, e, depth + 1, 0u);
-                    else dev_fail(status, kDevCapacity);
-                    fe += cs;
+                    for (int c = 0; c < 9; c++) nd.b[c] = c <= (int)s.d ? s.b[c] : 0u;
+                    nd.power = (uint8_t)v; nd.depth = (uint8_t)depth; nd.degree = (uint8_t)s.d; nd.pad = 0;
+                    nd.split_off = nd.nsplit = 0;
+                    nodes_raw[slot] = nd;
+                } else {
+                    dev_fail(status, kDevCapacity);
                 }
+                atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmCount + v), 1ull);
+                atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmSize + v), (unsigned long long)size);
+                unsigned long long fe = 0;
+                for (uint32_t c = 0; c < s.d; c++) {
+                    uint32_t a = s.b[c], e = s.b[c + 1];
+                    uint32_t cs = rs[e] - rs[a];
+                    if (e - a >= 2 && cs <= tmax) {
+                        uint32_t fs = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
+                        if (fs < fused_cap) fused_list[fs] = make_uint4(a, e, depth + 1, 0u);
+                        else dev_fail(status, kDevCapacity);
+                        fe += cs;
+                    }
+                }
+                if (fe) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), fe);
+            } else if (P[L] == 0 && P[R] == 0) {
+                // a root (of the array, or of one array of a batch) that fits a fused tile
+                uint32_t fs = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
+                if (fs < fused_cap) fused_list[fs] = make_uint4(L, R, 0u, 0u);
+                else dev_fail(status, kDevCapacity);
+                atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), (unsigned long long)size);
             }
-            if (fe) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), fe);
-        } else if (P[L] == 0 && P[R] == 0) {
-            // a root (of the array, or of one array of a batch) that fits a fused tile
-            uint32_t fs = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
-            if (fs < fused_cap) fused_list[fs] = make_uint4(L, R, 0u, 0u);
-            else dev_fail(status, kDevCapacity);
-            atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), (unsigned long long)size);
         }
     }
 }
@@ -405,7 +452,7 @@ __global__ void __launch_bounds__(256) k_dump_node_first(MinTree T, uint32_t r, 
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j == 0) node_first[0] = 0;
     if (j == 0 || j >= r) return;
-    if (node_info[j] & 0x80) {
+    if (node_info[j - 1] & 0x80) {
         node_first[j] = j;
     } else {
         uint32_t v = P[j];
@@ -423,7 +470,7 @@ __global__ void __launch_bounds__(256) k_dump_hist(const uint8_t* __restrict__ P
     uint32_t base = blockIdx.x * kMaskTile;
     for (uint32_t q = threadIdx.x; q < kMaskTile; q += blockDim.x) {
         uint32_t j = base + q + 1;
-        if (j < r && (node_info[j] & 0x80)) atomicAdd(&h[P[j]], 1u);
+        if (j < r && (node_info[j - 1] & 0x80)) atomicAdd(&h[P[j]], 1u);
     }
     __syncthreads();
     if (threadIdx.x < kMaxLevels) hist[(size_t)blockIdx.x * kMaxLevels + threadIdx.x] = h[threadIdx.x];
@@ -463,7 +510,7 @@ __global__ void __launch_bounds__(256) k_dump_rank(const uint8_t* __restrict__ P
     uint32_t base = blockIdx.x * kMaskTile;
     for (uint32_t q0 = 0; q0 < (uint32_t)kMaskTile; q0 += 32) {
         uint32_t j = base + q0 + lane + 1;
-        bool st = j < r && (node_info[j] & 0x80);
+        bool st = j < r && (node_info[j - 1] & 0x80);
         uint32_t p = st ? P[j] : 0xFFu;
         uint32_t peers = __match_any_sync(0xffffffffu, p);
         uint32_t below_me = __popc(peers & ((1u << lane) - 1));
@@ -484,7 +531,7 @@ __global__ void __launch_bounds__(256) k_dump_nodes(MinTree T, uint32_t r, int k
                                                     uint32_t* __restrict__ status) {
     const uint8_t* P = T.lv[0];
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    if (j >= r || !(node_info[j] & 0x80)) return;
+    if (j >= r || !(node_info[j - 1] & 0x80)) return;
     uint32_t v = P[j];
     NodeShape s;
     if (!node_shape(T, P, j, v, k, s)) dev_fail(status, kDevDegree);
@@ -518,20 +565,22 @@ void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st) {
     }
 }
 
-void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, const WsView& ws, cudaStream_t st) {
+void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, uint64_t n, int k, uint32_t tmax, const WsView& ws,
+                  cudaStream_t st) {
     uint32_t nb = r - 1;
     uint32_t tiles = (uint32_t)ceil_div(nb, kMaskTile);
     k_mask_reduce<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.mt_f, ws.mt_g);
     k_mask_scan<<<1, 1024, 0, st>>>(ws.mt_f, ws.mt_g, tiles, ws.mt_fpre, ws.mt_gsuf);
+    const uint32_t log2k = k == 2 ? 1u : (k == 4 ? 2u : 3u);
     k_mask_apply<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.run_starts, ws.mt_fpre, ws.mt_gsuf, ws.node_info,
-                                                  dump_leaf ? leaf_depth : nullptr);
+                                                  dump_leaf ? leaf_depth : nullptr, ws.batch_off ? 0ull : n, log2k, tmax);
     g_launches += 3;
 }
 
-void launch_node_pass(uint32_t r, int k, uint32_t tmax, uint64_t n, const WsView& ws, cudaStream_t st) {
-    uint32_t nb = r - 1;
-    uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(nb, 256), 152 * 16);
-    k_node_pass<<<blocks, 256, 0, st>>>(make_mintree(ws), k, tmax, ws.batch_off ? 0ull : n, ws.run_starts, ws.node_info,
+void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st) {
+    uint32_t words = (uint32_t)ceil_div(r - 1, 16);
+    uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(std::max<uint32_t>(words, 1), 256), 152 * 8);
+    k_node_pass<<<blocks, 256, 0, st>>>(make_mintree(ws), k, tmax, ws.run_starts, ws.node_info,
                                                               ws.counters, ws.nodes_raw, ws.nodes_cap, ws.fused_list, ws.fused_cap);
     g_launches += 1;
 }

@@ -128,7 +128,7 @@ def lib():
 
 
 def _check(fn, code):
-    if code == 7:  # device-side check: report which one
+    if code in (5, 7):  # device-side check or bounded device wait: report which one
         s = Stats()
         lib().mps_last_stats(ctypes.byref(s))
         err = MpsError(fn, code)
