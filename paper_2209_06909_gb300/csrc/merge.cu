@@ -45,44 +45,87 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// ---- bulk global -> shared copies on the TMA engine, completed on an mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Orders this thread's earlier shared-memory accesses before later writes by
+// the async (TMA) proxy.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// bytes (a multiple of 16) from 16-byte aligned gmem to 16-byte aligned smem
+__device__ __forceinline__ void bulk_copy_g2s(void* smem, const void* gmem, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(smem)),
+                 "l"(gmem), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+constexpr uint32_t kMbarSpinLimit = 1u << 24;
+
 constexpr int kFusedThreads = 256;
 constexpr uint32_t kNoMid = 0xFFFFu;
 // boundary-list entries one thread holds while compacting: ceil((C/2 + 8) / 256), odd
 constexpr int kKeepMax = 25;
 
-// Number of elements of A = src[s..m) among the first `diag` outputs of the
-// stable merge of A and B = src[m..e) (A first on equal keys): merge path.
+// Number of elements of A[0..na) among the first `diag` outputs of the stable
+// merge of A and B[0..nb) (A first on equal keys): merge path.
 template <typename K>
-__device__ __forceinline__ uint32_t merge_path(const K* __restrict__ src, uint32_t s, uint32_t m, uint32_t e, uint32_t diag) {
-    const uint32_t na = m - s, nbn = e - m;
-    uint32_t l = diag > nbn ? diag - nbn : 0u, h = min(diag, na);
+__device__ __forceinline__ uint32_t merge_path2(const K* __restrict__ A, uint32_t na, const K* __restrict__ B, uint32_t nb,
+                                                uint32_t diag) {
+    uint32_t l = diag > nb ? diag - nb : 0u, h = min(diag, na);
     while (l < h) {
         const uint32_t mid = (l + h) >> 1;
-        if (src[s + mid] <= src[m + diag - 1 - mid]) l = mid + 1; else h = mid;
+        if (A[mid] <= B[diag - 1 - mid]) l = mid + 1; else h = mid;
     }
     return l;
 }
 
-// Writes outputs [o, stop) of the stable merge of src[ia..m) and src[ib..e)
+// Writes outputs [o, stop) of the stable merge of A[ia..na) and B[ib..nb)
 // (ties to A).  Branch-free: every step loads the next element of the side it
-// took; reads are clamped to e - 1 so they stay inside the buffer.
+// took.  A[na] and B[nb] are read (never used), so one element past each side
+// must be readable shared memory.
+template <typename K, bool V>
+__device__ __forceinline__ void serial_merge2(const K* __restrict__ A, uint32_t na, const K* __restrict__ B, uint32_t nb,
+                                              const uint32_t* __restrict__ vA, const uint32_t* __restrict__ vB,
+                                              K* __restrict__ dst, uint32_t* __restrict__ vdst, uint32_t ia, uint32_t ib,
+                                              uint32_t o, uint32_t stop) {
+    K ka = A[ia];
+    K kb = B[ib];
+    for (; o < stop; o++) {
+        const bool take_a = (ib >= nb) || (ia < na && ka <= kb);
+        dst[o] = take_a ? ka : kb;
+        if (V) vdst[o] = take_a ? vA[ia] : vB[ib];
+        ia += take_a ? 1u : 0u;
+        ib += take_a ? 0u : 1u;
+        const K kn = take_a ? A[ia] : B[ib];
+        ka = take_a ? kn : ka;
+        kb = take_a ? kb : kn;
+    }
+}
+
+// The same on one buffer: A = src[s..m), B = src[m..e).
+template <typename K>
+__device__ __forceinline__ uint32_t merge_path(const K* __restrict__ src, uint32_t s, uint32_t m, uint32_t e, uint32_t diag) {
+    return merge_path2(src + s, m - s, src + m, e - m, diag);
+}
 template <typename K, bool V>
 __device__ __forceinline__ void serial_merge(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
                                              uint32_t* __restrict__ vdst, uint32_t ia, uint32_t m, uint32_t ib, uint32_t e,
                                              uint32_t o, uint32_t stop) {
-    const uint32_t last = e - 1;
-    K ka = src[min(ia, last)];
-    K kb = src[min(ib, last)];
-    for (; o < stop; o++) {
-        const bool take_a = (ib >= e) || (ia < m && ka <= kb);
-        dst[o] = take_a ? ka : kb;
-        if (V) vdst[o] = vsrc[take_a ? ia : ib];
-        ia += take_a ? 1u : 0u;
-        ib += take_a ? 0u : 1u;
-        const K kn = src[min(take_a ? ia : ib, last)];
-        ka = take_a ? kn : ka;
-        kb = take_a ? kb : kn;
-    }
+    // positions relative to A = src[.., m) and B = src[m, e): A starts where the merge's A begins (ia is absolute)
+    serial_merge2<K, V>(src, m, src + m, e - m, vsrc, V ? vsrc + m : nullptr, dst, vdst, ia, ib - m, o, stop);
 }
 
 // Outputs per thread when NT threads share a merge pass of `total` outputs:
@@ -680,7 +723,7 @@ __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict_
 }
 
 constexpr int kLvlThreads = 256;
-constexpr uint32_t kLvlPad = 16;  // elements of slack per level-merge buffer
+constexpr uint32_t kLvlPad = 64;  // elements of slack per level-merge buffer
 
 // Block-wide copy of src[0..total) (shared memory) to dst[0..total) (global),
 // where src + q and dst + q share their offset within 16 bytes (src sits
@@ -696,23 +739,6 @@ __device__ __forceinline__ void store_vec(T* __restrict__ dst, const T* __restri
     uint4* d4 = reinterpret_cast<uint4*>(dst + head);
     for (uint32_t q = threadIdx.x; q < nvec; q += kLvlThreads) d4[q] = s4[q];
     for (uint32_t q = head + nvec * VE + threadIdx.x; q < total; q += kLvlThreads) dst[q] = src[q];
-}
-
-template <typename K, bool V>
-__device__ __forceinline__ void issue_unit_copies(const UnitDesc& D, K* dst, uint32_t* vdst, const K* __restrict__ leaf,
-                                                  const uint32_t* __restrict__ vleaf, const K* __restrict__ inner,
-                                                  const uint32_t* __restrict__ vinner) {
-    for (uint32_t c = 0; c < D.d; c++) {
-        const uint32_t o = D.off[c], m = D.off[c + 1] - o, s = D.src[c];
-        const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (8 + c)) & 1u;
-        const K* srck = lf ? leaf : inner;
-        const uint32_t* srcv = lf ? vleaf : vinner;
-        for (uint32_t i = threadIdx.x; i < m; i += kLvlThreads) {
-            const uint32_t g = rv ? s - i : s + i;
-            cp_async<sizeof(K)>(dst + o + i, srck + g);
-            if (V) cp_async<4>(vdst + o + i, srcv + g);
-        }
-    }
 }
 
 // Round t of the tournament over the unit's d slices: slices are grouped in
@@ -753,6 +779,45 @@ __device__ __forceinline__ void unit_round(const K* __restrict__ src, K* __restr
     }
 }
 
+// Round 0 of a unit whose slices sit at their own positions pos[c] (as staged
+// by the loads): slices (0,1), (2,3), ... are merged into dst at the unit's
+// contiguous offsets off[]; a last slice without a partner is copied.
+template <typename K, bool V>
+__device__ __forceinline__ void unit_round0(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
+                                            uint32_t* __restrict__ vdst, const uint32_t* __restrict__ off,
+                                            const uint32_t* __restrict__ pos, uint32_t d) {
+    const uint32_t total = off[d];
+    const uint32_t ipt = chunk_per_thread<kLvlThreads>(total);
+    const uint32_t base = threadIdx.x * ipt;
+    if (base >= total) return;
+    uint32_t o = base;
+    const uint32_t oe = min(base + ipt, total);
+    uint32_t c0 = 0;
+    for (uint32_t c = 2; c < d; c += 2)
+        if (off[c] <= o) c0 = c;
+    while (o < oe) {
+        const uint32_t c1 = min(c0 + 2, d);
+        const uint32_t s = off[c0], e = off[c1];
+        const uint32_t stop = min(e, oe);
+        if (c0 + 1 >= d) {
+            const uint32_t p = pos[c0] - s;
+            for (; o < stop; o++) {
+                dst[o] = src[p + o];
+                if (V) vdst[o] = vsrc[p + o];
+            }
+        } else {
+            const uint32_t pa = pos[c0], pb = pos[c0 + 1];
+            const uint32_t na = off[c0 + 1] - s, nb = e - off[c0 + 1];
+            const uint32_t diag = o - s;
+            const uint32_t l = merge_path2(src + pa, na, src + pb, nb, diag);
+            serial_merge2<K, V>(src + pa, na, src + pb, nb, V ? vsrc + pa : nullptr, V ? vsrc + pb : nullptr, dst, vdst, l,
+                                diag - l, o, stop);
+            o = stop;
+        }
+        c0 = c1;
+    }
+}
+
 // Level merge: persistent blocks, each over a contiguous range of work units.
 // Per unit: read its descriptor, copy its slices to shared memory, merge them
 // in tournament rounds, write the result.  Small blocks (128 threads, 2*C
@@ -764,14 +829,19 @@ __global__ void __launch_bounds__(kLvlThreads)
                   const uint32_t* __restrict__ vleaf, K* __restrict__ buf0, K* __restrict__ buf1, uint32_t* __restrict__ vbuf0,
                   uint32_t* __restrict__ vbuf1, uint32_t C, uint64_t n, uint32_t* __restrict__ status) {
     extern __shared__ uint4 smem_raw[];
-    // two buffers of C elements plus room to shift the last round's output
-    // onto the 16-byte grid of its destination
+    // two buffers of C elements plus slack: slices are staged with gaps that
+    // put each one on the 16-byte grid of its source, and the last round's
+    // output is shifted onto the 16-byte grid of its destination
     const uint32_t CP = C + kLvlPad;
     K* La = reinterpret_cast<K*>(smem_raw);
     K* Lb = La + CP;
     uint32_t* vLa = V ? reinterpret_cast<uint32_t*>(Lb + CP) : nullptr;
     uint32_t* vLb = V ? vLa + CP : nullptr;
     __shared__ UnitDesc ring[2];
+    __shared__ uint32_t s_pos[8];
+    __shared__ __align__(8) uint64_t s_bar;
+    uint32_t phase = 0;
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
 
     const uint32_t total_units = (uint32_t)ctr[kCtrUnits];
     const uint32_t per = (total_units + gridDim.x - 1) / gridDim.x;
@@ -805,26 +875,83 @@ __global__ void __launch_bounds__(kLvlThreads)
         const bool odd = D.flags >> 31;
         const K* inner = odd ? buf0 : buf1;                 // children sit at depth + 1
         const uint32_t* vinner = odd ? vbuf0 : vbuf1;
+        constexpr uint32_t VK = 16 / sizeof(K);
+        // ---- stage the slices: slice c lands at s_pos[c], with its element i at
+        // the same offset within 16 bytes as in its source, so that the aligned
+        // middle of a forward slice is one bulk copy; reversed slices and the
+        // unaligned ends are copied element by element (cp.async)
+        if (threadIdx.x == 0) {
+            uint32_t P = 0, tx = 0;
+            for (uint32_t c = 0; c < d; c++) {
+                const uint32_t m = D.off[c + 1] - D.off[c];
+                const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (8 + c)) & 1u;
+                const K* src = (lf ? leaf : inner) + D.src[c];
+                const uint32_t lead = rv ? 0u : (uint32_t)((reinterpret_cast<uintptr_t>(src) & 15u) / sizeof(K));
+                s_pos[c] = P + lead;
+                if (!rv) {
+                    const uint32_t ib = min(m, (VK - lead) & (VK - 1u));
+                    tx += (m - ib) / VK * 16u;
+                }
+                P = (P + lead + m + VK - 1) / VK * VK;
+            }
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&s_bar, tx);
+            for (uint32_t c = 0; c < d; c++) {
+                const uint32_t m = D.off[c + 1] - D.off[c];
+                const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (8 + c)) & 1u;
+                if (rv) continue;
+                const K* src = (lf ? leaf : inner) + D.src[c];
+                const uint32_t lead = s_pos[c] % VK;
+                const uint32_t ib = min(m, (VK - lead) & (VK - 1u));
+                const uint32_t bytes = (m - ib) / VK * 16u;
+                if (bytes) bulk_copy_g2s(La + s_pos[c] + ib, src + ib, bytes, &s_bar);
+            }
+        }
+        __syncthreads();
         for (uint32_t c = 0; c < d; c++) {
-            const uint32_t o = D.off[c], m = D.off[c + 1] - o, s0 = D.src[c];
+            const uint32_t m = D.off[c + 1] - D.off[c], s0 = D.src[c], pc = s_pos[c];
             const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (8 + c)) & 1u;
             const K* srck = lf ? leaf : inner;
             const uint32_t* srcv = lf ? vleaf : vinner;
-            for (uint32_t i = threadIdx.x; i < m; i += kLvlThreads) {
-                const uint32_t g = rv ? s0 - i : s0 + i;
-                cp_async<sizeof(K)>(La + o + i, srck + g);
-                if (V) cp_async<4>(vLa + o + i, srcv + g);
+            if (rv) {
+                for (uint32_t i = threadIdx.x; i < m; i += kLvlThreads) {
+                    cp_async<sizeof(K)>(La + pc + i, srck + (s0 - i));
+                    if (V) cp_async<4>(vLa + pc + i, srcv + (s0 - i));
+                }
+            } else {
+                const uint32_t lead = pc % VK;
+                const uint32_t ib = min(m, (VK - lead) & (VK - 1u));
+                const uint32_t ie = ib + (m - ib) / VK * VK;
+                for (uint32_t i = threadIdx.x; i < ib; i += kLvlThreads) cp_async<sizeof(K)>(La + pc + i, srck + s0 + i);
+                for (uint32_t i = ie + threadIdx.x; i < m; i += kLvlThreads) cp_async<sizeof(K)>(La + pc + i, srck + s0 + i);
+                if (V)
+                    for (uint32_t i = threadIdx.x; i < m; i += kLvlThreads) cp_async<4>(vLa + pc + i, srcv + s0 + i);
             }
         }
         cp_async_commit();
         cp_async_wait<0>();
-        __syncthreads();
+        {
+            uint32_t spins = 0;
+            bool done = mbar_try_wait(&s_bar, phase);
+            while (!done && spins < kMbarSpinLimit) {
+                done = mbar_try_wait(&s_bar, phase);
+                spins++;
+            }
+            if (__syncthreads_or(!done)) {
+                // the bulk copies did not complete: report it, give them one more
+                // bounded wait, and stop (the whole block leaves together)
+                if (threadIdx.x == 0) dev_fail(status, kDevSpin);
+                for (spins = 0; !mbar_try_wait(&s_bar, phase) && spins < kMbarSpinLimit; spins++) {
+                }
+                return;
+            }
+            phase ^= 1u;
+        }
         K* out = odd ? buf1 : buf0;
         uint32_t* vout = odd ? vbuf1 : vbuf0;
         const uint32_t ob = D.out_base;
         // the last round writes element q at shift + q, where shift puts it on
         // the 16-byte grid of out[ob + q] (16-byte stores below)
-        constexpr uint32_t VK = 16 / sizeof(K);
         const uint32_t shk = (uint32_t)((reinterpret_cast<uintptr_t>(out + ob) & 15u) / sizeof(K));
         const uint32_t shv = V ? (uint32_t)((reinterpret_cast<uintptr_t>(vout + ob) & 15u) / 4u) : 0u;
         uint32_t nr = 0;
@@ -837,7 +964,8 @@ __global__ void __launch_bounds__(kLvlThreads)
             const bool last = t + 1 == nr;
             K* dk = oth + (last ? shk : 0u);
             uint32_t* dv = V ? voth + (last ? shv : 0u) : nullptr;
-            unit_round<K, V>(cur, dk, vcur, dv, D.off, d, t);
+            if (t == 0) unit_round0<K, V>(cur, dk, vcur, dv, D.off, s_pos, d);
+            else unit_round<K, V>(cur, dk, vcur, dv, D.off, d, t);
             __syncthreads();
             oth = cur; cur = dk;
             voth = vcur; vcur = dv;
