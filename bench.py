@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-arrays section")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-requests", type=int, default=160)
+    ap.add_argument("--ref-sample-log2", type=int, default=21, help="keys per oracle step of the reference arm (log2)")
     return ap.parse_args()
 
 
@@ -114,6 +115,30 @@ def gen_input(kind, n, seed):
     if kind == "perm":
         return inputs.random_permutation(n, seed)
     return inputs.random_runs_geometric(n, seed, mean=GEOM_MEAN)
+
+
+# ------------------------------------------------------------- multi-rank
+
+def rank_seed(rank: int) -> int:
+    """Seed of the array rank `rank` sorts: every rank sorts its own
+    independent array (weak scaling, no collective on the data path)."""
+    return 1000 + rank
+
+
+def job_time_ms(ms_local: float, dist=None, device=None) -> float:
+    """The job's time per step: the maximum over ranks of each rank's timed
+    region (one all_reduce MAX; the local time when running alone)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput in GKeys/s: the keys of all ranks over the job's time."""
+    return world * n_per_rank / (ms * 1e-3) / 1e9
 
 
 def time_sorts(mps, torch, d_in, d_out, ws, k, steps, warmup, stream, barrier=None):
@@ -343,7 +368,7 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    n_sample = 1 << 21
+    n_sample = 1 << args.ref_sample_log2
     a = gen_input("perm", n_sample, 1234)
     for _ in range(args.warmup):
         oracle.sort(a, k=args.k, want_tree=False)
@@ -358,10 +383,11 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "single-array sort, uint32 keys, uniform random permutation, k=%d "
-                                   "(oracle steps sort a 2^21-key sample)" % args.k,
+                                   "(oracle steps sort a 2^%d-key sample)" % (args.k, args.ref_sample_log2),
                        "n": n_sample, "k": args.k, "input": "random permutation"},
             "cpu_baseline": {"value": value, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
-                             "sample": "random permutation of 2^21 uint32 keys per step, one host core"},
+                             "sample": "random permutation of 2^%d uint32 keys per step, one host core"
+                                       % args.ref_sample_log2},
             "e2e": {"value": value, "unit": "GKeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -389,7 +415,7 @@ def run_mps(args):
     n, k = args.n, args.k
     stream = torch.cuda.current_stream(dev)
 
-    a = gen_input("perm", n, 1000 + rank)
+    a = gen_input("perm", n, rank_seed(rank))
     d_in = mps.to_device(a, dev)
     d_out = torch.empty_like(d_in)
     ws = mps.workspace(n, 4, False, max(k, 2), dev)
@@ -419,12 +445,8 @@ def run_mps(args):
         bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"} & set(clocks["reasons"])
         if not bad:
             break
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-
-    value = world * n / (ms * 1e-3) / 1e9
+    ms = job_time_ms(ms, dist if world > 1 else None, dev)
+    value = job_value(n, world, ms)
     b = 4.0
     b_alg = b * (n + 2.0 * stats["merge_cost"])
     # dominant kernel: largest share of the timed region
