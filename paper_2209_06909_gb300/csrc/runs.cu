@@ -105,13 +105,43 @@ __device__ __forceinline__ uint32_t lt_mask(const K (&v)[kDetItems + 2]) {
     return msk;
 }
 
-__device__ __forceinline__ uint4 thread_runsum(uint32_t lt, uint64_t n, uint64_t i0, const uint64_t* __restrict__ off,
-                                              uint32_t m) {
-    uint32_t s0 = 0, s1 = 1, s2 = 2, c0 = 0, c1 = 0, c2 = 0;
+// A thread's 16 elements under the automaton, for each entry state s in
+// {B, A, D}: the start masks ms[s] (bit j: element i0 + j starts a run), and
+// the summary (exit-state map, starts per entry state).  Also the directions:
+// bit j of *dm = a run starting at element i0 + j is strictly decreasing.
+// Without an array start inside the chunk, each 8-element half is one lookup
+// in lut[state * 256 + comparison bits] = start mask | exit state << 8;
+// otherwise (batches) the automaton steps element by element.
+struct ThreadRuns {
+    uint4 sum;
+    uint32_t ms[3];
+    uint32_t dm;
+};
+
+__device__ __forceinline__ ThreadRuns thread_runs(uint32_t lt, uint64_t n, uint64_t i0, const uint64_t* __restrict__ off,
+                                                  uint32_t m, const uint16_t* __restrict__ lut) {
+    ThreadRuns R;
     uint64_t nx = next_start(off, m, i0);
+    if (i0 + kDetItems <= n && nx >= i0 + kDetItems && i0 != nx) {
+        const uint32_t lo = lt & 0xFFu, hi = (lt >> 8) & 0xFFu;
+        uint32_t map = 0;
+#pragma unroll
+        for (uint32_t st = 0; st < 3; st++) {
+            const uint32_t e1 = lut[st * 256 + lo];
+            const uint32_t e2 = lut[(e1 >> 8) * 256 + hi];
+            R.ms[st] = (e1 & 0xFFu) | ((e2 & 0xFFu) << 8);
+            map |= (e2 >> 8) << (2 * st);
+        }
+        R.sum = make_uint4(map, __popc(R.ms[0]), __popc(R.ms[1]), __popc(R.ms[2]));
+        // the element after the chunk must exist and be in the same array
+        const bool tail_ok = i0 + kDetItems < n && nx != i0 + kDetItems;
+        R.dm = (lt >> 1) & (tail_ok ? 0xFFFFu : 0x7FFFu);
+        return R;
+    }
+    uint32_t s0 = 0, s1 = 1, s2 = 2, m0 = 0, m1 = 0, m2 = 0, dm = 0;
 #pragma unroll
     for (int j = 0; j < kDetItems; j++) {
-        uint64_t i = i0 + j;
+        const uint64_t i = i0 + j;
         if (i < n) {
             if (i == nx) {
                 nx = next_start(off, m, i + 1);
@@ -120,10 +150,17 @@ __device__ __forceinline__ uint4 thread_runsum(uint32_t lt, uint64_t n, uint64_t
                 const bool l = (lt >> j) & 1u;
                 s0 = step_state(s0, l); s1 = step_state(s1, l); s2 = step_state(s2, l);
             }
-            c0 += (s0 == 0); c1 += (s1 == 0); c2 += (s2 == 0);
+            m0 |= (s0 == 0 ? 1u : 0u) << j;
+            m1 |= (s1 == 0 ? 1u : 0u) << j;
+            m2 |= (s2 == 0 ? 1u : 0u) << j;
+            // descending iff the next element is in the same array and smaller
+            if (i + 1 < n && i + 1 != nx && ((lt >> (j + 1)) & 1u)) dm |= 1u << j;
         }
     }
-    return make_uint4(s0 | (s1 << 2) | (s2 << 4), c0, c1, c2);
+    R.ms[0] = m0; R.ms[1] = m1; R.ms[2] = m2;
+    R.dm = dm;
+    R.sum = make_uint4(s0 | (s1 << 2) | (s2 << 4), __popc(m0), __popc(m1), __popc(m2));
+    return R;
 }
 
 // ---- single-pass tile scan with decoupled look-back
@@ -170,7 +207,16 @@ __global__ void __launch_bounds__(kDetThreads, 5) k_detect(const K* __restrict__
     __shared__ uint32_t s_tile, s_state, s_base, s_count;
     __shared__ uint32_t s_rs[kDetTile];
     __shared__ uint8_t s_rd[kDetTile];
+    __shared__ uint16_t s_lut[3 * 256];
     if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(counters + kCtrDetTile), 1ull);
+    for (uint32_t e = threadIdx.x; e < 3 * 256; e += kDetThreads) {
+        uint32_t st = e >> 8, msk = 0;
+        for (uint32_t j = 0; j < 8; j++) {
+            st = step_state(st, ((e >> j) & 1u) != 0);
+            msk |= (st == 0 ? 1u : 0u) << j;
+        }
+        s_lut[e] = (uint16_t)(msk | (st << 8));
+    }
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint32_t tiles = (uint32_t)ceil_div(n, kDetTile);
@@ -181,9 +227,9 @@ __global__ void __launch_bounds__(kDetThreads, 5) k_detect(const K* __restrict__
         load_window(keys, n, i0, v);
         lt = lt_mask(v);
     }
-    const uint4 s = thread_runsum(lt, n, i0, off, m);
+    const ThreadRuns tr = thread_runs(lt, n, i0, off, m, s_lut);
     uint4 tot;
-    const uint4 pre = block_scan_excl<kDetThreads, false>(s, OpRunSum(), runsum_identity(), tmp, &tot);
+    const uint4 pre = block_scan_excl<kDetThreads, false>(tr.sum, OpRunSum(), runsum_identity(), tmp, &tot);
     if (threadIdx.x < 32) {
         // Look-back by warp 0: lane i reads the word of tile (window end - i).
         // The nearest published prefix ends the walk; the summaries of the
@@ -255,23 +301,15 @@ __global__ void __launch_bounds__(kDetThreads, 5) k_detect(const K* __restrict__
     }
     __syncthreads();
     const uint32_t st_in = s_state;
-    uint32_t st = map_get(pre.x, st_in);
+    const uint32_t st = map_get(pre.x, st_in);  // state entering this thread's chunk
+    uint32_t msk = st == 0 ? tr.ms[0] : (st == 1 ? tr.ms[1] : tr.ms[2]);
     uint32_t idx = runsum_count(pre, st_in);
-    uint64_t nx = next_start(off, m, i0);
-#pragma unroll
-    for (int j = 0; j < kDetItems; j++) {
-        const uint64_t i = i0 + j;
-        if (i < n) {
-            const bool reset = (i == nx);
-            if (reset) nx = next_start(off, m, i + 1);
-            st = reset ? 0u : step_state(st, (lt >> j) & 1u);
-            if (st == 0) {
-                s_rs[idx] = (uint32_t)i;
-                // descending iff the next element is in the same array and smaller
-                s_rd[idx] = (i + 1 < n && i + 1 != nx && ((lt >> (j + 1)) & 1u)) ? 1 : 0;
-                idx++;
-            }
-        }
+    while (msk) {
+        const uint32_t j = __ffs(msk) - 1;
+        msk &= msk - 1;
+        s_rs[idx] = (uint32_t)(i0 + j);
+        s_rd[idx] = (uint8_t)((tr.dm >> j) & 1u);
+        idx++;
     }
     __syncthreads();
     const uint32_t base = s_base, cnt = s_count;
@@ -346,10 +384,19 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
                     const uint64_t a2 = (uint64_t)(sp - base) + (si - base);         // 2n * a
                     const uint64_t b2 = (uint64_t)(si - base) + (rv[q + 1] - base);  // 2n * b
                     const uint64_t X = a2 << ww, Y = b2 << ww;
-                    uint64_t x = __umul64hi(X, mg), y = __umul64hi(Y, mg);
-                    uint64_t rx = X - x * d, ry = Y - y * d;
-                    while (rx >= d) { x++; rx -= d; }
-                    while (ry >= d) { y++; ry -= d; }
+                    uint64_t x, y;
+                    if ((d & (d - 1)) == 0) {
+                        // 2n a power of two: the exact quotient is a shift
+                        const uint32_t sh = (uint32_t)__ffsll((long long)d) - 1u;
+                        x = X >> sh;
+                        y = Y >> sh;
+                    } else {
+                        x = __umul64hi(X, mg);
+                        y = __umul64hi(Y, mg);
+                        uint64_t rx = X - x * d, ry = Y - y * d;
+                        while (rx >= d) { x++; rx -= d; }
+                        while (ry >= d) { y++; ry -= d; }
+                    }
                     const uint32_t h = 63u - (uint32_t)__clzll((long long)(x ^ y));
                     const uint32_t p2 = ww - h;
                     pk = (p2 + log2k - 1) / log2k;

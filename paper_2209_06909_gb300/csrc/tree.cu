@@ -126,27 +126,31 @@ MinTree make_mintree(const WsView& ws) {
 
 // ------------------------------------------------------------- masks
 
-constexpr uint64_t kBits = (1ull << 56) - 1;
-constexpr uint64_t kMaskIdentity = 255ull << 56;
+// A summary is (minimum power) << 32 | bit set of powers, bit p - 1 standing
+// for power p (powers are 1..32 for n < 2^31; power 0, an array start, has no
+// bit).  The identity has minimum 255 and no bits.
+constexpr uint64_t kMaskIdentity = 255ull << 32;
 
-__device__ __forceinline__ uint64_t below(uint32_t m) { return m >= 56 ? kBits : ((1ull << m) - 1); }
-__device__ __forceinline__ uint32_t mmin(uint64_t x) { return (uint32_t)(x >> 56); }
-__device__ __forceinline__ uint64_t melem(uint32_t p) { return (1ull << p) | ((uint64_t)p << 56); }
+// bits of the powers 1 .. m-1
+__device__ __forceinline__ uint32_t below(uint32_t m) { return m <= 1 ? 0u : (m >= 33 ? ~0u : (~0u >> (33 - m))); }
+__device__ __forceinline__ uint32_t mmin(uint64_t x) { return (uint32_t)(x >> 32); }
+__device__ __forceinline__ uint32_t mbits(uint64_t x) { return (uint32_t)x; }
+__device__ __forceinline__ uint64_t melem(uint32_t p) { return ((uint64_t)p << 32) | (p ? (1u << (p - 1)) : 0u); }
 
 // suffix-minima summary, X then Y
 struct OpF {
     __device__ unsigned long long operator()(unsigned long long X, unsigned long long Y) const {
-        uint32_t mx = mmin(X), my = mmin(Y);
-        uint64_t bits = (Y & kBits) | (X & kBits & below(my));
-        return bits | ((uint64_t)(mx < my ? mx : my) << 56);
+        const uint32_t mx = mmin(X), my = mmin(Y);
+        const uint32_t bits = mbits(Y) | (mbits(X) & below(my));
+        return ((uint64_t)(mx < my ? mx : my) << 32) | bits;
     }
 };
 // prefix-minima summary, X then Y
 struct OpG {
     __device__ unsigned long long operator()(unsigned long long X, unsigned long long Y) const {
-        uint32_t mx = mmin(X), my = mmin(Y);
-        uint64_t bits = (X & kBits) | (Y & kBits & below(mx));
-        return bits | ((uint64_t)(mx < my ? mx : my) << 56);
+        const uint32_t mx = mmin(X), my = mmin(Y);
+        const uint32_t bits = mbits(X) | (mbits(Y) & below(mx));
+        return ((uint64_t)(mx < my ? mx : my) << 32) | bits;
     }
 };
 // the same prefix-minima summary for a reverse-order scan: a follows b in scan order
@@ -276,15 +280,14 @@ __global__ void __launch_bounds__(kMaskThreads, 3) k_mask_apply(const uint8_t* _
     unsigned long long sg = block_scan_excl<kMaskThreads, true>(g, OpGRev(), kMaskIdentity, tmp, nullptr);
     pf = OpF()(fpre[blockIdx.x], pf);
     sg = OpG()(sg, gsuf[blockIdx.x]);
-    // bit sets of the right-side summaries per item (right to left); powers are
-    // at most 32, so bits 1..32 of a summary fit in 32 bits
+    // bit sets of the right-side summaries per item (right to left)
     uint32_t rb[kMaskItems];
     uint32_t d0 = 0;  // depth of run 0 (thread holding boundary 1 only)
 #pragma unroll
     for (int q = kMaskItems - 1; q >= 0; q--) {
-        rb[q] = (uint32_t)((sg & kBits) >> 1);
+        rb[q] = mbits(sg);
         const unsigned long long e = elem(q);
-        if (q == 0 && b0 == 0) d0 = (uint32_t)__popcll(OpG()(e, sg) & kBits & ~1ull);
+        if (q == 0 && b0 == 0) d0 = (uint32_t)__popc(mbits(OpG()(e, sg)));
         sg = OpG()(e, sg);
     }
     unsigned long long cost = 0, nodes = 0;
@@ -296,15 +299,15 @@ __global__ void __launch_bounds__(kMaskThreads, 3) k_mask_apply(const uint8_t* _
         if (b < nb) {
             const uint32_t j = b + 1;
             const uint32_t p = mmin(e);
-            const uint64_t left = pf & kBits & ~1ull, right = (uint64_t)rb[q] << 1;
-            const uint32_t depth = __popcll((left | right) & below(p));
+            const uint32_t left = mbits(pf), right = rb[q];
+            const uint32_t depth = __popc((left | right) & below(p));
             // power 0 marks an array start inside a batch: never a node boundary
-            const uint32_t start = (p == 0 || ((left >> p) & 1ull)) ? 0u : 1u;
+            const uint32_t start = (p == 0 || ((left >> (p - 1)) & 1u)) ? 0u : 1u;
             const uint32_t query = start && (depth == 0 || p < vskip) ? 1u : 0u;
             word[q >> 2] |= (depth | (query << 6) | (start << 7)) << (8 * (q & 3));
             nodes += start;
-            const uint64_t incl = OpF()(pf, e) & kBits & ~1ull;
-            const uint32_t dj = (uint32_t)__popcll(incl | right);  // depth of run j
+            const uint32_t incl = mbits(OpF()(pf, e));
+            const uint32_t dj = (uint32_t)__popc(incl | right);  // depth of run j
             cost += (unsigned long long)dj * (rv[q + 2] - rv[q + 1]);
             if (j == 1) {
                 cost += (unsigned long long)d0 * (rv[1] - rv[0]);
