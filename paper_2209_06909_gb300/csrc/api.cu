@@ -88,7 +88,7 @@ struct Plan {
         o_split = take((size_t)(unit_cap + 1) * k * 4);
         o_udesc = take((size_t)unit_cap * 128);
         o_ufirst = take((size_t)unit_cap * 4);
-        o_ptiles = take((size_t)(unit_cap / 4096 + 2) * 4);
+        o_ptiles = take((size_t)(unit_cap / kPackTile + 2) * 4);
         o_hist = take(mask_tiles * kMaxLevels * 4);
         o_bprm = take((size_t)2 * std::max<uint32_t>(m, 1) * 8);
         o_ktmp = take(n * kb);

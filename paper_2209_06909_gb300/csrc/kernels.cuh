@@ -7,7 +7,8 @@
 
 namespace mps {
 
-constexpr int kDetTile = 4096;     // elements per run-detection tile
+constexpr int kDetTile = 8192;     // elements per run-detection tile
+constexpr int kPackTile = 512;     // splitter intervals per unit-packing tile
 constexpr int kMaskTile = 4096;    // boundaries per mask-scan tile
 constexpr int kMaxLevels = 64;     // bound on distinct powers (P <= 32 for n < 2^31)
 constexpr int kMinTreeLevels = 8;  // fan-out 32 min-tree over the powers

@@ -582,8 +582,7 @@ static_assert(sizeof(UnitDesc) == 128, "UnitDesc layout");
 // in the children).  With spacing ts = c/(2k) no interval exceeds c/2, so a
 // unit stays below q + c/2 = c elements and averages about c/2.
 constexpr int kPackThreads = 256;
-constexpr int kPackItems = 16;
-constexpr int kPackTile = kPackThreads * kPackItems;
+constexpr int kPackItems = kPackTile / kPackThreads;
 
 __device__ __forceinline__ uint32_t interval_rank(const uint32_t* __restrict__ tab, uint32_t i, int k, uint32_t d) {
     uint32_t r = 0;

@@ -32,7 +32,7 @@ namespace mps {
 namespace {
 
 constexpr int kDetThreads = 256;
-constexpr int kDetItems = 16;
+constexpr int kDetItems = 32;
 static_assert(kDetThreads * kDetItems == kDetTile, "detection tile");
 
 // Smallest array start >= x among off[0..m] (a batch of m arrays laid end to
@@ -94,23 +94,23 @@ __device__ __forceinline__ void load_window(const K* __restrict__ keys, uint64_t
     v[kDetItems + 1] = (i0 + kDetItems < n) ? keys[i0 + kDetItems] : K(0);
 }
 
-// Bit j (j = 0..16) = key[i0 + j] < key[i0 + j - 1]: the comparisons that
-// drive the automaton for the thread's 16 elements, plus one more for the
+// Bit j (j = 0..32) = key[i0 + j] < key[i0 + j - 1]: the comparisons that
+// drive the automaton for the thread's 32 elements, plus one more for the
 // direction of a run that starts at its last element.
 template <typename K>
-__device__ __forceinline__ uint32_t lt_mask(const K (&v)[kDetItems + 2]) {
-    uint32_t msk = 0;
+__device__ __forceinline__ uint64_t lt_mask(const K (&v)[kDetItems + 2]) {
+    uint64_t msk = 0;
 #pragma unroll
-    for (int j = 0; j <= kDetItems; j++) msk |= (v[1 + j] < v[j] ? 1u : 0u) << j;
+    for (int j = 0; j <= kDetItems; j++) msk |= (uint64_t)(v[1 + j] < v[j] ? 1u : 0u) << j;
     return msk;
 }
 
-// A thread's 16 elements under the automaton, for each entry state s in
+// A thread's 32 elements under the automaton, for each entry state s in
 // {B, A, D}: the start masks ms[s] (bit j: element i0 + j starts a run), and
 // the summary (exit-state map, starts per entry state).  Also the directions:
 // bit j of *dm = a run starting at element i0 + j is strictly decreasing.
-// Without an array start inside the chunk, each 8-element half is one lookup
-// in lut[state * 256 + comparison bits] = start mask | exit state << 8;
+// Without an array start inside the chunk, each 8-element quarter is one
+// lookup in lut[state * 256 + comparison bits] = start mask | exit state << 8;
 // otherwise (batches) the automaton steps element by element.
 struct ThreadRuns {
     uint4 sum;
@@ -118,24 +118,28 @@ struct ThreadRuns {
     uint32_t dm;
 };
 
-__device__ __forceinline__ ThreadRuns thread_runs(uint32_t lt, uint64_t n, uint64_t i0, const uint64_t* __restrict__ off,
+__device__ __forceinline__ ThreadRuns thread_runs(uint64_t lt, uint64_t n, uint64_t i0, const uint64_t* __restrict__ off,
                                                   uint32_t m, const uint16_t* __restrict__ lut) {
     ThreadRuns R;
     uint64_t nx = next_start(off, m, i0);
     if (i0 + kDetItems <= n && nx >= i0 + kDetItems && i0 != nx) {
-        const uint32_t lo = lt & 0xFFu, hi = (lt >> 8) & 0xFFu;
         uint32_t map = 0;
 #pragma unroll
         for (uint32_t st = 0; st < 3; st++) {
-            const uint32_t e1 = lut[st * 256 + lo];
-            const uint32_t e2 = lut[(e1 >> 8) * 256 + hi];
-            R.ms[st] = (e1 & 0xFFu) | ((e2 & 0xFFu) << 8);
-            map |= (e2 >> 8) << (2 * st);
+            uint32_t s = st, msk = 0;
+#pragma unroll
+            for (int q = 0; q < kDetItems / 8; q++) {
+                const uint32_t e = lut[s * 256 + (uint32_t)((lt >> (8 * q)) & 0xFFu)];
+                msk |= (e & 0xFFu) << (8 * q);
+                s = e >> 8;
+            }
+            R.ms[st] = msk;
+            map |= s << (2 * st);
         }
         R.sum = make_uint4(map, __popc(R.ms[0]), __popc(R.ms[1]), __popc(R.ms[2]));
         // the element after the chunk must exist and be in the same array
         const bool tail_ok = i0 + kDetItems < n && nx != i0 + kDetItems;
-        R.dm = (lt >> 1) & (tail_ok ? 0xFFFFu : 0x7FFFu);
+        R.dm = (uint32_t)(lt >> 1) & (tail_ok ? 0xFFFFFFFFu : 0x7FFFFFFFu);
         return R;
     }
     uint32_t s0 = 0, s1 = 1, s2 = 2, m0 = 0, m1 = 0, m2 = 0, dm = 0;
@@ -165,8 +169,8 @@ __device__ __forceinline__ ThreadRuns thread_runs(uint32_t lt, uint64_t n, uint6
 
 // ---- single-pass tile scan with decoupled look-back
 // Each tile publishes a 64-bit word: flag (bits 62-63) and either its own
-// summary (flag 1: map in bits 0-5, B-counts per entry state in 13-bit fields
-// at 6, 19, 32) or its inclusive prefix (flag 2: state after the tile in bits
+// summary (flag 1: map in bits 0-5, B-counts per entry state in 14-bit fields
+// at 6, 20, 34) or its inclusive prefix (flag 2: state after the tile in bits
 // 0-1, runs up to and including the tile in bits 2-33).  Tile 0 starts in
 // state B, so a prefix needs only the one state and count.
 constexpr uint64_t kFlagAgg = 1ull << 62;
@@ -182,12 +186,13 @@ __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
 __device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
 }
+static_assert(kDetTile < (1 << 14), "tile counts fit 14 bits");
 __device__ __forceinline__ uint64_t pack_agg(uint4 a) {
-    return kFlagAgg | (uint64_t)a.x | ((uint64_t)a.y << 6) | ((uint64_t)a.z << 19) | ((uint64_t)a.w << 32);
+    return kFlagAgg | (uint64_t)a.x | ((uint64_t)a.y << 6) | ((uint64_t)a.z << 20) | ((uint64_t)a.w << 34);
 }
 __device__ __forceinline__ uint4 unpack_agg(uint64_t w) {
-    return make_uint4((uint32_t)(w & 63u), (uint32_t)((w >> 6) & 0x1FFFu), (uint32_t)((w >> 19) & 0x1FFFu),
-                      (uint32_t)((w >> 32) & 0x1FFFu));
+    return make_uint4((uint32_t)(w & 63u), (uint32_t)((w >> 6) & 0x3FFFu), (uint32_t)((w >> 20) & 0x3FFFu),
+                      (uint32_t)((w >> 34) & 0x3FFFu));
 }
 __device__ __forceinline__ uint32_t runsum_count(uint4 a, uint32_t st) { return st == 0 ? a.y : (st == 1 ? a.z : a.w); }
 
@@ -199,7 +204,7 @@ __device__ __forceinline__ uint32_t runsum_count(uint4 a, uint32_t st) { return 
 // its run starts and directions, staged in shared memory, as one contiguous
 // coalesced range.
 template <typename K>
-__global__ void __launch_bounds__(kDetThreads, 5) k_detect(const K* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
+__global__ void __launch_bounds__(kDetThreads, 4) k_detect(const K* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
                                                         uint32_t m, uint64_t* __restrict__ tile_state,
                                                         uint64_t* __restrict__ counters, uint32_t* __restrict__ run_starts,
                                                         uint8_t* __restrict__ run_desc) {
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(kDetThreads, 5) k_detect(const K* __restrict__
     const uint32_t tile = s_tile;
     const uint32_t tiles = (uint32_t)ceil_div(n, kDetTile);
     const uint64_t i0 = (uint64_t)tile * kDetTile + (uint64_t)threadIdx.x * kDetItems;
-    uint32_t lt;
+    uint64_t lt;
     {
         K v[kDetItems + 2];
         load_window(keys, n, i0, v);
@@ -381,23 +386,23 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
                 }
                 if (i >= 1 && i < r && !arr_start) {
                     const uint64_t d = 2 * nn;
-                    const uint64_t a2 = (uint64_t)(sp - base) + (si - base);         // 2n * a
-                    const uint64_t b2 = (uint64_t)(si - base) + (rv[q + 1] - base);  // 2n * b
-                    const uint64_t X = a2 << ww, Y = b2 << ww;
-                    uint64_t x, y;
+                    const uint32_t a2 = (sp - base) + (si - base);         // 2n * a  (< 2n <= 2^32)
+                    const uint32_t b2 = (si - base) + (rv[q + 1] - base);  // 2n * b
+                    uint32_t h;
                     if ((d & (d - 1)) == 0) {
-                        // 2n a power of two: the exact quotient is a shift
-                        const uint32_t sh = (uint32_t)__ffsll((long long)d) - 1u;
-                        x = X >> sh;
-                        y = Y >> sh;
+                        // 2n a power of two: x = a2 * 2^w / 2n is a shift, and x, y < 2^w <= 2^31
+                        const int sh = (int)ww - ((int)__ffsll((long long)d) - 1);
+                        const uint32_t x = sh >= 0 ? a2 << sh : a2 >> -sh;
+                        const uint32_t y = sh >= 0 ? b2 << sh : b2 >> -sh;
+                        h = 31u - (uint32_t)__clz((int)(x ^ y));
                     } else {
-                        x = __umul64hi(X, mg);
-                        y = __umul64hi(Y, mg);
+                        const uint64_t X = (uint64_t)a2 << ww, Y = (uint64_t)b2 << ww;
+                        uint64_t x = __umul64hi(X, mg), y = __umul64hi(Y, mg);
                         uint64_t rx = X - x * d, ry = Y - y * d;
                         while (rx >= d) { x++; rx -= d; }
                         while (ry >= d) { y++; ry -= d; }
+                        h = 63u - (uint32_t)__clzll((long long)(x ^ y));
                     }
-                    const uint32_t h = 63u - (uint32_t)__clzll((long long)(x ^ y));
                     const uint32_t p2 = ww - h;
                     pk = (p2 + log2k - 1) / log2k;
                     bits |= 1ull << pk;
