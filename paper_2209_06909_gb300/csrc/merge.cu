@@ -219,16 +219,6 @@ __device__ __forceinline__ uint32_t odd_chunk(uint32_t m) {
     return per | 1u;
 }
 
-// Scan element of a level: bit 31 = a smaller power was seen (the group of
-// equal powers restarts), bits 16..30 = power-p boundaries in the current
-// group (so far), bits 0..15 = smaller-power boundaries (kept for later levels).
-struct OpLevel {
-    __device__ uint32_t operator()(uint32_t X, uint32_t Y) const {
-        const uint32_t kept = (X + Y) & 0xFFFFu;
-        return (Y & 0x80000000u) ? ((Y & 0xFFFF0000u) | kept)
-                                 : (((X & 0xFFFF0000u) + (Y & 0x7FFF0000u)) | kept);
-    }
-};
 struct OpMax2 {
     __device__ uint4 operator()(uint4 X, uint4 Y) const { return make_uint4(max(X.x, Y.x), max(X.y, Y.y), 0u, 0u); }
 };
@@ -365,30 +355,20 @@ __global__ void __launch_bounds__(kFusedThreads)
             per = odd_chunk(na);
             e0 = min(na, tid * per);
             e1 = min(na, e0 + per);
-            // group index q of every power-p boundary (segmented count) and the
-            // positions of the smaller powers that stay for later levels
-            uint32_t acc = 0;
-            for (uint32_t e = e0; e < e1; e++) {
-                const uint32_t pw = be_pow(bl0[e]);
-                acc = OpLevel()(acc, pw < p ? 0x80000001u : (pw == p ? 0x00010000u : 0u));
-            }
-            if (tid == 0) s_rmask = 0;
-            uint32_t tot;
-            const uint32_t pre = block_scan_excl<kFusedThreads, false>(acc, OpLevel(), 0u, stmp, &tot);
-            const uint32_t nkeep = tot & 0xFFFFu;
-            if (nkeep == na) continue;  // no boundary of power p in this subtree
-            // round of each boundary: ctz(q) for power p (the bracket round of
-            // the node's tournament), T for smaller powers (a delimiter); the
-            // kept boundaries wait in registers until the level is merged
+            // Round of each boundary: for power p, ctz(q) with q its index in the
+            // group of power-p boundaries that forms one node (the bracket round
+            // of the node's tournament); T for a smaller power (a delimiter).
+            // The list holds no power above p any more, so a group's boundaries
+            // are adjacent: q is found by looking back at most k - 1 entries.
+            // Kept (smaller-power) boundaries wait in registers until the
+            // level is merged.
             uint32_t keep[kKeepMax];
             uint32_t nk = 0, rmask = 0;
-            uint32_t run = pre;
             for (uint32_t e = e0; e < e1; e++) {
                 const uint32_t v = bl0[e];
-                const uint32_t pw = be_pow(v);
-                run = OpLevel()(run, pw < p ? 0x80000001u : (pw == p ? 0x00010000u : 0u));
-                if (pw == p) {
-                    const uint32_t q = (run >> 16) & 0x7FFFu;
+                if (be_pow(v) == p) {
+                    uint32_t q = 1;
+                    while (q < 8u && e >= q && be_pow(bl0[e - q]) == p) q++;
                     const uint32_t rd = min((uint32_t)__ffs(q) - 1u, T - 1u);
                     bl0[e] = (v & 0x00FFFFFFu) | (rd << 24);
                     rmask |= 1u << rd;
@@ -397,7 +377,10 @@ __global__ void __launch_bounds__(kFusedThreads)
                     keep[nk++] = v & 0x00FFFFFFu;
                 }
             }
-            const uint32_t kpos = pre & 0xFFFFu;
+            if (tid == 0) s_rmask = 0;
+            uint32_t nkeep;
+            const uint32_t kpos = block_sum_excl<kFusedThreads>(nk, stmp, &nkeep);
+            if (nkeep == na) continue;  // no boundary of power p in this subtree
             if (rmask) atomicOr(&s_rmask, rmask);
             __syncthreads();
             const uint32_t rounds = s_rmask;
