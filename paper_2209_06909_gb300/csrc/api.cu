@@ -125,6 +125,7 @@ struct Plan {
         w.pack_tiles = reinterpret_cast<uint32_t*>(b + o_ptiles);
         w.unit_cap = unit_cap;
         w.canon_idx = reinterpret_cast<uint32_t*>(b + o_canon);
+        w.cand_cap = (uint32_t)(rmax + 1);
         w.hist = reinterpret_cast<uint32_t*>(b + o_hist);
         w.keys_tmp = b + o_ktmp;
         w.vals_tmp = vals ? reinterpret_cast<uint32_t*>(b + o_vtmp) : nullptr;

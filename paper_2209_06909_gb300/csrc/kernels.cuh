@@ -32,6 +32,7 @@ enum : int {
     kCtrMaxRun = 203,   // longest run (elements)
     kCtrMaxLen = 204,   // longest array of a batch (elements)
     kCtrDetTile = 205,  // next run-detection tile to take
+    kCtrCand = 206,     // node-pass candidates listed by the mask pass
     kCtrWords = 256
 };
 
@@ -76,7 +77,9 @@ struct WsView {
     uint32_t* unit_first;          // first splitter interval of each packed work unit
     uint32_t* pack_tiles;          // per-tile counts / offsets of the packing scan
     uint32_t unit_cap;
-    uint32_t* canon_idx;           // dump: canonical index of each node start
+    uint32_t* canon_idx;           // dump: canonical index of each node start; before that, the
+                                   // node pass's candidate list (boundary indices)
+    uint32_t cand_cap;             // entries of canon_idx
     uint32_t* hist;                // dump: per-tile power histograms
     void* keys_tmp;
     uint32_t* vals_tmp;

@@ -33,25 +33,44 @@ namespace {
 
 // ------------------------------------------------------------- min-tree
 
-__global__ void __launch_bounds__(1024) k_mintree(const uint8_t* __restrict__ src, uint32_t src_len, uint8_t* __restrict__ dst1,
-                                                  uint8_t* __restrict__ dst2, uint32_t dst2_pad_from, uint32_t dst2_pad_to) {
-    __shared__ uint32_t wmin[32];
-    uint32_t i = blockIdx.x * 1024u + threadIdx.x;
-    uint32_t v = i < src_len ? src[i] : 255u;
-    v = __reduce_min_sync(0xffffffffu, v);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        dst1[blockIdx.x * 32u + warp] = (uint8_t)v;
-        wmin[warp] = v;
+// Two levels of the min-tree at once: dst1[e] = min(src[32e .. 32e+31]) and
+// dst2[e] = min(src[1024e .. 1024e+1023]), each written up to its padded
+// length (a multiple of 32, 255 past the data).  A thread reads 16 source
+// bytes; a block covers 4096 (128 dst1 and 4 dst2 entries).
+__global__ void __launch_bounds__(256) k_mintree(const uint8_t* __restrict__ src, uint32_t src_len, uint8_t* __restrict__ dst1,
+                                                 uint32_t dst1_len, uint8_t* __restrict__ dst2, uint32_t dst2_len) {
+    __shared__ uint32_t wmin[8];
+    const uint32_t i0 = (blockIdx.x * 256u + threadIdx.x) * 16u;
+    uint32_t m = 255u;
+    if (i0 < src_len) {
+        const uint4 w = *reinterpret_cast<const uint4*>(src + i0);
+        uint32_t x = __vminu4(__vminu4(w.x, w.y), __vminu4(w.z, w.w));
+        if (i0 + 16u > src_len) {  // bytes past the data count as 255
+            const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+            x = 0xFFFFFFFFu;
+            for (uint32_t q = 0; q < 16u && i0 + q < src_len; q++) {
+                const uint32_t b = (wd[q >> 2] >> (8 * (q & 3))) & 0xFFu;
+                x = __vminu4(x, b * 0x01010101u);
+            }
+        }
+        x = __vminu4(x, x >> 16);
+        x = __vminu4(x, x >> 8);
+        m = x & 0xFFu;
     }
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t m1 = min(m, __shfl_xor_sync(0xffffffffu, m, 1));  // 32 source bytes
+    const uint32_t e1 = (blockIdx.x * 256u + threadIdx.x) >> 1;
+    if (!(lane & 1u) && e1 < dst1_len) dst1[e1] = (uint8_t)m1;
     if (dst2 == nullptr) return;
+    const uint32_t wm = __reduce_min_sync(0xffffffffu, m1);  // 512 source bytes
+    if (lane == 0) wmin[warp] = wm;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t w = __reduce_min_sync(0xffffffffu, wmin[lane]);
-        if (lane == 0) dst2[blockIdx.x] = (uint8_t)w;
-        if (blockIdx.x == 0)
-            for (uint32_t q = dst2_pad_from + lane; q < dst2_pad_to; q += 32) dst2[q] = 255;
+    if (threadIdx.x < 4) {
+        const uint32_t e2 = blockIdx.x * 4u + threadIdx.x;
+        if (e2 < dst2_len) dst2[e2] = (uint8_t)min(wmin[2 * threadIdx.x], wmin[2 * threadIdx.x + 1]);
     }
+    if (blockIdx.x == 0)
+        for (uint32_t q = gridDim.x * 4u + threadIdx.x; q < dst2_len; q += 256u) dst2[q] = 255;
 }
 
 struct MinTree {
@@ -238,7 +257,8 @@ __global__ void __launch_bounds__(kMaskThreads, 3) k_mask_apply(const uint8_t* _
                                                              const unsigned long long* __restrict__ fpre,
                                                              const unsigned long long* __restrict__ gsuf,
                                                              uint8_t* __restrict__ node_info, uint8_t* __restrict__ leaf_depth,
-                                                             uint64_t n_single, uint32_t log2k, uint32_t tmax) {
+                                                             uint64_t n_single, uint32_t log2k, uint32_t tmax,
+                                                             uint32_t* __restrict__ cand, uint32_t cand_cap) {
     static_assert(kMaskItems == 16, "one 16-byte word of node_info per thread");
     __shared__ unsigned long long tmp[kMaskThreads / 32 + 1];
     const uint32_t r = (uint32_t)ctr[kCtrR];
@@ -318,6 +338,34 @@ __global__ void __launch_bounds__(kMaskThreads, 3) k_mask_apply(const uint8_t* _
         pf = OpF()(pf, e);
     }
     if (live) *reinterpret_cast<uint4*>(node_info + b0) = make_uint4(word[0], word[1], word[2], word[3]);
+    // append the marked starts to the candidate list of the node pass (one
+    // atomic per warp that has any)
+    {
+        uint32_t qm = 0;  // bit q: boundary b0 + q is marked
+#pragma unroll
+        for (int q = 0; q < kMaskItems; q++) qm |= ((word[q >> 2] >> (8 * (q & 3) + 6)) & 1u) << q;
+        const uint32_t cnt = __popc(qm);
+        const uint32_t lane = threadIdx.x & 31u;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+        if (wtot) {
+            uint32_t wbase = 0;
+            if (lane == 31) wbase = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrCand), (unsigned long long)wtot);
+            wbase = __shfl_sync(0xffffffffu, wbase, 31);
+            uint32_t pos = wbase + incl - cnt;
+            while (qm) {
+                const uint32_t q = __ffs(qm) - 1;
+                qm &= qm - 1;
+                if (pos < cand_cap) cand[pos] = b0 + q + 1;
+                pos++;
+            }
+        }
+    }
     cost = block_reduce<kMaskThreads>(cost, OpAddU64(), 0ull, tmp);
     nodes = block_reduce<kMaskThreads>(nodes, OpAddU64(), 0ull, tmp);
     if (threadIdx.x == 0) {
@@ -354,29 +402,31 @@ __device__ __forceinline__ bool node_shape(const MinTree& T, const uint8_t* P, u
 }
 
 // Finds the nodes larger than T_max among the node starts that k_mask_apply
-// marked for a query (16 boundaries per 16-byte load; unmarked words are
-// skipped whole).  A large node becomes a level-merge record and appends each
+// marked for a query and listed in `cand` (boundary indices j).  A large node becomes a level-merge record and appends each
 // child that is an inner node of at most T_max elements to the list of fused
 // subtrees (its parent is large, so it is maximal); a small root is a fused
 // subtree too.
 __global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tmax,
                                                    const uint32_t* __restrict__ rs, const uint8_t* __restrict__ node_info,
                                                    uint64_t* __restrict__ ctr, LevelNode* __restrict__ nodes_raw, uint32_t nodes_cap,
-                                                   uint4* __restrict__ fused_list, uint32_t fused_cap) {
+                                                   uint4* __restrict__ fused_list, uint32_t fused_cap,
+                                                   const uint32_t* __restrict__ cand, uint32_t cand_cap) {
     const uint8_t* P = T.lv[0];
     uint32_t* status = reinterpret_cast<uint32_t*>(ctr + kCtrStatus);
     const uint32_t r = (uint32_t)ctr[kCtrR];
-    const uint32_t nb = r - 1;
-    const uint32_t words = (nb + 15) >> 4;
-    for (uint32_t wi = blockIdx.x * blockDim.x + threadIdx.x; wi < words; wi += gridDim.x * blockDim.x) {
-        const uint4 w4 = reinterpret_cast<const uint4*>(node_info)[wi];
-        if (!((w4.x | w4.y | w4.z | w4.w) & 0x40404040u)) continue;
-        const uint32_t wd[4] = {w4.x, w4.y, w4.z, w4.w};
-        for (uint32_t q = 0; q < 16; q++) {
-            const uint32_t info = (wd[q >> 2] >> (8 * (q & 3))) & 0xFFu;
-            const uint32_t b = wi * 16 + q;
-            if (!(info & 0x40) || b >= nb) continue;
-            const uint32_t j = b + 1;
+    const uint64_t ncand = ctr[kCtrCand];
+    if (ncand > cand_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) dev_fail(status, kDevCapacity);
+        return;
+    }
+    for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < (uint32_t)ncand; ci += gridDim.x * blockDim.x) {
+        {
+            const uint32_t j = cand[ci];
+            if (j == 0 || j >= r) {
+                dev_fail(status, kDevRange);
+                continue;
+            }
+            const uint32_t info = node_info[j - 1];
             const uint32_t v = P[j];
             const uint32_t depth = info & 0x3F;
             const uint32_t L = nsv_left(T, j, v, true);
@@ -559,11 +609,12 @@ __global__ void __launch_bounds__(256) k_dump_nodes(MinTree T, uint32_t r, int k
 void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st) {
     // level t has ws.lv_len[t] valid entries; padding of 255 up to a multiple of 32
     for (int t = 0; t + 1 < ws.nlv; t += 2) {
-        uint32_t src_len = ws.lv_len[t];
-        uint32_t blocks = (src_len + 1023) / 1024;
+        const uint32_t src_len = ws.lv_len[t];
+        const uint32_t blocks = (src_len + 4095) / 4096;
+        const uint32_t len1 = (uint32_t)((ceil_div(src_len, 32) + 31) / 32 * 32);
+        const uint32_t len2 = (uint32_t)((ceil_div(src_len, 1024) + 31) / 32 * 32);
         uint8_t* dst2 = (t + 2 < ws.nlv) ? ws.lv[t + 2] : nullptr;
-        uint32_t pad_from = blocks, pad_to = (blocks + 31) / 32 * 32;
-        k_mintree<<<blocks, 1024, 0, st>>>(ws.lv[t], src_len, ws.lv[t + 1], dst2, pad_from, pad_to);
+        k_mintree<<<blocks, 256, 0, st>>>(ws.lv[t], src_len, ws.lv[t + 1], len1, dst2, len2);
         g_launches += 1;
     }
 }
@@ -576,15 +627,15 @@ void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, uint64_t n, i
     k_mask_scan<<<1, 1024, 0, st>>>(ws.mt_f, ws.mt_g, tiles, ws.mt_fpre, ws.mt_gsuf);
     const uint32_t log2k = k == 2 ? 1u : (k == 4 ? 2u : 3u);
     k_mask_apply<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.run_starts, ws.mt_fpre, ws.mt_gsuf, ws.node_info,
-                                                  dump_leaf ? leaf_depth : nullptr, ws.batch_off ? 0ull : n, log2k, tmax);
+                                                  dump_leaf ? leaf_depth : nullptr, ws.batch_off ? 0ull : n, log2k, tmax,
+                                                  ws.canon_idx, ws.cand_cap);
     g_launches += 3;
 }
 
 void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st) {
-    uint32_t words = (uint32_t)ceil_div(r - 1, 16);
-    uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(std::max<uint32_t>(words, 1), 256), 152 * 8);
-    k_node_pass<<<blocks, 256, 0, st>>>(make_mintree(ws), k, tmax, ws.run_starts, ws.node_info,
-                                                              ws.counters, ws.nodes_raw, ws.nodes_cap, ws.fused_list, ws.fused_cap);
+    (void)r;
+    k_node_pass<<<152 * 4, 256, 0, st>>>(make_mintree(ws), k, tmax, ws.run_starts, ws.node_info, ws.counters, ws.nodes_raw,
+                                         ws.nodes_cap, ws.fused_list, ws.fused_cap, ws.canon_idx, ws.cand_cap);
     g_launches += 1;
 }
 
