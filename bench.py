@@ -300,7 +300,7 @@ def bench_serve(mps, torch, dev, stream, nreq=160):
     cap = nreq / serial_s  # requests per second the serial server sustains
     pool = torch.empty(64 << 30, dtype=torch.uint8, device=dev)
     sweep = []
-    for factor in (0.5, 1.0, 4.0):
+    for factor in (0.5, 1.0, 4.0, 8.0):
         rate = cap * factor
         gaps = np.random.default_rng(9).exponential(1.0 / rate, nreq)
         arrive = np.cumsum(gaps)

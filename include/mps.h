@@ -174,9 +174,10 @@ mps_status mps_batch_graph_destroy(mps_batch_graph* g);
  * device buffers they own (inputs must stay unchanged and outputs untouched
  * until the request completes).  A worker thread admits pending requests
  * against a device memory budget -- the pool the caller hands over at
- * creation -- groups consecutive requests of the same kind into a batch,
- * stages their inputs in the pool, sorts the batch (mps_sort_batch's kernels,
- * no host synchronisation), and copies each result to its client's output.
+ * creation -- gathers the pending requests of the oldest request's kind into
+ * a batch, stages their inputs in the pool, sorts the batch (mps_sort_batch's
+ * kernels, no host synchronisation), and copies each result to its client's
+ * output.
  * Up to max_inflight batches run at once on separate streams, so requests
  * that arrive while others are on the GPU are admitted as pool memory and a
  * stream free up, and their work overlaps on the device.  Each result is

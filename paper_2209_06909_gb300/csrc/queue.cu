@@ -2,11 +2,12 @@
 //
 // Clients submit sort requests (device input and output buffers they own).
 // A worker thread admits pending requests against a device memory budget --
-// a pool the caller hands over at creation -- groups consecutive requests of
+// a pool the caller hands over at creation -- groups pending requests of
 // one kind (uint32 keys, or uint64 keys with uint32 payloads) into a batch,
-// copies their inputs into pool memory laid end to end, sorts the batch with
-// the batch path (no host synchronisation inside), copies every result to its
-// client's output buffer, and records an event.  Several batches are in
+// gathers their inputs into pool memory laid end to end (one kernel), sorts
+// the batch with the batch path (no host synchronisation inside), scatters
+// every result to its client's output buffer (one kernel), and records an
+// event.  Several batches are in
 // flight at once on separate streams, so requests that arrive while others
 // run are admitted as soon as pool memory and a stream free up, and their
 // work overlaps on the device.  A finished batch releases its pool memory.
@@ -33,6 +34,71 @@ mps_status batch_dispatch(const void* keys_in, const uint32_t* vals_in, void* ke
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// Per request of a batch: its buffers (keys in, payload in, keys out, payload out).
+struct ReqPtrs {
+    const void* kin;
+    const uint32_t* vin;
+    void* kout;
+    uint32_t* vout;
+};
+
+constexpr uint32_t kSegTile = 4096;  // batch elements per block of the copy kernels
+
+// Moves every request's elements between its own buffers and the batch's
+// buffers laid end to end (off[i] = first batch element of request i):
+// GATHER copies request inputs into kin/vin, otherwise batch outputs
+// kout/vout are scattered to the requests.  A block takes kSegTile batch
+// elements, finds the request holding its first one and walks forward.
+template <typename K, bool V, bool GATHER>
+__global__ void __launch_bounds__(256) k_copy_requests(const ReqPtrs* __restrict__ tab, const uint64_t* __restrict__ off,
+                                                       uint32_t m, uint64_t n, K* __restrict__ kin, uint32_t* __restrict__ vin,
+                                                       const K* __restrict__ kout, const uint32_t* __restrict__ vout) {
+    for (uint64_t x0 = (uint64_t)blockIdx.x * kSegTile; x0 < n; x0 += (uint64_t)gridDim.x * kSegTile) {
+        const uint64_t x1 = min(n, x0 + kSegTile);
+        uint32_t lo = 0, hi = m;  // last request with off[i] <= x0
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (off[mid] <= x0) lo = mid; else hi = mid;
+        }
+        for (uint32_t i = lo; i < m && off[i] < x1; i++) {
+            const uint64_t a = max(off[i], x0), b = min(off[i + 1], x1);
+            const ReqPtrs R = tab[i];
+            for (uint64_t x = a + threadIdx.x; x < b; x += 256) {
+                const uint64_t j = x - off[i];
+                if (GATHER) {
+                    kin[x] = static_cast<const K*>(R.kin)[j];
+                    if (V) vin[x] = R.vin[j];
+                } else {
+                    static_cast<K*>(R.kout)[j] = kout[x];
+                    if (V) R.vout[j] = vout[x];
+                }
+            }
+        }
+    }
+}
+
+template <typename K, bool V>
+void copy_requests(bool gather, const ReqPtrs* tab, const uint64_t* off, uint32_t m, uint64_t n, void* kin, uint32_t* vin,
+                   const void* kout, const uint32_t* vout, cudaStream_t st) {
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((n + kSegTile - 1) / kSegTile, 152 * 8);
+    if (gather)
+        k_copy_requests<K, V, true><<<grid, 256, 0, st>>>(tab, off, m, n, static_cast<K*>(kin), vin, nullptr, nullptr);
+    else
+        k_copy_requests<K, V, false><<<grid, 256, 0, st>>>(tab, off, m, n, nullptr, nullptr, static_cast<const K*>(kout),
+                                                            vout);
+}
+
+void move_requests(bool gather, mps_key_type kt, bool vals, const ReqPtrs* tab, const uint64_t* off, uint32_t m, uint64_t n,
+                   void* kin, uint32_t* vin, const void* kout, const uint32_t* vout, cudaStream_t st) {
+    if (kt == MPS_U32) {
+        if (vals) copy_requests<uint32_t, true>(gather, tab, off, m, n, kin, vin, kout, vout, st);
+        else copy_requests<uint32_t, false>(gather, tab, off, m, n, kin, vin, kout, vout, st);
+    } else {
+        if (vals) copy_requests<uint64_t, true>(gather, tab, off, m, n, kin, vin, kout, vout, st);
+        else copy_requests<uint64_t, false>(gather, tab, off, m, n, kin, vin, kout, vout, st);
+    }
+}
 
 constexpr size_t kPoolAlign = 256;
 
@@ -146,7 +212,9 @@ mps_status launch_batch(mps_queue* q, std::vector<uint64_t>& ids, int sidx, Batc
     size_t ws = 0;
     mps_status s = mps_batch_workspace_size(n, m, kt, vals, q->cfg.k ? q->cfg.k : 4, &ws);
     if (s != MPS_OK) return s;
-    const size_t sizes[6] = {n * kb, n * kb, vals ? n * 4 : 0, vals ? n * 4 : 0, (size_t)(m + 1) * 8, ws};
+    // offsets (m + 1) and the request pointer table (m) travel in one copy
+    const size_t tab_bytes = (size_t)(m + 1) * 8 + (size_t)m * sizeof(ReqPtrs);
+    const size_t sizes[6] = {n * kb, n * kb, vals ? n * 4 : 0, vals ? n * 4 : 0, tab_bytes, ws};
     size_t offs[6];
     for (int i = 0; i < 6; i++) {
         if (!q->alloc.alloc(sizes[i], &offs[i])) {
@@ -163,32 +231,29 @@ mps_status launch_batch(mps_queue* q, std::vector<uint64_t>& ids, int sidx, Batc
     uint64_t* d_off = reinterpret_cast<uint64_t*>(pool + offs[4]);
     void* d_ws = pool + offs[5];
     cudaStream_t st = q->streams[sidx];
+    // the pinned staging buffer of this stream is free: its last copy finished
+    // before the stream's previous batch completed
     uint64_t* h_off = q->h_off[sidx];
+    ReqPtrs* h_tab = reinterpret_cast<ReqPtrs*>(h_off + (m + 1));
     uint64_t acc = 0;
     for (uint32_t i = 0; i < m; i++) {
         const mps_request& r = q->tickets[ids[i]].req;
         h_off[i] = acc;
-        if (r.n) {
-            cudaMemcpyAsync(kin + acc * kb, r.d_keys_in, r.n * kb, cudaMemcpyDeviceToDevice, st);
-            if (vals) cudaMemcpyAsync(vin + acc, r.d_vals_in, r.n * 4, cudaMemcpyDeviceToDevice, st);
-        }
+        h_tab[i] = ReqPtrs{r.d_keys_in, r.d_vals_in, r.d_keys_out, r.d_vals_out};
         acc += r.n;
     }
     h_off[m] = acc;
-    cudaMemcpyAsync(d_off, h_off, (size_t)(m + 1) * 8, cudaMemcpyHostToDevice, st);
+    const ReqPtrs* d_tab = reinterpret_cast<const ReqPtrs*>(d_off + (m + 1));
+    cudaMemcpyAsync(d_off, h_off, tab_bytes, cudaMemcpyHostToDevice, st);
     *q->h_status[sidx] = 0;  // the stream is idle: no copy into this buffer is pending
     if (n) {
+        move_requests(true, kt, vals, d_tab, d_off, m, n, kin, vin, nullptr, nullptr, st);
         s = mps::batch_dispatch(kin, vin, kout, vout, n, d_off, m, max_len, kt, q->cfg.k ? q->cfg.k : 4, d_ws, ws, false,
                                 st);
         if (s != MPS_OK) return s;
         // device status word: entry 5 of the workspace's leading 64-bit counter block
         cudaMemcpyAsync(q->h_status[sidx], reinterpret_cast<char*>(d_ws) + 5 * 8, 4, cudaMemcpyDeviceToHost, st);
-    }
-    for (uint32_t i = 0; i < m; i++) {
-        const mps_request& r = q->tickets[ids[i]].req;
-        if (!r.n) continue;
-        cudaMemcpyAsync(r.d_keys_out, kout + h_off[i] * kb, r.n * kb, cudaMemcpyDeviceToDevice, st);
-        if (vals) cudaMemcpyAsync(r.d_vals_out, vout + h_off[i], r.n * 4, cudaMemcpyDeviceToDevice, st);
+        move_requests(false, kt, vals, d_tab, d_off, m, n, nullptr, nullptr, kout, vout, st);
     }
     if (cudaEventCreateWithFlags(&B.done, cudaEventDisableTiming) != cudaSuccess) return MPS_ERR_CUDA;
     if (cudaEventRecord(B.done, st) != cudaSuccess) return MPS_ERR_CUDA;
@@ -310,7 +375,8 @@ mps_status mps_queue_create(const mps_queue_config* cfg, mps_queue** out) {
     q->h_status.assign(q->cfg.max_inflight, nullptr);
     for (uint32_t i = 0; i < q->cfg.max_inflight; i++) {
         if (cudaStreamCreateWithFlags(&q->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaMallocHost(&q->h_off[i], ((size_t)q->cfg.max_batch + 1) * 8) != cudaSuccess ||
+            cudaMallocHost(&q->h_off[i], ((size_t)q->cfg.max_batch + 1) * 8 + (size_t)q->cfg.max_batch * sizeof(ReqPtrs)) !=
+                cudaSuccess ||
             cudaMallocHost(&q->h_status[i], 8) != cudaSuccess) {
             for (uint32_t j = 0; j <= i; j++) {
                 if (q->streams[j]) cudaStreamDestroy(q->streams[j]);
