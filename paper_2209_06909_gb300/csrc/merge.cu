@@ -75,6 +75,7 @@ __device__ __forceinline__ void bulk_copy_g2s(void* smem, const void* gmem, uint
 constexpr uint32_t kMbarSpinLimit = 1u << 24;
 
 constexpr int kFusedThreads = 256;
+constexpr uint32_t kFusedPad = 16;  // elements of slack per fused-kernel buffer
 constexpr uint32_t kNoMid = 0xFFFFu;
 // boundary-list entries one thread holds while compacting: ceil((C/2 + 8) / 256), odd
 constexpr int kKeepMax = 25;
@@ -225,9 +226,12 @@ struct OpMax2 {
 
 template <typename K, bool V>
 struct FusedSmem {
+    // key and payload buffers of C elements plus kFusedPad of slack (the loaded
+    // tile sits on its source's 16-byte grid; merges read two past the end)
     static __host__ __device__ size_t bytes(uint32_t C) {
         const uint32_t bmax = C / 2 + 8;
-        return (size_t)2 * C * sizeof(K) + (V ? (size_t)2 * C * 4 : 0) + (size_t)2 * bmax * 4;
+        const size_t cp = (size_t)C + kFusedPad;
+        return 2 * cp * sizeof(K) + (V ? 2 * cp * 4 : 0) + (size_t)2 * bmax * 4;
     }
 };
 
@@ -246,16 +250,21 @@ __global__ void __launch_bounds__(kFusedThreads)
             const uint8_t* __restrict__ P, uint32_t C, int k, uint64_t n_total, uint32_t* __restrict__ status) {
     extern __shared__ uint4 smem_raw[];
     const uint32_t BMAX = C / 2 + 8;
+    const uint32_t CP = C + kFusedPad;
     K* kA = reinterpret_cast<K*>(smem_raw);
-    K* kB = kA + C;
-    uint32_t* vA = V ? reinterpret_cast<uint32_t*>(kB + C) : nullptr;
-    uint32_t* vB = V ? vA + C : nullptr;
-    uint32_t* bl0 = V ? (vB + C) : reinterpret_cast<uint32_t*>(kB + C);
+    K* kB = kA + CP;
+    uint32_t* vA = V ? reinterpret_cast<uint32_t*>(kB + CP) : nullptr;
+    uint32_t* vB = V ? vA + CP : nullptr;
+    uint32_t* bl0 = V ? (vB + CP) : reinterpret_cast<uint32_t*>(kB + CP);
     uint32_t* bl1 = bl0 + BMAX;
     __shared__ uint32_t stmp[kFusedThreads / 32 + 1];
     __shared__ uint4 stmp4[kFusedThreads / 32 + 1];
+    __shared__ __align__(8) uint64_t s_bar;
+    uint32_t phase = 0;
     const uint32_t tid = threadIdx.x;
     const uint32_t F = (uint32_t)ctr[kCtrFrontier];
+    if (tid == 0) mbar_init(&s_bar, 1);
+    __syncthreads();
 
     for (uint32_t f = blockIdx.x; f < F; f += gridDim.x) {
         const uint4 fr = flist[f];
@@ -286,16 +295,44 @@ __global__ void __launch_bounds__(kFusedThreads)
         uint8_t* dflag = PS + (C / 2 + 64);
         const uint32_t pa = (L + 1) & ~3u, pb = (R + 3) & ~3u;
         const uint32_t da = L & ~3u, db = (R + 3) & ~3u;
+        // keys: element x lands at kA[lead + x], on the 16-byte grid of its
+        // source, so the aligned middle is one bulk copy (TMA) completed on
+        // s_bar; the unaligned ends and the payloads are copied per element
+        constexpr uint32_t VK = 16 / sizeof(K);
+        const K* ksrc = leaf + s_lo;
+        const uint32_t lead = (uint32_t)((reinterpret_cast<uintptr_t>(ksrc) & 15u) / sizeof(K));
+        const uint32_t kib = min(len, (VK - lead) & (VK - 1u));
+        const uint32_t kie = kib + (len - kib) / VK * VK;
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&s_bar, (kie - kib) * (uint32_t)sizeof(K));
+            if (kie > kib) bulk_copy_g2s(kA + lead + kib, ksrc + kib, (kie - kib) * (uint32_t)sizeof(K), &s_bar);
+        }
         for (uint32_t e = tid; e < nb; e += kFusedThreads) cp_async<4>(rsS + e, rs + L + 1 + e);
         for (uint32_t q = pa + 4 * tid; q < pb; q += 4 * kFusedThreads) cp_async<4>(PS + (q - pa), P + q);
         for (uint32_t q = da + 4 * tid; q < db; q += 4 * kFusedThreads) cp_async<4>(dflag + (q - da), rdesc + q);
-        for (uint32_t x = tid; x < len; x += kFusedThreads) {
-            cp_async<sizeof(K)>(kA + x, leaf + s_lo + x);
-            if (V) cp_async<4>(vA + x, vleaf + s_lo + x);
-        }
+        for (uint32_t x = tid; x < kib; x += kFusedThreads) cp_async<sizeof(K)>(kA + lead + x, ksrc + x);
+        for (uint32_t x = kie + tid; x < len; x += kFusedThreads) cp_async<sizeof(K)>(kA + lead + x, ksrc + x);
+        if (V)
+            for (uint32_t x = tid; x < len; x += kFusedThreads) cp_async<4>(vA + lead + x, vleaf + s_lo + x);
         cp_async_commit();
         cp_async_wait<0>();
-        __syncthreads();
+        {
+            uint32_t spins = 0;
+            bool done = mbar_try_wait(&s_bar, phase);
+            while (!done && spins < kMbarSpinLimit) {
+                done = mbar_try_wait(&s_bar, phase);
+                spins++;
+            }
+            if (__syncthreads_or(!done)) {
+                // the bulk copy did not complete: report it, one more bounded wait, stop
+                if (tid == 0) dev_fail(status, kDevSpin);
+                for (spins = 0; !mbar_try_wait(&s_bar, phase) && spins < kMbarSpinLimit; spins++) {
+                }
+                return;
+            }
+            phase ^= 1u;
+        }
         for (uint32_t e = tid; e < nb; e += kFusedThreads)
             bl0[e] = (rsS[e] - s_lo) | ((uint32_t)PS[e + (L + 1 - pa)] << 16);
         dflag += L - da;  // dflag[q] = direction of run L + q
@@ -320,7 +357,7 @@ __global__ void __launch_bounds__(kFusedThreads)
                         rs0 = re0;
                         re0 = rho < nb ? be_off(bl0[rho]) : len;
                     }
-                    const uint32_t src = dflag[rho] ? (rs0 + re0 - 1 - x) : x;
+                    const uint32_t src = lead + (dflag[rho] ? (rs0 + re0 - 1 - x) : x);
                     kB[x] = kA[src];
                     if (V) vB[x] = vA[src];
                 }
@@ -445,23 +482,32 @@ __device__ __forceinline__ uint32_t node_splitters(const LevelNode& nd, const ui
     return s;
 }
 
-// Per node of the level: number of splitters and work units (one unit more
-// than splitters), their offsets, and unit_node for each node's first unit.
-__global__ void __launch_bounds__(1024) k_level_prep(LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off,
+// Splitters of every node of the level (one thread per node), kept in nsplit.
+__global__ void __launch_bounds__(256) k_level_count(LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off,
                                                      int p, const uint32_t* __restrict__ rs, uint32_t ts,
-                                                     uint64_t* __restrict__ ctr, uint32_t* __restrict__ unit_node) {
+                                                     const uint64_t* __restrict__ ctr) {
+    LevelNode* nodes = nodes_lvl + level_off[p];
+    const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x)
+        nodes[v].nsplit = node_splitters(nodes[v], rs, ts);
+}
+
+// Per node of the level: offsets of its splitters and work units (one unit
+// more than splitters), and unit_node for each node's first unit.
+__global__ void __launch_bounds__(1024) k_level_prep(LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off,
+                                                     int p, uint64_t* __restrict__ ctr, uint32_t* __restrict__ unit_node) {
     LevelNode* nodes = nodes_lvl + level_off[p];
     const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
     __shared__ uint32_t tmp[1024 / 32 + 1];
     uint32_t per = (nn + 1023) / 1024;
     uint32_t b = min(nn, threadIdx.x * per), e = min(nn, b + per);
     uint32_t acc = 0;
-    for (uint32_t v = b; v < e; v++) acc += node_splitters(nodes[v], rs, ts);
+    for (uint32_t v = b; v < e; v++) acc += nodes[v].nsplit;
     uint32_t tot;
     uint32_t pre = block_sum_excl<1024>(acc, tmp, &tot);
     for (uint32_t v = b; v < e; v++) {
         LevelNode& nd = nodes[v];
-        uint32_t s = node_splitters(nd, rs, ts);
+        const uint32_t s = nd.nsplit;
         nd.split_off = pre;
         nd.nsplit = s;
         nd.unit_off = pre + v;   // units of node v: splitters before it plus one per earlier node
@@ -1019,7 +1065,8 @@ MergeGeom merge_geom(int key_bytes, bool vals, int k) {
     // persistent level merge: two buffers of c_level elements per block
     size_t lvl_smem = (size_t)2 * (g.c_level + kLvlPad) * ((size_t)key_bytes + (vals ? 4 : 0)) + 256;
     g.level_grid = 152 * (uint32_t)std::min<size_t>(16, (220 * 1024) / lvl_smem);
-    size_t fz_smem = (size_t)2 * g.c_fused * ((size_t)key_bytes + (vals ? 4 : 0)) + (size_t)2 * (g.c_fused / 2 + 8) * 4 + 1024;
+    size_t fz_smem = (size_t)2 * (g.c_fused + kFusedPad) * ((size_t)key_bytes + (vals ? 4 : 0)) +
+                     (size_t)2 * (g.c_fused / 2 + 8) * 4 + 1024;
     g.fused_grid = 152 * (uint32_t)std::max<size_t>(1, std::min<size_t>(8, (220 * 1024) / fz_smem));
     return g;
 }
@@ -1041,7 +1088,9 @@ template <typename K>
 void launch_level_plan(int p, uint32_t nn_bound, uint64_t elems_bound, int k, const K* leaf_keys, K* out,
                        const MergeGeom& g, const WsView& ws, cudaStream_t st) {
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
-    k_level_prep<<<1, 1024, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.run_starts, g.ts, ws.counters, ws.unit_node);
+    k_level_count<<<(uint32_t)std::min<uint64_t>(ceil_div(std::max<uint32_t>(nn_bound, 1), 256), 152 * 4), 256, 0, st>>>(
+        ws.nodes_lvl, ws.level_off, p, ws.run_starts, g.ts, ws.counters);
+    k_level_prep<<<1, 1024, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.counters, ws.unit_node);
     const uint64_t split_bound = elems_bound / g.ts + 1;
     const uint32_t split_blocks = (uint32_t)std::min<uint64_t>(ceil_div(split_bound * (uint64_t)k, 256), 152 * 16);
     k_level_split<K><<<split_blocks, 256, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.counters, ws.run_starts, ws.run_desc,
@@ -1057,7 +1106,7 @@ void launch_level_plan(int p, uint32_t nn_bound, uint64_t elems_bound, int k, co
     k_level_desc<<<desc_blocks, 256, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.unit_first, ws.split_tab,
                                               ws.counters, ws.run_starts, ws.run_desc, k,
                                               reinterpret_cast<UnitDesc*>(ws.unit_desc));
-    g_launches += 6;
+    g_launches += 7;
 }
 
 template <typename K, bool V>
