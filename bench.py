@@ -510,11 +510,15 @@ def run_mps(args):
             variants = []
             b_runs = gen_input("runs", n, 2000)
             d_runs = mps.to_device(b_runs, dev)
+            # fan-in study: k = 2 (the paper's baseline), 4 (the headline), 8
+            ws_k = {k: ws, 2: ws2}
             for kind, dsrc in (("perm", d_in), ("runs", d_runs)):
-                for kk in sorted({k, 2}):
+                for kk in sorted({k, 2, 8}):
                     if kind == "perm" and kk == k:
                         continue
-                    w = ws if kk == k else ws2
+                    if kk not in ws_k:
+                        ws_k[kk] = mps.workspace(n, 4, False, kk, dev)
+                    w = ws_k[kk]
                     vms = time_sorts(mps, torch, dsrc, d_out, w, kk, 8, 3, stream)
                     st = mps.last_stats()
                     ba = b * (n + 2.0 * st["merge_cost"])
@@ -524,7 +528,7 @@ def run_mps(args):
                                      "levels": st["num_levels"],
                                      "sort_frac_of_measured": ba / (vms * 1e-3) / 1e9 / peaks["hbm_gbs"]})
             line["variants"] = variants
-            del d_runs
+            del d_runs, ws_k
         del d_tmp
         for name, fn, flag in (("pairs", lambda: bench_pairs(mps, torch, dev, stream), args.no_variants),
                                ("batch", lambda: bench_batch(mps, torch, dev, stream), args.no_batch),

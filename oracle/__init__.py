@@ -65,6 +65,8 @@ def _load():
         lib.mpso_tree_from_powers.restype = ctypes.c_int
         lib.mpso_tree_from_lengths.argtypes = [P, U64, ctypes.c_uint32, P, P, P, P, P]
         lib.mpso_tree_from_lengths.restype = ctypes.c_int
+        lib.mpso_merge_cost_tail.argtypes = [P, U64, ctypes.c_uint32, ctypes.c_int, P]
+        lib.mpso_merge_cost_tail.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -165,3 +167,17 @@ def tree_from_lengths(lengths, k):
     return {"powers": pw[: r + 1].copy(), "nodes": nodes[:nn].copy(), "node_first": nf[:r].copy(),
             "leaf_depth": ld[:r].copy(), "r": r, "num_nodes": nn, "num_levels": int(counts[2]),
             "merge_cost": int(counts[3])}
+
+
+TAIL_POLICIES = {"kway_tree": 0, "alg2_pop_k_minus_1": 1, "merge_down": 2}
+
+
+def merge_cost_tail(lengths, k, policy):
+    """Merge cost of Alg. 2's run stack on run lengths alone, with the final
+    collapse done by ``policy``: "kway_tree" (power rule against a final power
+    0, the tree of Alg. 1), "alg2_pop_k_minus_1" (Alg. 2's last loop as
+    printed) or "merge_down" (the appendix's merge_down taken to any k)."""
+    ln = np.ascontiguousarray(lengths, dtype=np.uint64)
+    out = np.zeros(1, np.uint64)
+    _check(_load().mpso_merge_cost_tail(_ptr(ln), ln.size, k, TAIL_POLICIES[policy], _ptr(out)))
+    return int(out[0])

@@ -461,3 +461,74 @@ out:
     raw_tree_free(&t);
     return rc;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Final-collapse variants (merge cost only).                                 */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Merge cost of Alg. 2's run stack on run lengths alone, with one of three
+ * ways to empty the stack after the last run (the main loop is the same in
+ * all three: while the top power exceeds the new boundary's power, merge the
+ * group of equal top powers with the current run):
+ *   policy 0: the same power rule against a virtual final power 0 -- the tree
+ *             of Alg. 1 (KwayTree_k), as everywhere else in this oracle;
+ *   policy 1: Alg. 2's last loop as printed: pop up to k-1 runs at a time and
+ *             merge them with the current run;
+ *   policy 2: the appendix's merge_down for k = 4, taken to any k: first merge
+ *             the top x runs with the current run, x = (runs - 1) mod (k - 1),
+ *             so that every later merge takes k runs (k-1 popped + current).
+ * *cost receives M = the sum of the sizes of all merge results (Sec. 2.2).
+ */
+int mpso_merge_cost_tail(const uint64_t* lengths, uint64_t r, uint32_t k, int policy, uint64_t* cost) {
+    if (k < 2 || policy < 0 || policy > 2 || !cost) return MPSO_ERR_ARG;
+    *cost = 0;
+    if (r <= 1) return MPSO_OK;
+    uint32_t* starts = (uint32_t*)malloc((r + 1) * sizeof(uint32_t));
+    uint8_t* pw = (uint8_t*)calloc(r + 1, 1);
+    uint64_t* sl = (uint64_t*)malloc((r + 1) * sizeof(uint64_t)); /* stack: lengths */
+    uint32_t* sp_pw = (uint32_t*)malloc((r + 1) * sizeof(uint32_t)); /* stack: powers */
+    if (!starts || !pw || !sl || !sp_pw) {
+        free(starts); free(pw); free(sl); free(sp_pw);
+        return MPSO_ERR_NOMEM;
+    }
+    mpso_powers_from_lengths(lengths, r, k, pw, starts);
+    uint64_t sp = 0, cur = lengths[0], m = 0;
+    for (uint64_t i = 1; i < r; i++) {
+        const uint32_t P = pw[i];
+        while (sp > 0 && sp_pw[sp - 1] > P) {
+            const uint32_t top = sp_pw[sp - 1];
+            while (sp > 0 && sp_pw[sp - 1] == top) cur += sl[--sp];
+            m += cur;
+        }
+        sl[sp] = cur;
+        sp_pw[sp] = P;
+        sp++;
+        cur = lengths[i];
+    }
+    if (policy == 0) {
+        while (sp > 0) {
+            const uint32_t top = sp_pw[sp - 1];
+            while (sp > 0 && sp_pw[sp - 1] == top) cur += sl[--sp];
+            m += cur;
+        }
+    } else if (policy == 1) {
+        while (sp > 0) {
+            for (uint32_t c = 0; c + 1 < k && sp > 0; c++) cur += sl[--sp];
+            m += cur;
+        }
+    } else {
+        const uint64_t x = sp % (k - 1); /* (stack + current - 1) mod (k - 1) */
+        if (x > 0) {
+            for (uint64_t c = 0; c < x; c++) cur += sl[--sp];
+            m += cur;
+        }
+        while (sp > 0) {
+            for (uint32_t c = 0; c + 1 < k; c++) cur += sl[--sp];
+            m += cur;
+        }
+    }
+    *cost = m;
+    free(starts); free(pw); free(sl); free(sp_pw);
+    return MPSO_OK;
+}

@@ -353,3 +353,54 @@ def test_sort_edge_cases():
             assert np.array_equal(res["vals"], order.astype(np.uint32))
             if arr.size <= 1:
                 assert res["merge_cost"] == 0 and res["num_nodes"] == 0
+
+
+# ---------------------------------------------------------------- final collapse variants
+
+def _random_lengths(rng, r, hi):
+    return rng.integers(1, hi + 1, r).astype(np.uint64)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 8])
+def test_tail_kway_tree_policy_is_the_oracle_tree(k):
+    """Policy "kway_tree" is the oracle's own final collapse (power rule against
+    a final power 0), i.e. the merge cost of Alg. 1's tree."""
+    rng = np.random.default_rng(70 + k)
+    for _ in range(300):
+        L = _random_lengths(rng, int(rng.integers(1, 60)), int(rng.choice([3, 50, 2000])))
+        assert oracle.merge_cost_tail(L, k, "kway_tree") == oracle.tree_from_lengths(L, k)["merge_cost"]
+
+
+def test_tail_policies_agree_for_binary_merges():
+    """For k = 2 every node has one boundary, so the power rule, "pop k-1" and
+    merge_down all merge the top run with the current one: the same cost."""
+    rng = np.random.default_rng(72)
+    for _ in range(300):
+        L = _random_lengths(rng, int(rng.integers(1, 80)), 1000)
+        c = [oracle.merge_cost_tail(L, 2, p) for p in oracle.TAIL_POLICIES]
+        assert c[0] == c[1] == c[2]
+
+
+def test_merge_down_never_costs_more_than_kway_tree():
+    """Appendix (merge_down for k = 4): the changed final collapse "can only
+    reduce the resulting merge cost" relative to the tree of KwayTree_k."""
+    rng = np.random.default_rng(74)
+    lower = 0
+    for _ in range(2000):
+        L = _random_lengths(rng, int(rng.integers(1, 40)), int(rng.choice([4, 100, 5000])))
+        md = oracle.merge_cost_tail(L, 4, "merge_down")
+        kt = oracle.merge_cost_tail(L, 4, "kway_tree")
+        assert md <= kt
+        lower += md < kt
+    assert lower > 0  # the variants do differ
+
+
+def test_alg2_printed_tail_can_cost_more():
+    """Alg. 2's last loop (pop up to k-1 runs per merge) builds a different tree
+    from Alg. 1's at the end and can have a higher merge cost (k = 4)."""
+    rng = np.random.default_rng(76)
+    higher = 0
+    for _ in range(2000):
+        L = _random_lengths(rng, int(rng.integers(1, 40)), int(rng.choice([4, 100, 5000])))
+        higher += oracle.merge_cost_tail(L, 4, "alg2_pop_k_minus_1") > oracle.merge_cost_tail(L, 4, "kway_tree")
+    assert higher > 0
