@@ -213,6 +213,38 @@ def bench_pairs(mps, torch, dev, stream, steps=5):
             "stable_sample_checked": int(idx.size)}
 
 
+def bench_records(mps, torch, dev, stream, steps=5):
+    """Records (Sec. 5): n = 2^26 uint64 keys with uint64 payloads (16 bytes),
+    random runs of geometric mean sqrt(n); mps_sort_records, payloads checked
+    on a sample against the stable order of the keys."""
+    from paper_2209_06909_gb300 import inputs
+    n = 1 << 26
+    a = inputs.random_runs_geometric(n, 41, mean=float(np.sqrt(n)), dtype=np.uint64)
+    v = inputs.record_payload(n, 41)
+    d_k, d_v = mps.to_device(a, dev), mps.to_device(v, dev)
+    ok, ov = torch.empty_like(d_k), torch.empty_like(d_v)
+    ws = mps.records_workspace(n, 8, 4, dev)
+    for _ in range(2):
+        mps.sort_records(d_k, d_v, k=4, out_keys=ok, out_vals=ov, ws=ws, stream=stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        mps.sort_records(d_k, d_v, k=4, out_keys=ok, out_vals=ov, ws=ws, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    st = mps.last_stats()
+    keys = mps.to_numpy(ok, np.uint64)
+    vals = mps.to_numpy(ov, np.uint64)
+    assert np.all(keys[1:] >= keys[:-1])
+    order = np.argsort(a, kind="stable")[: 1 << 16]
+    assert np.array_equal(vals[: 1 << 16], v[order])
+    return {"workload": "n=2^26 records: uint64 key + uint64 payload, geometric runs of mean sqrt(n), k=4",
+            "ms": ms, "gkeys_s": n / (ms * 1e-3) / 1e9, "merge_cost_per_n": st["merge_cost"] / n,
+            "payload_sample_checked": 1 << 16}
+
+
 def bench_batch(mps, torch, dev, stream, steps=5):
     """4096 uint32 arrays, sizes log-uniform [2^4, 2^20]: one graph-captured
     batched sort (autotuned k) against one plain mps_sort_keys per array."""
@@ -531,6 +563,7 @@ def run_mps(args):
             del d_runs, ws_k
         del d_tmp
         for name, fn, flag in (("pairs", lambda: bench_pairs(mps, torch, dev, stream), args.no_variants),
+                               ("records", lambda: bench_records(mps, torch, dev, stream), args.no_variants),
                                ("batch", lambda: bench_batch(mps, torch, dev, stream), args.no_batch),
                                ("serve", lambda: bench_serve(mps, torch, dev, stream, args.serve_requests),
                                 args.no_serve)):

@@ -110,6 +110,18 @@ mps_status mps_sort_pairs(const void* d_keys_in, const uint32_t* d_vals_in, void
                           uint32_t* d_vals_out, uint64_t n, mps_key_type kt, int k,
                           void* d_ws, size_t ws_bytes, const mps_tree* opt_tree, cudaStream_t stream);
 
+/* Records (Sec. 5, "records" experiment: a long key and a pointer, 16 bytes):
+ * stable sort of n keys each carrying a 64-bit payload.  The keys are sorted
+ * with their input indices as uint32 payloads (as mps_sort_pairs), and every
+ * payload is then moved once through that stable permutation:
+ * d_vals_out[i] = d_vals_in[perm[i]].  d_vals_in and d_vals_out must not
+ * overlap.  Workspace: mps_records_workspace_size(n, kt, k) bytes (the pairs
+ * workspace plus 8 bytes per key).  Synchronises the stream. */
+mps_status mps_records_workspace_size(uint64_t n, mps_key_type kt, int k, size_t* bytes);
+mps_status mps_sort_records(const void* d_keys_in, const uint64_t* d_vals_in, void* d_keys_out,
+                            uint64_t* d_vals_out, uint64_t n, mps_key_type kt, int k, void* d_ws,
+                            size_t ws_bytes, cudaStream_t stream);
+
 /* Run structure, powers and canonical merge tree of d_keys without moving
  * any key (the keys are not modified).  `out` must be non-NULL. */
 mps_status mps_merge_tree(const void* d_keys, uint64_t n, mps_key_type kt, int k, const mps_tree* out,

@@ -13,6 +13,8 @@ Workloads (Sec. 5, "random runs" and "random permutations" inputs):
     mean (support 1, 2, ...), values uniform over the key type;
   * ``random_runs_loguniform``: ascending runs with lengths floor(2^U(a, b)),
     keys drawn from a pool of distinct values (heavy duplicates);
+  * ``record_payload``: 64-bit payloads of the records workload (a long key
+    and a pointer, random runs of geometric mean sqrt(n));
   * ``batch_arrays`` and ``request_stream`` for the batched and served modes.
 The last run is truncated at n.  Generated runs are not necessarily the
 detected runs (adjacent runs may fuse); the sort detects runs itself.
@@ -112,6 +114,11 @@ def random_runs_loguniform(n: int, seed: int, log2_lo: float = 1.0, log2_hi: flo
         pool = np.unique((pool >> np.uint64(32)).astype(np.uint32))
     L = _lengths_until(n, lambda m: np.floor(np.exp2(rng.uniform(log2_lo, log2_hi, m))).astype(np.int64))
     return _fill_runs(L, lambda m: pool[rng.integers(0, pool.size, m)])
+
+
+def record_payload(n: int, seed: int) -> np.ndarray:
+    """uint64 payloads standing in for pointers: uniform 64-bit values."""
+    return _rng(seed ^ 0xACE).integers(0, np.iinfo(np.uint64).max, n, dtype=np.uint64, endpoint=True)
 
 
 def payload_index(n: int) -> np.ndarray:

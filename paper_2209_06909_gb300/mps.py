@@ -69,7 +69,7 @@ EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_t
            "mps_batch_workspace_size", "mps_sort_batch", "mps_sort_batch_pairs", "mps_batch_autotune",
            "mps_batch_graph_create", "mps_batch_graph_launch", "mps_batch_graph_destroy",
            "mps_queue_create", "mps_queue_submit", "mps_queue_poll", "mps_queue_wait", "mps_queue_pause",
-           "mps_queue_destroy"]
+           "mps_queue_destroy", "mps_records_workspace_size", "mps_sort_records"]
 
 # Largest n accepted by mps_sort_keys_noalloc (its scratch is compiled into the library).
 NOALLOC_MAX_N = 1 << 20
@@ -117,6 +117,10 @@ def lib():
     L.mps_queue_destroy.argtypes = [P]
     for fn in ("mps_queue_create", "mps_queue_submit", "mps_queue_poll", "mps_queue_wait", "mps_queue_pause",
                "mps_queue_destroy"):
+        getattr(L, fn).restype = I
+    L.mps_records_workspace_size.argtypes = [U64, I, I, ctypes.POINTER(ctypes.c_size_t)]
+    L.mps_sort_records.argtypes = [P, P, P, P, U64, I, I, P, ctypes.c_size_t, P]
+    for fn in ("mps_records_workspace_size", "mps_sort_records"):
         getattr(L, fn).restype = I
     L.mps_status_string.argtypes = [I]
     L.mps_status_string.restype = ctypes.c_char_p
@@ -234,6 +238,30 @@ def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, k: int = 4, out_keys=None
     _check("mps_sort_pairs", lib().mps_sort_pairs(keys.data_ptr(), vals.data_ptr(), out_keys.data_ptr(),
                                                   out_vals.data_ptr(), n, kt, k, ws.data_ptr(), ws.numel(), ts,
                                                   _stream(stream)))
+    return out_keys, out_vals
+
+
+def records_workspace(n: int, key_bytes: int, k: int = 4, device="cuda") -> torch.Tensor:
+    b = ctypes.c_size_t(0)
+    _check("mps_records_workspace_size",
+           lib().mps_records_workspace_size(n, 0 if key_bytes == 4 else 1, k, ctypes.byref(b)))
+    return torch.empty(max(b.value, 16), dtype=torch.uint8, device=device)
+
+
+def sort_records(keys: torch.Tensor, vals: torch.Tensor, k: int = 4, out_keys=None, out_vals=None, ws=None,
+                 stream=None):
+    """Stable sort of records with 8-byte payloads (mps_sort_records)."""
+    n = keys.numel()
+    kt = _key_type(keys)
+    if vals.element_size() != 8 or vals.numel() != n:
+        raise TypeError("vals must be n 8-byte values")
+    out_keys = torch.empty_like(keys) if out_keys is None else out_keys
+    out_vals = torch.empty_like(vals) if out_vals is None else out_vals
+    if ws is None:
+        ws = records_workspace(n, keys.element_size(), k, keys.device)
+    _check("mps_sort_records", lib().mps_sort_records(keys.data_ptr(), vals.data_ptr(), out_keys.data_ptr(),
+                                                      out_vals.data_ptr(), n, kt, k, ws.data_ptr(), ws.numel(),
+                                                      _stream(stream)))
     return out_keys, out_vals
 
 

@@ -11,6 +11,8 @@ tree is still checked through its merge cost:
     equal the oracle's;
   * pairs (n = 2^27, uint64 keys with 2^16 distinct values, payload = index):
     keys and payload order equal the oracle's;
+  * records (n = 2^26, uint64 keys and uint64 payloads, runs of geometric
+    mean sqrt(n)): keys equal the oracle's, payloads follow its order;
   * 4096-array batch: every 61st array equals the oracle's sort, every array is
     non-decreasing with the same sum and xor as its input, and the batch's
     merge cost is the sum of the oracle's per-array merge costs;
@@ -88,6 +90,20 @@ def test_pairs_2e27():
     want = oracle.sort(a, v, k=4, want_tree=False)
     assert np.array_equal(got_k, want["keys"])
     assert np.array_equal(got_v, want["vals"])
+
+
+def test_records_2e26():
+    n = 1 << 26
+    a = inputs.random_runs_geometric(n, 41, mean=float(np.sqrt(n)), dtype=np.uint64)
+    v = inputs.record_payload(n, 41)
+    ok, ov = mps.sort_records(mps.to_device(a, DEV), mps.to_device(v, DEV), k=4)
+    torch.cuda.synchronize()
+    got_k = mps.to_numpy(ok, np.uint64)
+    got_v = mps.to_numpy(ov, np.uint64)
+    del ok, ov
+    want = oracle.sort(a, inputs.payload_index(n), k=4, want_tree=False)
+    assert np.array_equal(got_k, want["keys"])
+    assert np.array_equal(got_v, v[want["vals"]])
 
 
 def test_batch_4096_arrays():
