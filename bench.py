@@ -509,7 +509,8 @@ def run_mps(args):
     line = {"metric": "sorted_keys_per_second", "value": value, "unit": "GKeys/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "single-array sort, n=2^28 uint32 keys, uniform random permutation, k=%d" % k,
+            "config": {"workload": "single-array sort, n=2^%d uint32 keys, uniform random permutation, k=%d"
+                                   % (int(round(math.log2(n))), k),
                        "n": n, "k": k, "input": "random permutation", "per_gpu_arrays": 1,
                        "l2": "input 1 GiB > 129 MB L2 (no flush needed)"},
             "clocks": clocks, "gpu_launches": int(stats["launches"]) * args.steps,
