@@ -235,10 +235,12 @@ struct FusedSmem {
     }
 };
 
-// Fused subtrees: persistent blocks over the list of maximal subtrees of at
-// most C elements.  A block loads one subtree (reversing strictly descending
-// runs), executes all its levels in shared memory, largest power first, and
-// writes the subtree root's output.  Level p: the boundaries of power p form
+// Fused subtrees: persistent blocks over the list of fused tiles of at most C
+// elements: a maximal subtree, or consecutive sibling subtrees together with
+// their parent's power as a floor (levels at or below the floor are not merged
+// here, so the siblings stay apart).  A block loads one tile (reversing
+// strictly descending runs), executes all its levels in shared memory, largest
+// power first, and writes the result.  Level p: the boundaries of power p form
 // groups between boundaries of smaller power (one group = one node); the
 // group index q of each boundary gives the tournament round ctz(q) in which
 // its two sides meet.
@@ -270,6 +272,7 @@ __global__ void __launch_bounds__(kFusedThreads)
         const uint4 fr = flist[f];
         const uint32_t L = fr.x, R = fr.y;
         const bool odd = fr.z & 1u;
+        const uint32_t floor_p = fr.w;  // boundaries of power <= floor_p are never merged here
         if (L >= R) {
             if (tid == 0) dev_fail(status, kDevFusedRange);
             continue;
@@ -388,7 +391,7 @@ __global__ void __launch_bounds__(kFusedThreads)
         while ((1u << T) < (uint32_t)k) T++;
         __shared__ uint32_t s_rmask;
 
-        for (uint32_t p = pmax; p >= pmin && p >= 1; p--) {
+        for (uint32_t p = pmax; p >= pmin && p >= 1 && p > floor_p; p--) {
             per = odd_chunk(na);
             e0 = min(na, tid * per);
             e1 = min(na, e0 + per);

@@ -450,15 +450,32 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tm
                 }
                 atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmCount + v), 1ull);
                 atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmSize + v), (unsigned long long)size);
+                // Consecutive small inner children share one fused tile while
+                // they fit: the tile carries the node's power v as a floor, so
+                // its boundaries between the siblings (power v) stay delimiters
+                // and only levels above v are merged.
                 unsigned long long fe = 0;
-                for (uint32_t c = 0; c < s.d; c++) {
-                    uint32_t a = s.b[c], e = s.b[c + 1];
-                    uint32_t cs = rs[e] - rs[a];
-                    if (e - a >= 2 && cs <= tmax) {
+                uint32_t ga = 0, ge = 0, gsz = 0;  // open group: runs [ga, ge), gsz elements
+                for (uint32_t c = 0; c <= s.d; c++) {
+                    bool take = false;
+                    uint32_t a = 0, e = 0, cs = 0;
+                    if (c < s.d) {
+                        a = s.b[c];
+                        e = s.b[c + 1];
+                        cs = rs[e] - rs[a];
+                        take = e - a >= 2 && cs <= tmax;
+                    }
+                    if (gsz && !(take && a == ge && gsz + cs <= tmax)) {
                         uint32_t fs = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
-                        if (fs < fused_cap) fused_list[fs] = make_uint4(a, e, depth + 1, 0u);
+                        if (fs < fused_cap) fused_list[fs] = make_uint4(ga, ge, depth + 1, v);
                         else dev_fail(status, kDevCapacity);
-                        fe += cs;
+                        fe += gsz;
+                        gsz = 0;
+                    }
+                    if (take) {
+                        if (!gsz) ga = a;
+                        ge = e;
+                        gsz += cs;
                     }
                 }
                 if (fe) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), fe);
