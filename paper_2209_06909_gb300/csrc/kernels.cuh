@@ -33,6 +33,7 @@ enum : int {
     kCtrMaxLen = 204,   // longest array of a batch (elements)
     kCtrDetTile = 205,  // next run-detection tile to take
     kCtrCand = 206,     // node-pass candidates listed by the mask pass
+    kCtrMaxIvl = 207,   // largest splitter interval of the current level
     kCtrWords = 256
 };
 

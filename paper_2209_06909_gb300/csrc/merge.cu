@@ -521,6 +521,7 @@ __global__ void __launch_bounds__(1024) k_level_prep(LevelNode* __restrict__ nod
     if (threadIdx.x == 0) {
         ctr[kCtrSplits] = tot;
         ctr[kCtrIntervals] = tot + nn;
+        ctr[kCtrMaxIvl] = 0;
     }
 }
 
@@ -611,8 +612,10 @@ static_assert(sizeof(UnitDesc) == 128, "UnitDesc layout");
 // Splitter intervals are packed into work units: a unit starts at interval
 // i when rank(i) / q exceeds rank(i-1) / q, where rank(i) is the output
 // position of the interval's first element (the sum of its start positions
-// in the children).  With spacing ts = c/(2k) no interval exceeds c/2, so a
-// unit stays below q + c/2 = c elements and averages about c/2.
+// in the children).  A unit then holds less than q + (largest interval)
+// elements; q = c - (the level's largest interval, measured on the device)
+// keeps it within c.  With spacing ts = c/(2k) no interval exceeds c/2, so
+// q >= c/2.
 constexpr int kPackThreads = 256;
 constexpr int kPackItems = kPackTile / kPackThreads;
 
@@ -638,11 +641,41 @@ __device__ __forceinline__ bool starts_unit(const LevelNode* __restrict__ nodes,
     return rc / q > rp / q;
 }
 
+// Largest splitter interval of the level (elements), into ctr[kCtrMaxIvl].
+__global__ void __launch_bounds__(256) k_interval_max(const LevelNode* __restrict__ nodes_lvl,
+                                                      const uint32_t* __restrict__ level_off, int p,
+                                                      const uint32_t* __restrict__ unit_node, const uint32_t* __restrict__ tab,
+                                                      uint64_t* __restrict__ ctr, int k) {
+    __shared__ uint32_t tmp[256 / 32 + 1];
+    const LevelNode* nodes = nodes_lvl + level_off[p];
+    const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
+    const uint32_t ni = (uint32_t)ctr[kCtrIntervals];
+    uint32_t mx = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+        const uint32_t v = unit_node[i];
+        if (v >= nn) continue;  // reported by the packing kernels
+        const LevelNode& nd = nodes[v];
+        const uint32_t local = i - nd.unit_off;
+        const uint32_t r0 = local == 0 ? 0u : interval_rank(tab, i, k, nd.degree);
+        const uint32_t r1 = local + 1 < nd.nunits ? interval_rank(tab, i + 1, k, nd.degree) : nd.sR - nd.sL;
+        mx = max(mx, r1 - r0);
+    }
+    mx = block_reduce<256>(mx, OpMax32(), 0u, tmp);
+    if (threadIdx.x == 0 && mx) atomicMax(reinterpret_cast<unsigned long long*>(ctr + kCtrMaxIvl), (unsigned long long)mx);
+}
+
+// Packing quantum q = c - (largest interval), at least c/2.
+__device__ __forceinline__ uint32_t pack_quantum(const uint64_t* __restrict__ ctr, uint32_t c) {
+    const uint64_t mi = ctr[kCtrMaxIvl];
+    return mi < c / 2 ? c - (uint32_t)mi : c / 2;
+}
+
 __global__ void __launch_bounds__(kPackThreads) k_pack_reduce(const LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off, int p,
                                                               const uint32_t* __restrict__ unit_node,
                                                               const uint32_t* __restrict__ tab, const uint64_t* __restrict__ ctr,
-                                                              int k, uint32_t q, uint32_t* __restrict__ tiles) {
+                                                              int k, uint32_t c, uint32_t* __restrict__ tiles) {
     __shared__ uint32_t tmp[kPackThreads / 32 + 1];
+    const uint32_t q = pack_quantum(ctr, c);
     const LevelNode* nodes = nodes_lvl + level_off[p];
     const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
     uint32_t* status = reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(ctr) + kCtrStatus);
@@ -675,9 +708,10 @@ __global__ void __launch_bounds__(1024) k_pack_scan(uint32_t* __restrict__ tiles
 __global__ void __launch_bounds__(kPackThreads) k_pack_apply(const LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off, int p,
                                                               const uint32_t* __restrict__ unit_node,
                                                              const uint32_t* __restrict__ tab, const uint64_t* __restrict__ ctr,
-                                                             int k, uint32_t q, const uint32_t* __restrict__ tiles,
+                                                             int k, uint32_t c, const uint32_t* __restrict__ tiles,
                                                              uint32_t* __restrict__ unit_first) {
     __shared__ uint32_t tmp[kPackThreads / 32 + 1];
+    const uint32_t q = pack_quantum(ctr, c);
     const LevelNode* nodes = nodes_lvl + level_off[p];
     const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
     uint32_t* status = reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(ctr) + kCtrStatus);
@@ -1100,16 +1134,18 @@ void launch_level_plan(int p, uint32_t nn_bound, uint64_t elems_bound, int k, co
                                                     leaf_keys, out, tmp, g.ts, k, ws.unit_node, ws.split_tab);
     const uint64_t ivl_bound = split_bound + nn_bound;
     const uint32_t tiles = (uint32_t)ceil_div(ivl_bound, kPackTile);
+    k_interval_max<<<(uint32_t)std::min<uint64_t>(ceil_div(ivl_bound, 256), 152 * 8), 256, 0, st>>>(
+        ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.split_tab, ws.counters, k);
     k_pack_reduce<<<tiles, kPackThreads, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.split_tab, ws.counters, k,
-                                                  g.q, ws.pack_tiles);
+                                                  g.c_level, ws.pack_tiles);
     k_pack_scan<<<1, 1024, 0, st>>>(ws.pack_tiles, tiles, ws.counters);
     k_pack_apply<<<tiles, kPackThreads, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.split_tab, ws.counters, k,
-                                                 g.q, ws.pack_tiles, ws.unit_first);
+                                                 g.c_level, ws.pack_tiles, ws.unit_first);
     const uint32_t desc_blocks = (uint32_t)std::min<uint64_t>(ceil_div(ivl_bound, 256), 152 * 16);
     k_level_desc<<<desc_blocks, 256, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.unit_first, ws.split_tab,
                                               ws.counters, ws.run_starts, ws.run_desc, k,
                                               reinterpret_cast<UnitDesc*>(ws.unit_desc));
-    g_launches += 7;
+    g_launches += 8;
 }
 
 template <typename K, bool V>
