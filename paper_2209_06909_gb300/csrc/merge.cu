@@ -402,6 +402,10 @@ __global__ void __launch_bounds__(kFusedThreads)
             // are adjacent: q is found by looking back at most k - 1 entries.
             // Kept (smaller-power) boundaries wait in registers until the
             // level is merged.
+            if (per > (uint32_t)kKeepMax) {  // per is the same for every thread of the block
+                if (tid == 0) dev_fail(status, kDevRange);
+                return;
+            }
             uint32_t keep[kKeepMax];
             uint32_t nk = 0, rmask = 0;
             for (uint32_t e = e0; e < e1; e++) {
@@ -884,10 +888,11 @@ __device__ __forceinline__ void unit_round0(const K* __restrict__ src, K* __rest
 }
 
 // Level merge: persistent blocks, each over a contiguous range of work units.
-// Per unit: read its descriptor, copy its slices to shared memory, merge them
-// in tournament rounds, write the result.  Small blocks (128 threads, 2*C
-// elements of shared memory) keep many blocks resident per SM, which hides
-// the copy latency of one block behind the merging of the others.
+// Per unit: read its descriptor (the next one is prefetched), stage its slices
+// in shared memory (TMA bulk copies on an mbarrier for the aligned middles),
+// merge them in tournament rounds, and store the result with 16-byte stores.
+// Three blocks of 256 threads share an SM (two buffers of C + slack elements
+// each), so one block's staging overlaps the others' merging.
 template <typename K, bool V>
 __global__ void __launch_bounds__(kLvlThreads)
     k_level_merge(const UnitDesc* __restrict__ udesc, const uint64_t* __restrict__ ctr, const K* __restrict__ leaf,
@@ -1097,7 +1102,6 @@ MergeGeom merge_geom(int key_bytes, bool vals, int k) {
     else { g.c_fused = 4096; g.c_level = 4096; }
     g.tmax = g.c_fused;
     g.ts = g.c_level / (2u * (uint32_t)k);
-    g.q = g.c_level / 2;
     g.k = k;
     // persistent level merge: two buffers of c_level elements per block
     size_t lvl_smem = (size_t)2 * (g.c_level + kLvlPad) * ((size_t)key_bytes + (vals ? 4 : 0)) + 256;

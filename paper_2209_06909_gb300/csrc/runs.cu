@@ -11,8 +11,9 @@
 //     not lt : B->A, A->A, D->B          lt : B->D, A->B, D->D
 // and element 0 is always B.  A tile's effect is a map {B,A,D} -> {B,A,D}
 // plus, per entry state, the number of B states produced; maps compose
-// associatively, so the greedy scan becomes a reduce / scan / apply over
-// tiles.  Run i is descending iff key[s_i + 1] < key[s_i].
+// associatively, so the greedy scan becomes one pass: each tile scans its own
+// elements and takes its entry state and run offset from the tiles before it
+// (decoupled look-back).  Run i is descending iff key[s_i + 1] < key[s_i].
 //
 // Powers.  With run i-1 = [s_{i-1}, s_i) and run i = [s_i, s_{i+1}), Def. 3.1's
 // midpoints are a = (s_{i-1} + s_i) / 2n and b = (s_i + s_{i+1}) / 2n.  For a
