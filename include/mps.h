@@ -144,7 +144,8 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
  * arrays, and the launch sequence makes no host synchronisation, so it can be
  * captured in a CUDA graph (see mps_batch_graph_*).
  *   max_len : an upper bound on the longest array (sizes the level loop);
- *             0 means n.
+ *             0 means n.  An array longer than max_len is detected on the
+ *             device and reported as MPS_ERR_DEVICE_CHECK (status 16).
  *   k       : 2, 4, 8, or 0 for the fan-in chosen by mps_batch_autotune for
  *             this key type and mean array size (4 until tuned).
  * n must be below 2^31.  Workspace: mps_batch_workspace_size(n, m, kt,
