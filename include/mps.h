@@ -150,18 +150,24 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
  *             this key type and mean array size (4 until tuned).
  * n must be below 2^31.  Workspace: mps_batch_workspace_size(n, m, kt,
  * has_payload, k); k = 0 asks for the largest over k in {2, 4, 8}.
+ *   d_merge_costs : NULL, or device memory for m uint64 values that receives
+ *             each array's merge cost M = sum_i depth(run i) * L_i (Sec. 2.2)
+ *             in its own tree, the same value as sorting the array alone (0
+ *             for arrays of at most one run).  Written in stream order; a
+ *             graph (mps_batch_graph_*) rewrites it at every replay.
  * mps_sort_batch and mps_sort_batch_pairs synchronise the stream once at the
  * end to report device-side check failures. */
 mps_status mps_batch_workspace_size(uint64_t n, uint32_t m, mps_key_type kt, int has_payload, int k, size_t* bytes);
 
 mps_status mps_sort_batch(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
-                          uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes, cudaStream_t stream);
+                          uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes,
+                          uint64_t* d_merge_costs, cudaStream_t stream);
 
 /* Stable key-value form of mps_sort_batch (uint32 payload per key). */
 mps_status mps_sort_batch_pairs(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out,
                                 uint32_t* d_vals_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
                                 uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes,
-                                cudaStream_t stream);
+                                uint64_t* d_merge_costs, cudaStream_t stream);
 
 /* Times the batch with k = 2, 4 and 8 (keys only; the output buffer is
  * overwritten) and records the fastest for this key type and mean array
@@ -178,7 +184,7 @@ mps_status mps_batch_autotune(const void* d_keys_in, void* d_keys_out, const uin
 typedef struct mps_batch_graph mps_batch_graph;
 mps_status mps_batch_graph_create(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m,
                                   uint64_t n, uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes,
-                                  cudaStream_t stream, mps_batch_graph** out);
+                                  uint64_t* d_merge_costs, cudaStream_t stream, mps_batch_graph** out);
 mps_status mps_batch_graph_launch(mps_batch_graph* g, cudaStream_t stream, int check);
 mps_status mps_batch_graph_destroy(mps_batch_graph* g);
 
@@ -219,6 +225,7 @@ typedef struct {
     mps_status status;      /* MPS_OK, MPS_ERR_CANCELLED, MPS_ERR_DEVICE_CHECK, ... */
     uint32_t device_status; /* device-side check code when status is MPS_ERR_DEVICE_CHECK */
     uint64_t tag;
+    uint64_t merge_cost;    /* M of Sec. 2.2 for this request's array (0 unless status is MPS_OK) */
     double t_submit_ms, t_admit_ms, t_done_ms;  /* milliseconds since the queue was created */
 } mps_result;
 

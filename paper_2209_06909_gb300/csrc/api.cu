@@ -132,6 +132,7 @@ struct Plan {
         w.batch_off = nullptr;
         w.batch_m = 0;
         w.batch_max_len = 0;
+        w.batch_cost = nullptr;
         w.batch_prm = reinterpret_cast<uint2*>(b + o_bprm);
         return w;
     }
@@ -366,9 +367,10 @@ int power_bound(uint64_t max_len, int k) {
 template <typename K, bool V>
 mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, uint64_t n,
                       const uint64_t* d_off, uint32_t m, uint64_t max_len, int k, void* d_ws, size_t ws_bytes,
-                      bool sync_at_end, cudaStream_t st) {
+                      uint64_t* d_costs, bool sync_at_end, cudaStream_t st) {
     if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    if (d_costs && m) MPS_CUDA(cudaMemsetAsync(d_costs, 0, (size_t)m * 8, st));
     if (n == 0) return MPS_OK;
     if (!keys_in || !keys_out || !d_off || !d_ws || m == 0) return MPS_ERR_INVALID_ARG;
     if (V && (!vals_in || !vals_out)) return MPS_ERR_INVALID_ARG;
@@ -381,6 +383,7 @@ mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
     ws.batch_off = d_off;
     ws.batch_m = m;
     ws.batch_max_len = max_len;
+    ws.batch_cost = d_costs;
     const MergeGeom& g = plan.g;
     g_launches = 0;
     const uint32_t r_bound = (uint32_t)std::min<uint64_t>(plan.rmax, n + 1);
@@ -512,22 +515,22 @@ void set_tuned_k(mps_key_type kt, bool vals, uint64_t n, uint32_t m, int kk) {
 
 mps_status batch_dispatch(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out, uint64_t n,
                           const uint64_t* d_off, uint32_t m, uint64_t max_len, mps_key_type kt, int k, void* d_ws,
-                          size_t ws_bytes, bool sync_at_end, cudaStream_t st) {
+                          size_t ws_bytes, uint64_t* d_costs, bool sync_at_end, cudaStream_t st) {
     const bool vals = vals_in != nullptr || vals_out != nullptr;
     if (k == 0) k = tuned_k(kt, vals, n, m);
     if (kt == MPS_U32) {
         if (vals)
             return batch_impl<uint32_t, true>((const uint32_t*)keys_in, vals_in, (uint32_t*)keys_out, vals_out, n, d_off, m,
-                                              max_len, k, d_ws, ws_bytes, sync_at_end, st);
+                                              max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st);
         return batch_impl<uint32_t, false>((const uint32_t*)keys_in, nullptr, (uint32_t*)keys_out, nullptr, n, d_off, m,
-                                           max_len, k, d_ws, ws_bytes, sync_at_end, st);
+                                           max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st);
     }
     if (kt == MPS_U64) {
         if (vals)
             return batch_impl<uint64_t, true>((const uint64_t*)keys_in, vals_in, (uint64_t*)keys_out, vals_out, n, d_off, m,
-                                              max_len, k, d_ws, ws_bytes, sync_at_end, st);
+                                              max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st);
         return batch_impl<uint64_t, false>((const uint64_t*)keys_in, nullptr, (uint64_t*)keys_out, nullptr, n, d_off, m,
-                                           max_len, k, d_ws, ws_bytes, sync_at_end, st);
+                                           max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st);
     }
     return MPS_ERR_INVALID_ARG;
 }
@@ -558,17 +561,18 @@ mps_status mps_batch_workspace_size(uint64_t n, uint32_t m, mps_key_type kt, int
 }
 
 mps_status mps_sort_batch(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
-                          uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
-    return batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes, true,
-                          stream);
+                          uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes, uint64_t* d_merge_costs,
+                          cudaStream_t stream) {
+    return batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes,
+                          d_merge_costs, true, stream);
 }
 
 mps_status mps_sort_batch_pairs(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out, uint32_t* d_vals_out,
                                 const uint64_t* d_offsets, uint32_t m, uint64_t n, uint64_t max_len, mps_key_type kt, int k,
-                                void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+                                void* d_ws, size_t ws_bytes, uint64_t* d_merge_costs, cudaStream_t stream) {
     if (!d_vals_in || !d_vals_out) return n ? MPS_ERR_INVALID_ARG : MPS_OK;
     return batch_dispatch(d_keys_in, d_vals_in, d_keys_out, d_vals_out, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes,
-                          true, stream);
+                          d_merge_costs, true, stream);
 }
 
 mps_status mps_batch_autotune(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
@@ -580,13 +584,13 @@ mps_status mps_batch_autotune(const void* d_keys_in, void* d_keys_out, const uin
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return MPS_ERR_CUDA;
     mps_status s = MPS_OK;
     for (int kk : {2, 4, 8}) {
-        s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, kk, d_ws, ws_bytes, true,
-                           stream);
+        s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, kk, d_ws, ws_bytes,
+                           nullptr, true, stream);
         if (s != MPS_OK) break;
         cudaEventRecord(a, stream);
         for (int rep = 0; rep < 2; rep++)
-            batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, kk, d_ws, ws_bytes, false,
-                           stream);
+            batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, kk, d_ws, ws_bytes,
+                           nullptr, false, stream);
         cudaEventRecord(b, stream);
         if (cudaEventSynchronize(b) != cudaSuccess) { s = MPS_ERR_CUDA; break; }
         float ms = 0.f;
@@ -602,13 +606,13 @@ mps_status mps_batch_autotune(const void* d_keys_in, void* d_keys_out, const uin
 }
 
 mps_status mps_batch_graph_create(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
-                                  uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes, cudaStream_t stream,
-                                  mps_batch_graph** out) {
+                                  uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes,
+                                  uint64_t* d_merge_costs, cudaStream_t stream, mps_batch_graph** out) {
     if (!out || !stream) return MPS_ERR_INVALID_ARG;
     *out = nullptr;
     // one direct run validates the arguments and sets kernel attributes
     mps_status s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes,
-                                  true, stream);
+                                  d_merge_costs, true, stream);
     if (s != MPS_OK) return s;
     mps_batch_graph* g = new mps_batch_graph();
     g->counters = reinterpret_cast<uint64_t*>(d_ws);
@@ -616,8 +620,8 @@ mps_status mps_batch_graph_create(const void* d_keys_in, void* d_keys_out, const
         delete g;
         return MPS_ERR_CUDA;
     }
-    s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes, false,
-                       stream);
+    s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes,
+                       d_merge_costs, false, stream);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(stream, &graph);
     if (s != MPS_OK || e != cudaSuccess || !graph) {

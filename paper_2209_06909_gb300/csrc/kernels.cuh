@@ -88,6 +88,7 @@ struct WsView {
     const uint64_t* batch_off;     // [m+1] array starts, batch_off[m] = n
     uint32_t batch_m;
     uint64_t batch_max_len;        // caller's bound on the longest array (0: none)
+    uint64_t* batch_cost;          // [m] merge cost per array, or nullptr
     uint2* batch_prm;              // [2m] per-array power parameters
 };
 

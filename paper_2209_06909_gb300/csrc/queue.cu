@@ -28,7 +28,7 @@
 namespace mps {
 mps_status batch_dispatch(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out, uint64_t n,
                           const uint64_t* d_off, uint32_t m, uint64_t max_len, mps_key_type kt, int k, void* d_ws,
-                          size_t ws_bytes, bool sync_at_end, cudaStream_t st);
+                          size_t ws_bytes, uint64_t* d_costs, bool sync_at_end, cudaStream_t st);
 }
 
 namespace {
@@ -182,7 +182,9 @@ struct mps_queue {
     std::vector<cudaStream_t> streams;
     std::vector<int> stream_busy;
     std::vector<uint64_t*> h_off;     // pinned offsets staging, one per stream
-    std::vector<uint32_t*> h_status;  // pinned device-status readback, one per stream
+    // pinned readback, one per stream: the device status word, then at byte 8
+    // the merge cost of each request of the stream's batch
+    std::vector<uint32_t*> h_status;
     PoolAllocator alloc{0};
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -212,9 +214,10 @@ mps_status launch_batch(mps_queue* q, std::vector<uint64_t>& ids, int sidx, Batc
     size_t ws = 0;
     mps_status s = mps_batch_workspace_size(n, m, kt, vals, q->cfg.k ? q->cfg.k : 4, &ws);
     if (s != MPS_OK) return s;
-    // offsets (m + 1) and the request pointer table (m) travel in one copy
+    // offsets (m + 1) and the request pointer table (m) travel in one copy;
+    // the per-request merge costs (m) follow them in the same pool block
     const size_t tab_bytes = (size_t)(m + 1) * 8 + (size_t)m * sizeof(ReqPtrs);
-    const size_t sizes[6] = {n * kb, n * kb, vals ? n * 4 : 0, vals ? n * 4 : 0, tab_bytes, ws};
+    const size_t sizes[6] = {n * kb, n * kb, vals ? n * 4 : 0, vals ? n * 4 : 0, tab_bytes + (size_t)m * 8, ws};
     size_t offs[6];
     for (int i = 0; i < 6; i++) {
         if (!q->alloc.alloc(sizes[i], &offs[i])) {
@@ -244,15 +247,19 @@ mps_status launch_batch(mps_queue* q, std::vector<uint64_t>& ids, int sidx, Batc
     }
     h_off[m] = acc;
     const ReqPtrs* d_tab = reinterpret_cast<const ReqPtrs*>(d_off + (m + 1));
+    uint64_t* d_cost = reinterpret_cast<uint64_t*>(pool + offs[4] + tab_bytes);
     cudaMemcpyAsync(d_off, h_off, tab_bytes, cudaMemcpyHostToDevice, st);
-    *q->h_status[sidx] = 0;  // the stream is idle: no copy into this buffer is pending
+    // the stream is idle: no copy into its readback buffer is pending
+    uint32_t* h_st = q->h_status[sidx];
+    std::memset(h_st, 0, 8 + (size_t)m * 8);
     if (n) {
         move_requests(true, kt, vals, d_tab, d_off, m, n, kin, vin, nullptr, nullptr, st);
-        s = mps::batch_dispatch(kin, vin, kout, vout, n, d_off, m, max_len, kt, q->cfg.k ? q->cfg.k : 4, d_ws, ws, false,
-                                st);
+        s = mps::batch_dispatch(kin, vin, kout, vout, n, d_off, m, max_len, kt, q->cfg.k ? q->cfg.k : 4, d_ws, ws, d_cost,
+                                false, st);
         if (s != MPS_OK) return s;
         // device status word: entry 5 of the workspace's leading 64-bit counter block
-        cudaMemcpyAsync(q->h_status[sidx], reinterpret_cast<char*>(d_ws) + 5 * 8, 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(h_st, reinterpret_cast<char*>(d_ws) + 5 * 8, 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(reinterpret_cast<char*>(h_st) + 8, d_cost, (size_t)m * 8, cudaMemcpyDeviceToHost, st);
         move_requests(false, kt, vals, d_tab, d_off, m, n, nullptr, nullptr, kout, vout, st);
     }
     if (cudaEventCreateWithFlags(&B.done, cudaEventDisableTiming) != cudaSuccess) return MPS_ERR_CUDA;
@@ -270,14 +277,16 @@ void release_batch(mps_queue* q, Batch& B) {
     B.done = nullptr;
 }
 
-void finish_tickets(mps_queue* q, const std::vector<uint64_t>& ids, mps_status s, uint32_t dev_status = 0) {
+void finish_tickets(mps_queue* q, const std::vector<uint64_t>& ids, mps_status s, uint32_t dev_status = 0,
+                    const uint64_t* costs = nullptr) {
     const auto now = Clock::now();
-    for (uint64_t id : ids) {
-        Ticket& t = q->tickets[id];
+    for (size_t i = 0; i < ids.size(); i++) {
+        Ticket& t = q->tickets[ids[i]];
         t.done = true;
         t.t_done = now;
         t.res.status = s;
         t.res.device_status = dev_status;
+        t.res.merge_cost = (costs && s == MPS_OK) ? costs[i] : 0;
         t.res.tag = t.req.tag;
         t.res.t_submit_ms = ms_since(q->t0, t.t_submit);
         t.res.t_admit_ms = ms_since(q->t0, t.t_admit);
@@ -296,7 +305,7 @@ void worker_main(mps_queue* q) {
             if (e == cudaErrorNotReady) { i++; continue; }
             const uint32_t dev = *q->h_status[B.stream];
             mps_status s = e == cudaSuccess ? (dev ? (dev == mps::kDevSpin ? MPS_ERR_TIMEOUT : MPS_ERR_DEVICE_CHECK) : MPS_OK) : MPS_ERR_CUDA;
-            finish_tickets(q, B.tickets, s, dev);
+            finish_tickets(q, B.tickets, s, dev, reinterpret_cast<const uint64_t*>(q->h_status[B.stream] + 2));
             q->stream_busy[B.stream] = 0;
             release_batch(q, B);
             q->inflight.erase(q->inflight.begin() + i);
@@ -377,7 +386,7 @@ mps_status mps_queue_create(const mps_queue_config* cfg, mps_queue** out) {
         if (cudaStreamCreateWithFlags(&q->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
             cudaMallocHost(&q->h_off[i], ((size_t)q->cfg.max_batch + 1) * 8 + (size_t)q->cfg.max_batch * sizeof(ReqPtrs)) !=
                 cudaSuccess ||
-            cudaMallocHost(&q->h_status[i], 8) != cudaSuccess) {
+            cudaMallocHost(&q->h_status[i], 8 + (size_t)q->cfg.max_batch * 8) != cudaSuccess) {
             for (uint32_t j = 0; j <= i; j++) {
                 if (q->streams[j]) cudaStreamDestroy(q->streams[j]);
                 if (q->h_off[j]) cudaFreeHost(q->h_off[j]);

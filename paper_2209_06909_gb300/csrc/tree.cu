@@ -251,14 +251,22 @@ __device__ __forceinline__ uint32_t small_power(uint64_t nmax, uint64_t longest,
 // small_power().  Optionally writes the leaf depths, and adds to the counters
 // the merge cost M = sum_i depth(run i) L_i (Sec. 2.2) and the number of nodes.
 // Each thread holds 16 boundaries: 16-byte loads of powers and run starts and
-// one 16-byte store of node_info.
+// one 16-byte store of node_info.  With kArr (a batch whose caller asked for
+// per-array costs) each run's term depth * L is also added to the cost of the
+// array that holds it, arr_cost[a] for off[a] <= run start < off[a+1]: the
+// tree of a batch has every array as a root, so a run's depth counts the
+// merges inside its own array only and M of the array is Sec. 2.2's M of that
+// array sorted alone.
+template <bool kArr>
 __global__ void __launch_bounds__(kMaskThreads, 3) k_mask_apply(const uint8_t* __restrict__ powers, uint64_t* __restrict__ ctr,
                                                              const uint32_t* __restrict__ rs,
                                                              const unsigned long long* __restrict__ fpre,
                                                              const unsigned long long* __restrict__ gsuf,
                                                              uint8_t* __restrict__ node_info, uint8_t* __restrict__ leaf_depth,
                                                              uint64_t n_single, uint32_t log2k, uint32_t tmax,
-                                                             uint32_t* __restrict__ cand, uint32_t cand_cap) {
+                                                             uint32_t* __restrict__ cand, uint32_t cand_cap,
+                                                             const uint64_t* __restrict__ off, uint32_t m,
+                                                             unsigned long long* __restrict__ arr_cost) {
     static_assert(kMaskItems == 16, "one 16-byte word of node_info per thread");
     __shared__ unsigned long long tmp[kMaskThreads / 32 + 1];
     const uint32_t r = (uint32_t)ctr[kCtrR];
@@ -311,6 +319,29 @@ __global__ void __launch_bounds__(kMaskThreads, 3) k_mask_apply(const uint8_t* _
         sg = OpG()(e, sg);
     }
     unsigned long long cost = 0, nodes = 0;
+    // kArr: array a holds the run being counted, acost its running sum
+    uint32_t a = 0;
+    uint64_t a_end = 0;
+    unsigned long long acost = 0;
+    auto credit = [&](uint32_t start, unsigned long long t) {
+        if (start >= a_end) {
+            if (acost) atomicAdd(arr_cost + a, acost);
+            acost = 0;
+            do a_end = off[++a + 1]; while (start >= a_end);
+        }
+        acost += t;
+    };
+    if (kArr && live) {
+        // last array a < m with off[a] <= first run start of this thread
+        const uint32_t s0 = b0 == 0 ? rv[0] : rv[1];
+        uint32_t lo = 0, hi = m - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= s0) lo = mid; else hi = mid - 1;
+        }
+        a = lo;
+        a_end = off[a + 1];
+    }
     uint32_t word[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int q = 0; q < kMaskItems; q++) {
@@ -328,15 +359,20 @@ __global__ void __launch_bounds__(kMaskThreads, 3) k_mask_apply(const uint8_t* _
             nodes += start;
             const uint32_t incl = mbits(OpF()(pf, e));
             const uint32_t dj = (uint32_t)__popc(incl | right);  // depth of run j
-            cost += (unsigned long long)dj * (rv[q + 2] - rv[q + 1]);
             if (j == 1) {
-                cost += (unsigned long long)d0 * (rv[1] - rv[0]);
+                const unsigned long long t0 = (unsigned long long)d0 * (rv[1] - rv[0]);
+                cost += t0;
+                if (kArr) credit(rv[0], t0);
                 if (leaf_depth) leaf_depth[0] = (uint8_t)d0;
             }
+            const unsigned long long tj = (unsigned long long)dj * (rv[q + 2] - rv[q + 1]);
+            cost += tj;
+            if (kArr) credit(rv[q + 1], tj);
             if (leaf_depth) leaf_depth[j] = (uint8_t)dj;
         }
         pf = OpF()(pf, e);
     }
+    if (kArr && acost) atomicAdd(arr_cost + a, acost);
     if (live) *reinterpret_cast<uint4*>(node_info + b0) = make_uint4(word[0], word[1], word[2], word[3]);
     // append the marked starts to the candidate list of the node pass (one
     // atomic per warp that has any)
@@ -643,9 +679,15 @@ void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, uint64_t n, i
     k_mask_reduce<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.mt_f, ws.mt_g);
     k_mask_scan<<<1, 1024, 0, st>>>(ws.mt_f, ws.mt_g, tiles, ws.mt_fpre, ws.mt_gsuf);
     const uint32_t log2k = k == 2 ? 1u : (k == 4 ? 2u : 3u);
-    k_mask_apply<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.run_starts, ws.mt_fpre, ws.mt_gsuf, ws.node_info,
-                                                  dump_leaf ? leaf_depth : nullptr, ws.batch_off ? 0ull : n, log2k, tmax,
-                                                  ws.canon_idx, ws.cand_cap);
+    if (ws.batch_cost)
+        k_mask_apply<true><<<tiles, kMaskThreads, 0, st>>>(
+            ws.powers, ws.counters, ws.run_starts, ws.mt_fpre, ws.mt_gsuf, ws.node_info, dump_leaf ? leaf_depth : nullptr,
+            0ull, log2k, tmax, ws.canon_idx, ws.cand_cap, ws.batch_off, ws.batch_m,
+            reinterpret_cast<unsigned long long*>(ws.batch_cost));
+    else
+        k_mask_apply<false><<<tiles, kMaskThreads, 0, st>>>(
+            ws.powers, ws.counters, ws.run_starts, ws.mt_fpre, ws.mt_gsuf, ws.node_info, dump_leaf ? leaf_depth : nullptr,
+            ws.batch_off ? 0ull : n, log2k, tmax, ws.canon_idx, ws.cand_cap, nullptr, 0u, nullptr);
     g_launches += 3;
 }
 

@@ -48,7 +48,11 @@ class Request(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("device_status", ctypes.c_uint32), ("tag", ctypes.c_uint64),
-                ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+                ("merge_cost", ctypes.c_uint64), ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+
+
+def _result_dict(res: "Result") -> dict:
+    return {name: getattr(res, name) for name, _ in Result._fields_}
 
 
 class ProfileEntry(ctypes.Structure):
@@ -100,10 +104,10 @@ def lib():
     L.mps_sort_keys_noalloc.restype = I
     U32 = ctypes.c_uint32
     L.mps_batch_workspace_size.argtypes = [U64, U32, I, I, I, ctypes.POINTER(ctypes.c_size_t)]
-    L.mps_sort_batch.argtypes = [P, P, P, U32, U64, U64, I, I, P, ctypes.c_size_t, P]
-    L.mps_sort_batch_pairs.argtypes = [P, P, P, P, P, U32, U64, U64, I, I, P, ctypes.c_size_t, P]
+    L.mps_sort_batch.argtypes = [P, P, P, U32, U64, U64, I, I, P, ctypes.c_size_t, P, P]
+    L.mps_sort_batch_pairs.argtypes = [P, P, P, P, P, U32, U64, U64, I, I, P, ctypes.c_size_t, P, P]
     L.mps_batch_autotune.argtypes = [P, P, P, U32, U64, U64, I, P, ctypes.c_size_t, P, ctypes.POINTER(I)]
-    L.mps_batch_graph_create.argtypes = [P, P, P, U32, U64, U64, I, I, P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    L.mps_batch_graph_create.argtypes = [P, P, P, U32, U64, U64, I, I, P, ctypes.c_size_t, P, P, ctypes.POINTER(P)]
     L.mps_batch_graph_launch.argtypes = [P, P, I]
     L.mps_batch_graph_destroy.argtypes = [P]
     for fn in ("mps_batch_workspace_size", "mps_sort_batch", "mps_sort_batch_pairs", "mps_batch_autotune",
@@ -302,20 +306,27 @@ def batch_workspace(n: int, m: int, key_bytes: int, has_payload: bool = False, k
     return torch.empty(max(out.value, 16), dtype=torch.uint8, device=device)
 
 
+def _ptr(t: torch.Tensor | None):
+    return t.data_ptr() if t is not None else None
+
+
 def sort_batch(keys: torch.Tensor, offsets: torch.Tensor, k: int = 0, out: torch.Tensor | None = None,
-               ws: torch.Tensor | None = None, max_len: int = 0, stream=None) -> torch.Tensor:
+               ws: torch.Tensor | None = None, max_len: int = 0, stream=None,
+               merge_costs: torch.Tensor | None = None) -> torch.Tensor:
     """Sorts every array of a batch (mps_sort_batch); offsets: int64 device
-    tensor of m+1 array starts."""
+    tensor of m+1 array starts.  merge_costs: optional int64 device tensor of
+    m entries that receives each array's merge cost."""
     n, m = keys.numel(), offsets.numel() - 1
     out = torch.empty_like(keys) if out is None else out
     ws = batch_workspace(n, m, keys.element_size(), False, k, keys.device) if ws is None else ws
     _check("mps_sort_batch", lib().mps_sort_batch(keys.data_ptr(), out.data_ptr(), offsets.data_ptr(), m, n, max_len,
-                                                  _key_type(keys), k, ws.data_ptr(), ws.numel(), _stream(stream)))
+                                                  _key_type(keys), k, ws.data_ptr(), ws.numel(), _ptr(merge_costs),
+                                                  _stream(stream)))
     return out
 
 
 def sort_batch_pairs(keys: torch.Tensor, vals: torch.Tensor, offsets: torch.Tensor, k: int = 0, out_keys=None,
-                     out_vals=None, ws=None, max_len: int = 0, stream=None):
+                     out_vals=None, ws=None, max_len: int = 0, stream=None, merge_costs: torch.Tensor | None = None):
     n, m = keys.numel(), offsets.numel() - 1
     out_keys = torch.empty_like(keys) if out_keys is None else out_keys
     out_vals = torch.empty_like(vals) if out_vals is None else out_vals
@@ -323,7 +334,7 @@ def sort_batch_pairs(keys: torch.Tensor, vals: torch.Tensor, offsets: torch.Tens
     _check("mps_sort_batch_pairs", lib().mps_sort_batch_pairs(keys.data_ptr(), vals.data_ptr(), out_keys.data_ptr(),
                                                               out_vals.data_ptr(), offsets.data_ptr(), m, n, max_len,
                                                               _key_type(keys), k, ws.data_ptr(), ws.numel(),
-                                                              _stream(stream)))
+                                                              _ptr(merge_costs), _stream(stream)))
     return out_keys, out_vals
 
 
@@ -340,13 +351,13 @@ def batch_autotune(keys: torch.Tensor, offsets: torch.Tensor, out: torch.Tensor,
 class BatchGraph:
     """A batch sort captured once in a CUDA graph (mps_batch_graph_*)."""
 
-    def __init__(self, keys, offsets, out, ws, k=0, max_len=0, stream=None):
+    def __init__(self, keys, offsets, out, ws, k=0, max_len=0, stream=None, merge_costs=None):
         self.handle = ctypes.c_void_p()
-        self.keep = (keys, offsets, out, ws)
+        self.keep = (keys, offsets, out, ws, merge_costs)
         n, m = keys.numel(), offsets.numel() - 1
         _check("mps_batch_graph_create", lib().mps_batch_graph_create(
             keys.data_ptr(), out.data_ptr(), offsets.data_ptr(), m, n, max_len, _key_type(keys), k, ws.data_ptr(),
-            ws.numel(), _stream(stream), ctypes.byref(self.handle)))
+            ws.numel(), _ptr(merge_costs), _stream(stream), ctypes.byref(self.handle)))
 
     def launch(self, stream=None, check=False):
         _check("mps_batch_graph_launch", lib().mps_batch_graph_launch(self.handle, _stream(stream), int(check)))
@@ -388,8 +399,7 @@ class Queue:
         code = lib().mps_queue_wait(self.handle, ticket, timeout_ms, ctypes.byref(res))
         _check("mps_queue_wait", code)
         self.keep.pop(ticket, None)
-        return {"status": res.status, "device_status": res.device_status, "tag": res.tag,
-                "t_submit_ms": res.t_submit_ms, "t_admit_ms": res.t_admit_ms, "t_done_ms": res.t_done_ms}
+        return _result_dict(res)
 
     def poll(self, ticket: int):
         res = Result()
@@ -398,8 +408,7 @@ class Queue:
             return None
         _check("mps_queue_poll", code)
         self.keep.pop(ticket, None)
-        return {"status": res.status, "tag": res.tag, "t_submit_ms": res.t_submit_ms, "t_admit_ms": res.t_admit_ms,
-                "t_done_ms": res.t_done_ms}
+        return _result_dict(res)
 
     def pause(self, paused: bool = True):
         _check("mps_queue_pause", lib().mps_queue_pause(self.handle, int(paused)))

@@ -2,8 +2,9 @@
 
 Each array of a batch is its own Multiway Powersort problem: its own runs,
 powers (Def. 3.1 with the array's length) and merge tree.  The batch output
-must equal the concatenation of the per-array sorts, and the reported merge
-cost must equal the sum of the oracle's per-array merge costs.
+must equal the concatenation of the per-array sorts, each array's merge cost
+(Sec. 2.2) must equal the oracle's for that array sorted alone, and the
+reported total must equal their sum.
 """
 import numpy as np
 import pytest
@@ -54,8 +55,15 @@ def make_batch(seed, count, dtype=np.uint32, max_log2=15):
     return arrays, offsets
 
 
-def oracle_cost(arrays, k):
-    return sum(oracle.sort(a, k=k, want_tree=False)["merge_cost"] for a in arrays if a.size)
+def oracle_costs(arrays, k):
+    """Merge cost of every array sorted alone (0 for an empty array)."""
+    return np.array([oracle.sort(a, k=k, want_tree=False)["merge_cost"] if a.size else 0 for a in arrays],
+                    dtype=np.int64)
+
+
+def cost_buffer(m):
+    # filled with garbage: the call must overwrite every entry
+    return torch.full((m,), -1, dtype=torch.int64, device=DEV)
 
 
 @pytest.mark.parametrize("k", [2, 4, 8])
@@ -63,12 +71,16 @@ def test_batch_keys(k):
     arrays, offsets = make_batch(10 + k, 120)
     keys = np.concatenate(arrays)
     d_off = torch.from_numpy(offsets.view(np.int64)).to(DEV)
-    out = mps.sort_batch(mps.to_device(keys, DEV), d_off, k=k, max_len=int(max(a.size for a in arrays)))
+    costs = cost_buffer(len(arrays))
+    out = mps.sort_batch(mps.to_device(keys, DEV), d_off, k=k, max_len=int(max(a.size for a in arrays)),
+                         merge_costs=costs)
     torch.cuda.synchronize()
     got = mps.to_numpy(out, np.uint32)
     want = np.concatenate([np.sort(a) for a in arrays])
     assert np.array_equal(got, want)
-    assert mps.last_stats()["merge_cost"] == oracle_cost(arrays, k)
+    want_costs = oracle_costs(arrays, k)
+    assert np.array_equal(costs.cpu().numpy(), want_costs)
+    assert mps.last_stats()["merge_cost"] == int(want_costs.sum())
 
 
 def test_batch_large_arrays_level_merges():
@@ -76,10 +88,50 @@ def test_batch_large_arrays_level_merges():
     arrays, offsets = make_batch(77, 16, max_log2=19)
     keys = np.concatenate(arrays)
     d_off = torch.from_numpy(offsets.view(np.int64)).to(DEV)
-    out = mps.sort_batch(mps.to_device(keys, DEV), d_off, k=4)
+    costs = cost_buffer(len(arrays))
+    out = mps.sort_batch(mps.to_device(keys, DEV), d_off, k=4, merge_costs=costs)
     torch.cuda.synchronize()
     assert np.array_equal(mps.to_numpy(out, np.uint32), np.concatenate([np.sort(a) for a in arrays]))
-    assert mps.last_stats()["merge_cost"] == oracle_cost(arrays, 4)
+    want_costs = oracle_costs(arrays, 4)
+    assert np.array_equal(costs.cpu().numpy(), want_costs)
+    assert mps.last_stats()["merge_cost"] == int(want_costs.sum())
+
+
+def test_batch_costs_many_small_and_empty_arrays():
+    """Per-array costs where many arrays share one mask tile, with empty arrays
+    between them (the cost of an array depends on its runs only)."""
+    rng = np.random.default_rng(2024)
+    arrays = []
+    for i in range(3000):
+        m = 0 if i % 7 == 3 else int(rng.integers(1, 200))
+        arrays.append(inputs.random_runs_uniform_len(m, int(rng.integers(1 << 40)), hi=max(2, m // 3)).astype(np.uint32)
+                      if m else np.zeros(0, np.uint32))
+    offsets = np.zeros(len(arrays) + 1, np.uint64)
+    offsets[1:] = np.cumsum([a.size for a in arrays])
+    keys = np.concatenate(arrays)
+    d_off = torch.from_numpy(offsets.view(np.int64)).to(DEV)
+    costs = cost_buffer(len(arrays))
+    out = mps.sort_batch(mps.to_device(keys, DEV), d_off, k=4, merge_costs=costs)
+    torch.cuda.synchronize()
+    assert np.array_equal(mps.to_numpy(out, np.uint32), np.concatenate([np.sort(a) for a in arrays]))
+    assert np.array_equal(costs.cpu().numpy(), oracle_costs(arrays, 4))
+
+
+def test_batch_longer_than_max_len_is_reported():
+    """An array longer than the caller's max_len is a device-side check
+    failure (status 16), not a silently short level loop."""
+    arrays, offsets = make_batch(9, 40, max_log2=14)
+    keys = np.concatenate(arrays)
+    d_off = torch.from_numpy(offsets.view(np.int64)).to(DEV)
+    longest = int(max(a.size for a in arrays))
+    with pytest.raises(mps.MpsError) as ei:
+        mps.sort_batch(mps.to_device(keys, DEV), d_off, k=4, max_len=longest - 1)
+    assert mps.STATUS[ei.value.code] == "device-side check failed"
+    assert mps.last_stats()["device_status"] == 16
+    # the same batch with a sufficient bound sorts
+    out = mps.sort_batch(mps.to_device(keys, DEV), d_off, k=4, max_len=longest)
+    torch.cuda.synchronize()
+    assert np.array_equal(mps.to_numpy(out, np.uint32), np.concatenate([np.sort(a) for a in arrays]))
 
 
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
@@ -89,8 +141,10 @@ def test_batch_pairs_stable(dtype):
     keys = np.concatenate(arrays)
     vals = np.arange(keys.size, dtype=np.uint32)
     d_off = torch.from_numpy(offsets.view(np.int64)).to(DEV)
-    ok, ov = mps.sort_batch_pairs(mps.to_device(keys, DEV), mps.to_device(vals, DEV), d_off, k=4)
+    costs = cost_buffer(len(arrays))
+    ok, ov = mps.sort_batch_pairs(mps.to_device(keys, DEV), mps.to_device(vals, DEV), d_off, k=4, merge_costs=costs)
     torch.cuda.synchronize()
+    assert np.array_equal(costs.cpu().numpy(), oracle_costs(arrays, 4))
     want_k, want_v = [], []
     for i, a in enumerate(arrays):
         idx = np.arange(offsets[i], offsets[i + 1], dtype=np.uint32)
@@ -111,10 +165,14 @@ def test_batch_graph_and_autotune():
     best = mps.batch_autotune(d_in, d_off, out, ws)
     assert best in (2, 4, 8)
     stream = torch.cuda.Stream()
+    costs = cost_buffer(len(arrays))
+    want_costs = oracle_costs(arrays, best)
     with torch.cuda.stream(stream):
-        g = mps.BatchGraph(d_in, d_off, out, ws, k=0, stream=stream)
+        g = mps.BatchGraph(d_in, d_off, out, ws, k=0, stream=stream, merge_costs=costs)
         for _ in range(2):
             out.fill_(-1)
+            costs.fill_(-1)
             g.launch(stream=stream, check=True)
             assert np.array_equal(mps.to_numpy(out, np.uint32), np.concatenate([np.sort(a) for a in arrays]))
+            assert np.array_equal(costs.cpu().numpy(), want_costs)  # rewritten by every replay
         g.close()

@@ -2,7 +2,7 @@
 
 Requests of both kinds (uint32 keys; uint64 keys with uint32 payloads) are
 submitted together; every result must be bit for bit the sort the request
-gets alone through mps_sort_keys / mps_sort_pairs.  Failures are made on the
+gets alone through mps_sort_keys / mps_sort_pairs, with the same merge cost.  Failures are made on the
 host: an over-budget request, a malformed request, a wait that runs out while
 admission is paused, and destroy with requests still pending.
 """
@@ -44,12 +44,14 @@ def make_requests(seed, count):
 
 
 def alone(kind, a, v):
+    """The request's sort and merge cost through the single-array calls."""
     if a.size == 0:
-        return a, v
+        return a, v, 0
     if kind == "keys":
-        return mps.to_numpy(mps.sort_keys(mps.to_device(a, DEV), k=4), a.dtype), None
+        ok = mps.to_numpy(mps.sort_keys(mps.to_device(a, DEV), k=4), a.dtype)
+        return ok, None, mps.last_stats()["merge_cost"]
     ok, ov = mps.sort_pairs(mps.to_device(a, DEV), mps.to_device(v, DEV), k=4)
-    return mps.to_numpy(ok, a.dtype), mps.to_numpy(ov, np.uint32)
+    return mps.to_numpy(ok, a.dtype), mps.to_numpy(ov, np.uint32), mps.last_stats()["merge_cost"]
 
 
 def test_mixed_requests_match_alone():
@@ -93,8 +95,9 @@ def test_mixed_requests_match_alone():
     assert len(results) == len(reqs)
     for i, d_out, dvo in bufs:
         kind, a, v = reqs[i]
-        wk, wv = alone(kind, a, v)
+        wk, wv, wcost = alone(kind, a, v)
         assert np.array_equal(mps.to_numpy(d_out, a.dtype), wk), i
+        assert results[i]["merge_cost"] == wcost, i
         if kind == "pairs":
             assert np.array_equal(mps.to_numpy(dvo, np.uint32), wv), i
 
