@@ -292,7 +292,8 @@ typedef struct {
     uint32_t device_status;             /* device-side check code (0 = none): 1 node degree > k,
                                            2 capacity, 3 tile overflow, 11-15 work-unit / fused /
                                            lone-run ranges, 16 array longer than max_len, 17 a
-                                           bounded wait ran out (returned as MPS_ERR_TIMEOUT) */
+                                           bounded wait ran out (returned as MPS_ERR_TIMEOUT),
+                                           18 a splitter ranked outside its node (unsorted child) */
     uint32_t pad;
 } mps_stats;
 

@@ -49,7 +49,7 @@ struct Plan {
     int nlv_max = 0;
     // offsets
     size_t o_ctr, o_lvloff, o_det_state, o_rs, o_rdesc, o_fused, o_canon, o_lv[kMinTreeLevels], o_info,
-        o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_ufirst, o_ptiles, o_hist, o_ktmp, o_vtmp, total;
+        o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_ufirst, o_ptiles, o_isz, o_hist, o_ktmp, o_vtmp, total;
 
     uint32_t m = 0;  // arrays of a batch (0: a single array)
     size_t o_bprm = 0;
@@ -89,6 +89,7 @@ struct Plan {
         o_udesc = take((size_t)unit_cap * 128);
         o_ufirst = take((size_t)unit_cap * 4);
         o_ptiles = take((size_t)(unit_cap / kPackTile + 2) * 4);
+        o_isz = take((size_t)(unit_cap + 64) * 4);  // padded for 16-byte loads past the last interval
         o_hist = take(mask_tiles * kMaxLevels * 4);
         o_bprm = take((size_t)2 * std::max<uint32_t>(m, 1) * 8);
         o_ktmp = take(n * kb);
@@ -123,6 +124,7 @@ struct Plan {
         w.unit_desc = b + o_udesc;
         w.unit_first = reinterpret_cast<uint32_t*>(b + o_ufirst);
         w.pack_tiles = reinterpret_cast<uint32_t*>(b + o_ptiles);
+        w.ivl_size = reinterpret_cast<uint32_t*>(b + o_isz);
         w.unit_cap = unit_cap;
         w.canon_idx = reinterpret_cast<uint32_t*>(b + o_canon);
         w.cand_cap = (uint32_t)(rmax + 1);
@@ -300,11 +302,18 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     g_last.hbm_nodes = hbm_total;
     g_last.num_levels = (uint32_t)__builtin_popcountll(h_ctr[kCtrLevelBits]);
 
+    // merge cost of the nodes above T_max (one level-merge launch per power);
+    // the rest of M belongs to the nodes merged inside fused subtrees
+    uint64_t m_levels = 0;
+    for (int p = 1; p < kMaxLevels; p++) m_levels += h_ctr[kCtrHbmCount + p] ? h_ctr[kCtrHbmSize + p] : 0;
+    const uint64_t m_fused = g_last.merge_cost >= m_levels ? g_last.merge_cost - m_levels : 0;
     if (move_keys) {
         if (hbm_total) launch_bucket((uint32_t)hbm_total, ws, st);
         if (h_ctr[kCtrFrontier]) {
-            // algorithmic bytes: each element of a fused subtree is read and written once
-            ProfScope ps("fused_merge", 2.0 * b * (double)h_ctr[kCtrFrontierElems], st);
+            // algorithmic bytes (Sec. 2.2 cost model): one read and one write of
+            // b bytes per element per merge, i.e. 2 b M_fused; the kernel itself
+            // reads and writes each element of its subtrees once
+            ProfScope ps("fused_merge", 2.0 * b * (double)m_fused, st);
             launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, h_ctr[kCtrFrontier], g, ws, st);
         }
         uint64_t lvl_bytes = 0;
@@ -345,7 +354,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     MPS_CUDA(cudaStreamSynchronize(st));
     g_last.device_status = status;
     if (status) return device_error(status);
-    g_last.bytes_fused = (uint64_t)(2 * b * (double)h_ctr[kCtrFrontierElems]);
+    g_last.bytes_fused = (uint64_t)(2 * b * (double)m_fused);
     g_last.launches = g_launches;
     return MPS_OK;
 }

@@ -22,6 +22,7 @@ enum DevError : uint32_t {
     kDevPackNode = 15,   // packing saw an interval outside its level's nodes
     kDevMaxLen = 16,     // a batch array was longer than the caller's max_len
     kDevSpin = 17,       // a bounded wait on another block ran out
+    kDevSplitSlot = 18,  // a splitter ranked outside its node's splitters (children not sorted)
 };
 
 __device__ __forceinline__ void dev_fail(uint32_t* status, uint32_t code) { atomicCAS(status, 0u, code); }

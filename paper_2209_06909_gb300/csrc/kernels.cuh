@@ -8,7 +8,7 @@
 namespace mps {
 
 constexpr int kDetTile = 8192;     // elements per run-detection tile
-constexpr int kPackTile = 512;     // splitter intervals per unit-packing tile
+constexpr int kPackTile = 8192;    // splitter intervals per unit-packing block (64 per thread)
 constexpr int kMaskTile = 4096;    // boundaries per mask-scan tile
 constexpr int kMaxLevels = 64;     // bound on distinct powers (P <= 32 for n < 2^31)
 constexpr int kMinTreeLevels = 8;  // fan-out 32 min-tree over the powers
@@ -33,7 +33,6 @@ enum : int {
     kCtrMaxLen = 204,   // longest array of a batch (elements)
     kCtrDetTile = 205,  // next run-detection tile to take
     kCtrCand = 206,     // node-pass candidates listed by the mask pass
-    kCtrMaxIvl = 207,   // largest splitter interval of the current level
     kCtrWords = 256
 };
 
@@ -77,6 +76,7 @@ struct WsView {
     void* unit_desc;               // 128-byte work-unit descriptors of the current level
     uint32_t* unit_first;          // first splitter interval of each packed work unit
     uint32_t* pack_tiles;          // per-tile counts / offsets of the packing scan
+    uint32_t* ivl_size;            // [unit_cap + 64] interval sizes, bit 31 = first interval of its node
     uint32_t unit_cap;
     uint32_t* canon_idx;           // dump: canonical index of each node start; before that, the
                                    // node pass's candidate list (boundary indices)

@@ -525,7 +525,6 @@ __global__ void __launch_bounds__(1024) k_level_prep(LevelNode* __restrict__ nod
     if (threadIdx.x == 0) {
         ctr[kCtrSplits] = tot;
         ctr[kCtrIntervals] = tot + nn;
-        ctr[kCtrMaxIvl] = 0;
     }
 }
 
@@ -543,6 +542,7 @@ __global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict
     const LevelNode* nodes = nodes_lvl + level_off[p];
     const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
     const uint32_t total = (uint32_t)ctr[kCtrSplits];
+    uint32_t* status = reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(ctr) + kCtrStatus);
     const uint32_t my_c = threadIdx.x % k;
     // grid-stride over splitters; the k lanes of a splitter stay in one warp
     const uint32_t groups_per_grid = gridDim.x * (blockDim.x / k);
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict
     for (uint32_t it = 0; it < iters; it++) {
     const uint32_t g = it * groups_per_grid + blockIdx.x * (blockDim.x / k) + threadIdx.x / k;
     const bool active = g < total;
-    uint32_t split = 0, v = 0, c = 0, unit_base = 0;
+    uint32_t split = 0, v = 0, c = 0, unit_base = 0, nsp = 0;
     int d = 0;
     if (active) {
         uint32_t lo = 0, hi = nn;  // last node with split_off <= g
@@ -562,6 +562,7 @@ __global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict
         const LevelNode nd = nodes[v];
         d = nd.degree;
         unit_base = nd.unit_off;
+        nsp = nd.nsplit;
         const K* inner = ((nd.depth + 1) & 1) ? buf1 : buf0;
         uint32_t gg = g - nd.split_off;
         Child ch_c;
@@ -593,7 +594,11 @@ __global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict
     }
     uint32_t slot = split ? (split + ts - 1) / ts - 1 : 0u;
     for (int o = 1; o < k; o <<= 1) slot += __shfl_xor_sync(0xffffffffu, slot, o);
-    if (active) {
+    // sorted children give every splitter a slot below the node's splitter
+    // count; anything else (a child that is not sorted) is reported, not written
+    if (active && slot >= nsp) {
+        if (my_c == 0) dev_fail(status, kDevSplitSlot);
+    } else if (active) {
         if ((int)my_c < d) tab[(size_t)(unit_base + slot + 1) * k + my_c] = split;
         if (my_c == 0) unit_node[unit_base + slot + 1] = v;
     }
@@ -613,15 +618,17 @@ struct __align__(16) UnitDesc {
 };
 static_assert(sizeof(UnitDesc) == 128, "UnitDesc layout");
 
-// Splitter intervals are packed into work units: a unit starts at interval
-// i when rank(i) / q exceeds rank(i-1) / q, where rank(i) is the output
-// position of the interval's first element (the sum of its start positions
-// in the children).  A unit then holds less than q + (largest interval)
-// elements; q = c - (the level's largest interval, measured on the device)
-// keeps it within c.  With spacing ts = c/(2k) no interval exceeds c/2, so
-// q >= c/2.
-constexpr int kPackThreads = 256;
+// Splitter intervals are packed into work units greedily: walking a run of
+// consecutive intervals, a unit starts at the first interval of a node, at
+// the first interval of the run, and at every interval that would take the
+// unit past c elements; otherwise the interval joins the open unit.  With
+// splitters every ts = c/(2k) elements of each of at most k children no
+// interval exceeds c/2, so every unit fits c and, away from node ends, holds
+// more than c/2.  Each thread packs its own run of kPackItems intervals, so
+// runs are packed independently (a run boundary always starts a unit).
+constexpr int kPackThreads = 128;
 constexpr int kPackItems = kPackTile / kPackThreads;
+static_assert(kPackItems % 4 == 0, "16-byte loads of interval sizes");
 
 __device__ __forceinline__ uint32_t interval_rank(const uint32_t* __restrict__ tab, uint32_t i, int k, uint32_t d) {
     uint32_t r = 0;
@@ -629,65 +636,67 @@ __device__ __forceinline__ uint32_t interval_rank(const uint32_t* __restrict__ t
     return r;
 }
 
-__device__ __forceinline__ bool starts_unit(const LevelNode* __restrict__ nodes, uint32_t nn, const uint32_t* __restrict__ unit_node,
-                                            const uint32_t* __restrict__ tab, uint32_t i, int k, uint32_t q,
-                                            uint32_t* __restrict__ status) {
-    const uint32_t v = unit_node[i];
-    if (v >= nn) {
-        dev_fail(status, kDevPackNode);
-        return false;
-    }
-    const LevelNode& nd = nodes[v];
-    const uint32_t local = i - nd.unit_off;
-    if (local == 0) return true;
-    const uint32_t rc = interval_rank(tab, i, k, nd.degree);
-    const uint32_t rp = local == 1 ? 0u : interval_rank(tab, i - 1, k, nd.degree);
-    return rc / q > rp / q;
-}
-
-// Largest splitter interval of the level (elements), into ctr[kCtrMaxIvl].
-__global__ void __launch_bounds__(256) k_interval_max(const LevelNode* __restrict__ nodes_lvl,
-                                                      const uint32_t* __restrict__ level_off, int p,
-                                                      const uint32_t* __restrict__ unit_node, const uint32_t* __restrict__ tab,
-                                                      uint64_t* __restrict__ ctr, int k) {
-    __shared__ uint32_t tmp[256 / 32 + 1];
-    const LevelNode* nodes = nodes_lvl + level_off[p];
-    const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
-    const uint32_t ni = (uint32_t)ctr[kCtrIntervals];
-    uint32_t mx = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
-        const uint32_t v = unit_node[i];
-        if (v >= nn) continue;  // reported by the packing kernels
-        const LevelNode& nd = nodes[v];
-        const uint32_t local = i - nd.unit_off;
-        const uint32_t r0 = local == 0 ? 0u : interval_rank(tab, i, k, nd.degree);
-        const uint32_t r1 = local + 1 < nd.nunits ? interval_rank(tab, i + 1, k, nd.degree) : nd.sR - nd.sL;
-        mx = max(mx, r1 - r0);
-    }
-    mx = block_reduce<256>(mx, OpMax32(), 0u, tmp);
-    if (threadIdx.x == 0 && mx) atomicMax(reinterpret_cast<unsigned long long*>(ctr + kCtrMaxIvl), (unsigned long long)mx);
-}
-
-// Packing quantum q = c - (largest interval), at least c/2.
-__device__ __forceinline__ uint32_t pack_quantum(const uint64_t* __restrict__ ctr, uint32_t c) {
-    const uint64_t mi = ctr[kCtrMaxIvl];
-    return mi < c / 2 ? c - (uint32_t)mi : c / 2;
-}
-
-__global__ void __launch_bounds__(kPackThreads) k_pack_reduce(const LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off, int p,
-                                                              const uint32_t* __restrict__ unit_node,
-                                                              const uint32_t* __restrict__ tab, const uint64_t* __restrict__ ctr,
-                                                              int k, uint32_t c, uint32_t* __restrict__ tiles) {
-    __shared__ uint32_t tmp[kPackThreads / 32 + 1];
-    const uint32_t q = pack_quantum(ctr, c);
+// Size of every interval of the level (elements), with bit 31 set on the
+// first interval of each node: isz[i] for i < ctr[kCtrIntervals].
+__global__ void __launch_bounds__(256) k_interval_size(const LevelNode* __restrict__ nodes_lvl,
+                                                       const uint32_t* __restrict__ level_off, int p,
+                                                       const uint32_t* __restrict__ unit_node, const uint32_t* __restrict__ tab,
+                                                       const uint64_t* __restrict__ ctr, int k, uint32_t* __restrict__ isz) {
     const LevelNode* nodes = nodes_lvl + level_off[p];
     const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
     uint32_t* status = reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(ctr) + kCtrStatus);
     const uint32_t ni = (uint32_t)ctr[kCtrIntervals];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+        const uint32_t v = unit_node[i];
+        if (v >= nn) {
+            dev_fail(status, kDevPackNode);
+            isz[i] = 1u << 31;  // an empty interval that starts a unit
+            continue;
+        }
+        const LevelNode& nd = nodes[v];
+        const uint32_t local = i - nd.unit_off;
+        const uint32_t r0 = local == 0 ? 0u : interval_rank(tab, i, k, nd.degree);
+        const uint32_t r1 = local + 1 < nd.nunits ? interval_rank(tab, i + 1, k, nd.degree) : nd.sR - nd.sL;
+        isz[i] = ((r1 - r0) & 0x7FFFFFFFu) | (local == 0 ? 1u << 31 : 0u);
+    }
+}
+
+// Greedy packing of intervals [i0, i0 + kPackItems) clipped to ni: returns
+// the number of units that start there and, if `out` is given, writes the
+// index of each starting interval.  isz is padded past ni, so the 16-byte
+// loads of the last run stay inside it.
+__device__ __forceinline__ uint32_t pack_run(const uint32_t* __restrict__ isz, uint32_t i0, uint32_t ni, uint32_t c,
+                                             uint32_t* __restrict__ out) {
+    uint32_t cnt = 0, acc = 0;
+    const uint4* s4 = reinterpret_cast<const uint4*>(isz + i0);
+#pragma unroll 4
+    for (uint32_t q = 0; q < (uint32_t)kPackItems / 4; q++) {
+        const uint4 w4 = s4[q];
+        const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (uint32_t t = 0; t < 4; t++) {
+            const uint32_t j = 4 * q + t;
+            if (i0 + j < ni) {
+                const uint32_t sz = w[t] & 0x7FFFFFFFu;
+                if (j == 0 || (w[t] >> 31) || acc + sz > c) {
+                    if (out) out[cnt] = i0 + j;
+                    cnt++;
+                    acc = sz;
+                } else {
+                    acc += sz;
+                }
+            }
+        }
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(kPackThreads) k_pack_reduce(const uint32_t* __restrict__ isz, const uint64_t* __restrict__ ctr,
+                                                              uint32_t c, uint32_t* __restrict__ tiles) {
+    __shared__ uint32_t tmp[kPackThreads / 32 + 1];
+    const uint32_t ni = (uint32_t)ctr[kCtrIntervals];
     const uint32_t i0 = blockIdx.x * kPackTile + threadIdx.x * kPackItems;
-    uint32_t cnt = 0;
-    for (uint32_t j = 0; j < (uint32_t)kPackItems; j++)
-        if (i0 + j < ni) cnt += starts_unit(nodes, nn, unit_node, tab, i0 + j, k, q, status);
+    const uint32_t cnt = i0 < ni ? pack_run(isz, i0, ni, c, nullptr) : 0u;
     uint32_t tot;
     block_sum_excl<kPackThreads>(cnt, tmp, &tot);
     if (threadIdx.x == 0) tiles[blockIdx.x] = tot;
@@ -709,27 +718,15 @@ __global__ void __launch_bounds__(1024) k_pack_scan(uint32_t* __restrict__ tiles
     if (threadIdx.x == 0) ctr[kCtrUnits] = tot;
 }
 
-__global__ void __launch_bounds__(kPackThreads) k_pack_apply(const LevelNode* __restrict__ nodes_lvl, const uint32_t* __restrict__ level_off, int p,
-                                                              const uint32_t* __restrict__ unit_node,
-                                                             const uint32_t* __restrict__ tab, const uint64_t* __restrict__ ctr,
-                                                             int k, uint32_t c, const uint32_t* __restrict__ tiles,
+__global__ void __launch_bounds__(kPackThreads) k_pack_apply(const uint32_t* __restrict__ isz, const uint64_t* __restrict__ ctr,
+                                                             uint32_t c, const uint32_t* __restrict__ tiles,
                                                              uint32_t* __restrict__ unit_first) {
     __shared__ uint32_t tmp[kPackThreads / 32 + 1];
-    const uint32_t q = pack_quantum(ctr, c);
-    const LevelNode* nodes = nodes_lvl + level_off[p];
-    const uint32_t nn = (uint32_t)ctr[kCtrHbmCount + p];
-    uint32_t* status = reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(ctr) + kCtrStatus);
     const uint32_t ni = (uint32_t)ctr[kCtrIntervals];
     const uint32_t i0 = blockIdx.x * kPackTile + threadIdx.x * kPackItems;
-    uint32_t flags = 0, cnt = 0;
-    for (uint32_t j = 0; j < (uint32_t)kPackItems; j++)
-        if (i0 + j < ni && starts_unit(nodes, nn, unit_node, tab, i0 + j, k, q, status)) {
-            flags |= 1u << j;
-            cnt++;
-        }
-    uint32_t pos = tiles[blockIdx.x] + block_sum_excl<kPackThreads>(cnt, tmp, nullptr);
-    for (uint32_t j = 0; j < (uint32_t)kPackItems; j++)
-        if (flags & (1u << j)) unit_first[pos++] = i0 + j;
+    const uint32_t cnt = i0 < ni ? pack_run(isz, i0, ni, c, nullptr) : 0u;
+    const uint32_t pos = tiles[blockIdx.x] + block_sum_excl<kPackThreads>(cnt, tmp, nullptr);
+    if (i0 < ni) pack_run(isz, i0, ni, c, unit_first + pos);
 }
 
 // One thread per packed work unit of the level: fills its descriptor.
@@ -1138,13 +1135,11 @@ void launch_level_plan(int p, uint32_t nn_bound, uint64_t elems_bound, int k, co
                                                     leaf_keys, out, tmp, g.ts, k, ws.unit_node, ws.split_tab);
     const uint64_t ivl_bound = split_bound + nn_bound;
     const uint32_t tiles = (uint32_t)ceil_div(ivl_bound, kPackTile);
-    k_interval_max<<<(uint32_t)std::min<uint64_t>(ceil_div(ivl_bound, 256), 152 * 8), 256, 0, st>>>(
-        ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.split_tab, ws.counters, k);
-    k_pack_reduce<<<tiles, kPackThreads, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.split_tab, ws.counters, k,
-                                                  g.c_level, ws.pack_tiles);
+    k_interval_size<<<(uint32_t)std::min<uint64_t>(ceil_div(ivl_bound, 256), 152 * 8), 256, 0, st>>>(
+        ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.split_tab, ws.counters, k, ws.ivl_size);
+    k_pack_reduce<<<tiles, kPackThreads, 0, st>>>(ws.ivl_size, ws.counters, g.c_level, ws.pack_tiles);
     k_pack_scan<<<1, 1024, 0, st>>>(ws.pack_tiles, tiles, ws.counters);
-    k_pack_apply<<<tiles, kPackThreads, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.split_tab, ws.counters, k,
-                                                 g.c_level, ws.pack_tiles, ws.unit_first);
+    k_pack_apply<<<tiles, kPackThreads, 0, st>>>(ws.ivl_size, ws.counters, g.c_level, ws.pack_tiles, ws.unit_first);
     const uint32_t desc_blocks = (uint32_t)std::min<uint64_t>(ceil_div(ivl_bound, 256), 152 * 16);
     k_level_desc<<<desc_blocks, 256, 0, st>>>(ws.nodes_lvl, ws.level_off, p, ws.unit_node, ws.unit_first, ws.split_tab,
                                               ws.counters, ws.run_starts, ws.run_desc, k,
