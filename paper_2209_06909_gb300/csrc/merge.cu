@@ -77,8 +77,6 @@ constexpr uint32_t kMbarSpinLimit = 1u << 24;
 constexpr int kFusedThreads = 256;
 constexpr uint32_t kFusedPad = 16;  // elements of slack per fused-kernel buffer
 constexpr uint32_t kNoMid = 0xFFFFu;
-// boundary-list entries one thread holds while compacting: ceil((C/2 + 8) / 256), odd
-constexpr int kKeepMax = 25;
 
 // Number of elements of A[0..na) among the first `diag` outputs of the stable
 // merge of A and B[0..nb) (A first on equal keys): merge path.
@@ -387,6 +385,10 @@ __global__ void __launch_bounds__(kFusedThreads)
         uint32_t* vcur = vB;
         uint32_t* voth = vA;
         uint32_t na = nb;
+        // boundary list of the current level and the list the next level gets
+        // (bl1 is free once the load and reversal are done)
+        uint32_t* blc = bl0;
+        uint32_t* bln = bl1;
         uint32_t T = 0;  // tournament rounds per node: log2 k
         while ((1u << T) < (uint32_t)k) T++;
         __shared__ uint32_t s_rmask;
@@ -400,25 +402,18 @@ __global__ void __launch_bounds__(kFusedThreads)
             // of the node's tournament); T for a smaller power (a delimiter).
             // The list holds no power above p any more, so a group's boundaries
             // are adjacent: q is found by looking back at most k - 1 entries.
-            // Kept (smaller-power) boundaries wait in registers until the
-            // level is merged.
-            if (per > (uint32_t)kKeepMax) {  // per is the same for every thread of the block
-                if (tid == 0) dev_fail(status, kDevRange);
-                return;
-            }
-            uint32_t keep[kKeepMax];
             uint32_t nk = 0, rmask = 0;
             for (uint32_t e = e0; e < e1; e++) {
-                const uint32_t v = bl0[e];
+                const uint32_t v = blc[e];
                 if (be_pow(v) == p) {
                     uint32_t q = 1;
-                    while (q < 8u && e >= q && be_pow(bl0[e - q]) == p) q++;
+                    while (q < 8u && e >= q && be_pow(blc[e - q]) == p) q++;
                     const uint32_t rd = min((uint32_t)__ffs(q) - 1u, T - 1u);
-                    bl0[e] = (v & 0x00FFFFFFu) | (rd << 24);
+                    blc[e] = (v & 0x00FFFFFFu) | (rd << 24);
                     rmask |= 1u << rd;
                 } else {
-                    bl0[e] = (v & 0x00FFFFFFu) | (T << 24);
-                    keep[nk++] = v & 0x00FFFFFFu;
+                    blc[e] = (v & 0x00FFFFFFu) | (T << 24);
+                    nk++;
                 }
             }
             if (tid == 0) s_rmask = 0;
@@ -428,17 +423,22 @@ __global__ void __launch_bounds__(kFusedThreads)
             if (rmask) atomicOr(&s_rmask, rmask);
             __syncthreads();
             const uint32_t rounds = s_rmask;
-            const int first = round_entry(len, bl0, (int)na);
+            const int first = round_entry(len, blc, (int)na);
             // tournament rounds
             for (uint32_t t = 0; t < T; t++) {
                 if (!((rounds >> t) & 1u)) continue;
-                merge_round<K, V>(cur, oth, vcur, voth, len, bl0, (int)na, first, t);
+                merge_round<K, V>(cur, oth, vcur, voth, len, blc, (int)na, first, t);
                 __syncthreads();
                 K* tk = cur; cur = oth; oth = tk;
                 uint32_t* tv = vcur; vcur = voth; voth = tv;
             }
-            // drop the boundaries consumed at this level
-            for (uint32_t q = 0; q < nk; q++) bl0[kpos + q] = keep[q];
+            // the boundaries of smaller power (round tag T) form the next list
+            uint32_t w = kpos;
+            for (uint32_t e = e0; e < e1; e++) {
+                const uint32_t v = blc[e];
+                if (be_rnd(v) == T) bln[w++] = v & 0x00FFFFFFu;
+            }
+            uint32_t* tb = blc; blc = bln; bln = tb;
             na = nkeep;
             __syncthreads();
         }
@@ -1094,7 +1094,7 @@ __global__ void k_copy_lone_runs(const K* __restrict__ in, const uint32_t* __res
 
 MergeGeom merge_geom(int key_bytes, bool vals, int k) {
     MergeGeom g;
-    if (key_bytes == 4 && !vals) { g.c_fused = 6144; g.c_level = 8192; }
+    if (key_bytes == 4 && !vals) { g.c_fused = 6144; g.c_level = 9216; }
     else if (key_bytes == 8 && vals) { g.c_fused = 3072; g.c_level = 4096; }
     else { g.c_fused = 4096; g.c_level = 4096; }
     g.tmax = g.c_fused;
