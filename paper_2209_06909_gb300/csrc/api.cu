@@ -12,6 +12,7 @@
 // The host reads back the run count after step 1 and the per-level node
 // counts after step 4 to size the launches of steps 2-6.
 #include <algorithm>
+#include <memory>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -61,7 +62,9 @@ struct Plan {
         mask_tiles = ceil_div(rmax, kMaskTile);
         nodes_cap = (uint32_t)(34 * (n / g.tmax + 1) + 64);
         unit_cap = (uint32_t)(n / g.ts + n / g.tmax + 64);
-        fused_cap = (uint32_t)k * nodes_cap + 64;
+        // fused subtrees: at most k children of each node above T_max, plus one
+        // root per array (a single array, or every array of a batch)
+        fused_cap = (uint32_t)k * nodes_cap + std::max<uint32_t>(m, 1) + 64;
         uint64_t len = rmax + 1;
         nlv_max = 0;
         while (true) {
@@ -292,11 +295,32 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     }
     MPS_CUDA(cudaGetLastError());
     MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, sizeof(h_ctr), cudaMemcpyDeviceToHost, st));
-    MPS_CUDA(cudaStreamSynchronize(st));
+    // The host needs the counters to queue the level merges, but the node
+    // buckets and the fused merge take their counts from the device: they are
+    // queued first, and the host waits only for the counters, so that the
+    // GPU runs the fused merge while the host reads them.
+    cudaEvent_t ev_ctr = nullptr;
+    MPS_CUDA(cudaEventCreateWithFlags(&ev_ctr, cudaEventDisableTiming));
+    const cudaError_t rec_err = cudaEventRecord(ev_ctr, st);
+    std::unique_ptr<ProfScope> ps_fused;
+    if (rec_err == cudaSuccess && move_keys) {
+        launch_bucket(plan.nodes_cap, ws, st);
+        ps_fused.reset(new ProfScope("fused_merge", 0.0, st));
+        launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, plan.fused_cap, g, ws, st);
+    }
+    const cudaError_t wait_err = rec_err == cudaSuccess ? cudaEventSynchronize(ev_ctr) : rec_err;
+    cudaEventDestroy(ev_ctr);
+    // on any early return below, nothing is left running on the stream
+    auto drain = [&](mps_status code) {
+        ps_fused.reset();
+        cudaStreamSynchronize(st);
+        return code;
+    };
+    if (wait_err != cudaSuccess) return drain(MPS_ERR_CUDA);
     g_last.device_status = (uint32_t)h_ctr[kCtrStatus];
-    if ((uint32_t)h_ctr[kCtrStatus]) return device_error((uint32_t)h_ctr[kCtrStatus]);
+    if ((uint32_t)h_ctr[kCtrStatus]) return drain(device_error((uint32_t)h_ctr[kCtrStatus]));
     const uint64_t hbm_total = h_ctr[kCtrHbmTotal];
-    if (hbm_total > plan.nodes_cap || h_ctr[kCtrFrontier] > plan.fused_cap) return MPS_ERR_DEVICE_CHECK;
+    if (hbm_total > plan.nodes_cap || h_ctr[kCtrFrontier] > plan.fused_cap) return drain(MPS_ERR_DEVICE_CHECK);
     g_last.merge_cost = h_ctr[kCtrM];
     g_last.frontier_nodes = h_ctr[kCtrFrontier];
     g_last.hbm_nodes = hbm_total;
@@ -307,15 +331,15 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     uint64_t m_levels = 0;
     for (int p = 1; p < kMaxLevels; p++) m_levels += h_ctr[kCtrHbmCount + p] ? h_ctr[kCtrHbmSize + p] : 0;
     const uint64_t m_fused = g_last.merge_cost >= m_levels ? g_last.merge_cost - m_levels : 0;
+    if (ps_fused) {
+        // algorithmic bytes (Sec. 2.2 cost model): one read and one write of
+        // b bytes per element per merge, i.e. 2 b M_fused; the kernel itself
+        // reads and writes each element of its subtrees once.  The scope ends
+        // here, right behind the fused launch in stream order.
+        ps_fused->rec.bytes = 2.0 * b * (double)m_fused;
+        ps_fused.reset();
+    }
     if (move_keys) {
-        if (hbm_total) launch_bucket((uint32_t)hbm_total, ws, st);
-        if (h_ctr[kCtrFrontier]) {
-            // algorithmic bytes (Sec. 2.2 cost model): one read and one write of
-            // b bytes per element per merge, i.e. 2 b M_fused; the kernel itself
-            // reads and writes each element of its subtrees once
-            ProfScope ps("fused_merge", 2.0 * b * (double)m_fused, st);
-            launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, h_ctr[kCtrFrontier], g, ws, st);
-        }
         uint64_t lvl_bytes = 0;
         for (int p = kMaxLevels - 1; p >= 1; p--) {
             const uint32_t cnt = (uint32_t)h_ctr[kCtrHbmCount + p];

@@ -534,18 +534,25 @@ __global__ void k_bucket(const LevelNode* __restrict__ raw, const uint32_t* __re
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         LevelNode nd = raw[i];
         uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmFill + nd.power), 1ull);
-        out[level_off[nd.power] + slot] = nd;
+        // the per-power counts include nodes the node pass could not store
+        // (it reported that); nothing is written past the capacity
+        const uint32_t at = level_off[nd.power] + slot;
+        if (at < cap) out[at] = nd;
     }
 }
 
-// Exclusive offsets of the per-power node buckets (one thread).
-__global__ void k_level_offsets(const uint64_t* __restrict__ ctr, uint32_t* __restrict__ off) {
+// Exclusive offsets of the per-power node buckets (one thread).  Also caps
+// the fused-subtree count at the list's capacity, so that the fused merge,
+// which takes its work count from the device, never reads past the list (the
+// node pass reported any overflow as a device status).
+__global__ void k_level_offsets(uint64_t* __restrict__ ctr, uint32_t* __restrict__ off, uint32_t fused_cap) {
     if (threadIdx.x == 0) {
         uint32_t acc = 0;
         for (int p = 0; p < kMaxLevels; p++) {
             off[p] = acc;
             acc += (uint32_t)ctr[kCtrHbmCount + p];
         }
+        if (ctr[kCtrFrontier] > fused_cap) ctr[kCtrFrontier] = fused_cap;
     }
 }
 
@@ -699,7 +706,7 @@ void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaSt
 }
 
 void launch_bucket(uint32_t total_bound, const WsView& ws, cudaStream_t st) {
-    k_level_offsets<<<1, 32, 0, st>>>(ws.counters, ws.level_off);
+    k_level_offsets<<<1, 32, 0, st>>>(ws.counters, ws.level_off, ws.fused_cap);
     uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(std::max<uint32_t>(total_bound, 1), 256), 152 * 8);
     k_bucket<<<blocks, 256, 0, st>>>(ws.nodes_raw, ws.level_off, ws.counters, ws.nodes_lvl, ws.nodes_cap);
     g_launches += 2;

@@ -117,6 +117,26 @@ def test_batch_costs_many_small_and_empty_arrays():
     assert np.array_equal(costs.cpu().numpy(), oracle_costs(arrays, 4))
 
 
+def test_batch_of_many_tiny_arrays():
+    """Every array of two or more runs that fits a tile is its own fused root,
+    so a batch of many tiny arrays has far more fused subtrees than nodes
+    above T_max: the fused list is sized by the number of arrays."""
+    rng = np.random.default_rng(31)
+    m = 120_000
+    sizes = rng.integers(3, 9, m)
+    keys = rng.integers(0, 1 << 32, int(sizes.sum()), dtype=np.uint64).astype(np.uint32)
+    offsets = np.zeros(m + 1, np.uint64)
+    offsets[1:] = np.cumsum(sizes)
+    arrays = [keys[int(offsets[i]):int(offsets[i + 1])] for i in range(m)]
+    d_off = torch.from_numpy(offsets.view(np.int64)).to(DEV)
+    costs = cost_buffer(m)
+    out = mps.sort_batch(mps.to_device(keys, DEV), d_off, k=4, max_len=8, merge_costs=costs)
+    torch.cuda.synchronize()
+    assert np.array_equal(mps.to_numpy(out, np.uint32), np.concatenate([np.sort(a) for a in arrays]))
+    assert mps.last_stats()["frontier_nodes"] > 50_000
+    assert np.array_equal(costs.cpu().numpy(), oracle_costs(arrays, 4))
+
+
 def test_batch_longer_than_max_len_is_reported():
     """An array longer than the caller's max_len is a device-side check
     failure (status 16), not a silently short level loop."""
