@@ -258,7 +258,7 @@ __device__ __forceinline__ uint32_t small_power(uint64_t nmax, uint64_t longest,
 // merges inside its own array only and M of the array is Sec. 2.2's M of that
 // array sorted alone.
 template <bool kArr>
-__global__ void __launch_bounds__(kMaskThreads, 3) k_mask_apply(const uint8_t* __restrict__ powers, uint64_t* __restrict__ ctr,
+__global__ void __launch_bounds__(kMaskThreads, 4) k_mask_apply(const uint8_t* __restrict__ powers, uint64_t* __restrict__ ctr,
                                                              const uint32_t* __restrict__ rs,
                                                              const unsigned long long* __restrict__ fpre,
                                                              const unsigned long long* __restrict__ gsuf,
