@@ -9,11 +9,14 @@
 //   4. node pass (Alg. 1 unrolled)                  -> level nodes, fused subtrees, M
 //   5. fused merges of all small subtrees           -> their outputs
 //   6. level merges, largest power first            -> root output in keys_out
-// The host reads back the run count after step 1 and the per-level node
-// counts after step 4 to size the launches of steps 2-6.
+// The host reads back the run count after step 1 to size steps 2-4, and the
+// per-level node counts after step 4 to queue step 6; step 5 takes its count
+// from the device and is queued before that second read, so it runs while
+// the host waits.  Batches (mps_sort_batch*) read nothing back: every launch
+// is sized by bounds and takes its counts from the device.
 #include <algorithm>
-#include <memory>
 #include <cstdio>
+#include <memory>
 #include <cstring>
 #include <mutex>
 #include <string>
