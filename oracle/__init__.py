@@ -57,6 +57,11 @@ def _load():
         U64 = ctypes.c_uint64
         lib.mpso_sort.argtypes = [P, P, P, P, U64, ctypes.c_int, ctypes.c_uint32, P, P, P, P, P, P, P]
         lib.mpso_sort.restype = ctypes.c_int
+        lib.mpso_sort_min_run.argtypes = [P, P, P, P, U64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
+                                          P, P, P, P, P, P, P]
+        lib.mpso_sort_min_run.restype = ctypes.c_int
+        lib.mpso_find_runs_min.argtypes = [P, U64, ctypes.c_uint32, P, P, P]
+        lib.mpso_find_runs_min.restype = U64
         lib.mpso_power.argtypes = [U64, U64, U64, U64, U64, ctypes.c_uint32]
         lib.mpso_power.restype = ctypes.c_uint32
         lib.mpso_find_runs.argtypes = [P, U64, P, P]
@@ -89,21 +94,26 @@ def power(n, b1, e1, b2, e2, k):
     return int(_load().mpso_power(n, b1, e1, b2, e2, k))
 
 
-def find_runs(keys):
-    """Greedy run detection (Sec. 2); returns (run_starts[r+1], run_desc[r])."""
+def find_runs(keys, min_run_len=1):
+    """Greedy run detection (Sec. 2); returns (run_starts[r+1], run_desc[r]).
+    With min_run_len > 1 a shorter natural run is extended to min_run_len
+    elements (Sec. 5 "Minimal run length"); run_desc then flags a strictly
+    decreasing natural part."""
     a = np.ascontiguousarray(keys, dtype=np.uint64)
     n = a.size
     starts = np.zeros(n + 2, np.uint32)
     desc = np.zeros(n + 1, np.uint8)
-    r = int(_load().mpso_find_runs(_ptr(a), n, _ptr(starts), _ptr(desc)))
+    r = int(_load().mpso_find_runs_min(_ptr(a), n, int(min_run_len), _ptr(starts), _ptr(desc), None))
     return starts[: r + 1].copy(), desc[:r].copy()
 
 
-def sort(keys, vals=None, k=4, want_tree=True):
+def sort(keys, vals=None, k=4, want_tree=True, min_run_len=1):
     """Multiway Powersort of ``keys`` (uint32 or uint64), optional uint32 payload.
 
     Returns a dict with ``keys`` (and ``vals``) plus, if ``want_tree``, the run
-    structure and canonical tree (see the module docstring)."""
+    structure and canonical tree (see the module docstring).  ``min_run_len``
+    > 1 extends shorter natural runs to that length and insertion-sorts them
+    (Sec. 5 "Minimal run length"); 1 sorts the natural runs."""
     keys = np.ascontiguousarray(keys)
     if keys.dtype not in (np.uint32, np.uint64):
         raise TypeError("keys must be uint32 or uint64")
@@ -122,8 +132,8 @@ def sort(keys, vals=None, k=4, want_tree=True):
     nf = np.zeros(m + 1, np.uint32) if want_tree else None
     ld = np.zeros(m + 1, np.uint8) if want_tree else None
     counts = np.zeros(4, np.uint64)
-    rc = _load().mpso_sort(_ptr(keys), _ptr(vin), _ptr(out), _ptr(vout), n, kb, k,
-                           _ptr(rs), _ptr(rd), _ptr(pw), _ptr(nodes), _ptr(nf), _ptr(ld), _ptr(counts))
+    rc = _load().mpso_sort_min_run(_ptr(keys), _ptr(vin), _ptr(out), _ptr(vout), n, kb, k, int(min_run_len),
+                                   _ptr(rs), _ptr(rd), _ptr(pw), _ptr(nodes), _ptr(nf), _ptr(ld), _ptr(counts))
     _check(rc)
     r, nn, lv, mc = (int(x) for x in counts)
     res = {"keys": out, "r": r, "num_nodes": nn, "num_levels": lv, "merge_cost": mc}

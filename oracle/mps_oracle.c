@@ -11,7 +11,10 @@
  * order, with no blocking, fusion or parallel tricks:
  *   - runs: maximal weakly increasing or strictly decreasing segments, found
  *     greedily from the left (Sec. 2 "Preliminaries"; FirstRunOf in Alg. 2);
- *     strictly decreasing runs are reversed before merging (Sec. 2);
+ *     strictly decreasing runs are reversed before merging (Sec. 2).  An
+ *     optional minimum run length (Sec. 5 "Minimal run length", and the
+ *     appendix's 4-way Powersort) extends a shorter natural run to that many
+ *     elements and insertion-sorts it; 1 keeps the natural runs;
  *   - boundary power: the Power_k procedure of Alg. 2 (equivalently Def. 3.1),
  *     evaluated with exact 128-bit integer floors instead of real division;
  *   - merge policy: the run stack of Alg. 2 (KwayPowerSort_k) with weakly
@@ -64,19 +67,36 @@ static uint64_t first_run_of(const uint64_t* a, uint64_t b, uint64_t n, int* des
     return e;
 }
 
-/* Writes run starts s_0..s_{r-1}, s_r = n and direction flags; returns r. */
-uint64_t mpso_find_runs(const uint64_t* a, uint64_t n, uint32_t* starts, uint8_t* desc) {
+/* Runs with a minimum length min_run_len >= 1: the natural run found from b
+ * (FirstRunOf) ends the run unless it is shorter than min_run_len, in which
+ * case the run takes min(n, b + min_run_len) elements (Sec. 5 "Minimal run
+ * length").  The next run is searched from the end of this one in the input
+ * as given.  Writes run starts s_0..s_{r-1}, s_r = n, the direction of each
+ * run's natural part and, if nat_len is not NULL, that part's length;
+ * returns r. */
+uint64_t mpso_find_runs_min(const uint64_t* a, uint64_t n, uint32_t min_run_len, uint32_t* starts, uint8_t* desc,
+                            uint32_t* nat_len) {
     uint64_t r = 0, b = 0;
+    if (min_run_len < 1) min_run_len = 1;
     while (b < n) {
         int d = 0;
         uint64_t e = first_run_of(a, b, n, &d);
+        const uint64_t natural = e - b;
+        if (natural < min_run_len) e = (n - b > min_run_len) ? b + min_run_len : n;
         starts[r] = (uint32_t)b;
         desc[r] = (uint8_t)d;
+        if (nat_len) nat_len[r] = (uint32_t)natural;
         r++;
         b = e;
     }
     starts[r] = (uint32_t)n;
     return r;
+}
+
+/* Natural runs: writes run starts s_0..s_{r-1}, s_r = n and direction flags;
+ * returns r. */
+uint64_t mpso_find_runs(const uint64_t* a, uint64_t n, uint32_t* starts, uint8_t* desc) {
+    return mpso_find_runs_min(a, n, 1, starts, desc, NULL);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -280,15 +300,17 @@ static int collapse_top(stack_entry* st, uint64_t* sp, stack_entry* cur, raw_tre
  *   keys_in/keys_out : n keys of key_bytes (4 or 8) bytes; may alias.
  *   vals_in/vals_out : optional uint32 payload (both NULL or both set).
  *   k                : fan-in, k >= 2.
+ *   min_run_len      : minimum run length (>= 1; 1 = natural runs); run_desc
+ *                      then flags a strictly decreasing natural part.
  *   run_starts[r+1], run_desc[r], powers[r+1] (powers[0]=powers[r]=0),
  *   nodes[r-1], node_first[r], leaf_depth[r], counts[4] = {r, nodes, levels, M}:
  *   optional outputs (NULL to skip), sized for the worst case r = n.
  */
-int mpso_sort(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out,
-              uint64_t n, int key_bytes, uint32_t k,
-              uint32_t* run_starts, uint8_t* run_desc, uint8_t* powers,
-              mpso_node* nodes, uint32_t* node_first, uint8_t* leaf_depth, uint64_t* counts) {
-    if ((key_bytes != 4 && key_bytes != 8) || k < 2 || n >= (1ull << 32)) return MPSO_ERR_ARG;
+int mpso_sort_min_run(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out,
+                      uint64_t n, int key_bytes, uint32_t k, uint32_t min_run_len,
+                      uint32_t* run_starts, uint8_t* run_desc, uint8_t* powers,
+                      mpso_node* nodes, uint32_t* node_first, uint8_t* leaf_depth, uint64_t* counts) {
+    if ((key_bytes != 4 && key_bytes != 8) || k < 2 || n >= (1ull << 32) || min_run_len < 1) return MPSO_ERR_ARG;
     if ((vals_in == NULL) != (vals_out == NULL)) return MPSO_ERR_ARG;
     int rc = MPSO_OK;
     uint64_t* a = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
@@ -297,20 +319,38 @@ int mpso_sort(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint
     uint32_t* vbuf = vals_in ? (uint32_t*)malloc((n ? n : 1) * sizeof(uint32_t)) : NULL;
     uint32_t* st_s = (uint32_t*)malloc((n + 2) * sizeof(uint32_t));
     uint8_t* st_d = (uint8_t*)malloc(n + 2);
-    if (!a || !buf || !st_s || !st_d || (vals_in && (!v || !vbuf))) { rc = MPSO_ERR_NOMEM; goto done0; }
+    uint32_t* st_l = (uint32_t*)malloc((n + 2) * sizeof(uint32_t));
+    if (!a || !buf || !st_s || !st_d || !st_l || (vals_in && (!v || !vbuf))) { rc = MPSO_ERR_NOMEM; goto done0; }
     for (uint64_t i = 0; i < n; i++)
         a[i] = key_bytes == 4 ? ((const uint32_t*)keys_in)[i] : ((const uint64_t*)keys_in)[i];
     if (v) memcpy(v, vals_in, n * sizeof(uint32_t));
 
-    /* runs, then reverse the strictly decreasing ones (stable: no ties) */
-    uint64_t r = mpso_find_runs(a, n, st_s, st_d);
+    /* runs, then reverse the strictly decreasing natural parts (stable: no
+     * ties) and insertion-sort each extended run; its first natural-length
+     * elements are sorted already, and an element moves left only past
+     * strictly larger keys, so equal keys keep their order */
+    uint64_t r = mpso_find_runs_min(a, n, min_run_len, st_s, st_d, st_l);
     for (uint64_t i = 0; i < r; i++) {
-        if (!st_d[i]) continue;
-        uint64_t lo = st_s[i], hi = st_s[i + 1] - 1;
-        while (lo < hi) {
-            uint64_t tk = a[lo]; a[lo] = a[hi]; a[hi] = tk;
-            if (v) { uint32_t tv = v[lo]; v[lo] = v[hi]; v[hi] = tv; }
-            lo++; hi--;
+        const uint64_t s0 = st_s[i], s1 = st_s[i + 1], nat = st_l[i];
+        if (st_d[i]) {
+            uint64_t lo = s0, hi = s0 + nat - 1;
+            while (lo < hi) {
+                uint64_t tk = a[lo]; a[lo] = a[hi]; a[hi] = tk;
+                if (v) { uint32_t tv = v[lo]; v[lo] = v[hi]; v[hi] = tv; }
+                lo++; hi--;
+            }
+        }
+        for (uint64_t x = s0 + nat; x < s1; x++) {
+            const uint64_t key = a[x];
+            const uint32_t val = v ? v[x] : 0u;
+            uint64_t y = x;
+            while (y > s0 && a[y - 1] > key) {
+                a[y] = a[y - 1];
+                if (v) v[y] = v[y - 1];
+                y--;
+            }
+            a[y] = key;
+            if (v) v[y] = val;
         }
     }
 
@@ -356,8 +396,17 @@ done1:
     free(pw); free(st);
     raw_tree_free(&t);
 done0:
-    free(a); free(buf); free(v); free(vbuf); free(st_s); free(st_d);
+    free(a); free(buf); free(v); free(vbuf); free(st_s); free(st_d); free(st_l);
     return rc;
+}
+
+/* Multiway Powersort on natural runs (minimum run length 1). */
+int mpso_sort(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out,
+              uint64_t n, int key_bytes, uint32_t k,
+              uint32_t* run_starts, uint8_t* run_desc, uint8_t* powers,
+              mpso_node* nodes, uint32_t* node_first, uint8_t* leaf_depth, uint64_t* counts) {
+    return mpso_sort_min_run(keys_in, vals_in, keys_out, vals_out, n, key_bytes, k, 1, run_starts, run_desc, powers,
+                             nodes, node_first, leaf_depth, counts);
 }
 
 /* ------------------------------------------------------------------------- */

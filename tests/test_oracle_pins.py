@@ -404,3 +404,88 @@ def test_alg2_printed_tail_can_cost_more():
         L = _random_lengths(rng, int(rng.integers(1, 40)), int(rng.choice([4, 100, 5000])))
         higher += oracle.merge_cost_tail(L, 4, "alg2_pop_k_minus_1") > oracle.merge_cost_tail(L, 4, "kway_tree")
     assert higher > 0
+
+
+# ---- minimum run length (Sec. 5 "Minimal run length"; the appendix's
+# 4-way Powersort extends a natural run shorter than minRunLen to minRunLen
+# elements and insertion-sorts it; minRunLen = 1 keeps the natural runs)
+
+def _mixed_inputs(rng, count):
+    for i in range(count):
+        n = int(rng.integers(0, 300))
+        kind = i % 4
+        if kind == 0:
+            yield rng.integers(0, 5, n).astype(np.uint32)           # many ties
+        elif kind == 1:
+            yield rng.permutation(n).astype(np.uint32)               # short runs
+        elif kind == 2:
+            yield inputs.random_runs_uniform_len(n, int(rng.integers(1 << 30)), hi=30) if n else np.zeros(0, np.uint32)
+        else:
+            yield np.repeat(rng.integers(0, 1 << 31, max(1, n // 7)), 7)[:n].astype(np.uint32)
+
+
+def test_min_run_len_one_is_the_natural_run_sort():
+    rng = np.random.default_rng(80)
+    for a in _mixed_inputs(rng, 60):
+        for k in (2, 4):
+            x, y = oracle.sort(a, k=k), oracle.sort(a, k=k, min_run_len=1)
+            for key in ("keys", "run_starts", "run_desc", "powers", "node_first", "leaf_depth", "merge_cost"):
+                assert np.array_equal(x[key], y[key]), key
+
+
+@pytest.mark.parametrize("m0", [2, 3, 7, 24])
+def test_min_run_len_run_rule(m0):
+    """Every run is the longer of the natural run at its start (the greedy
+    scan, pinned above against brute force) and m0 elements, clipped at n;
+    only the last run can be shorter than m0."""
+    rng = np.random.default_rng(81 + m0)
+    for a in _mixed_inputs(rng, 80):
+        n = a.size
+        rs, _ = oracle.find_runs(a, min_run_len=m0)
+        assert rs[0] == 0 and rs[-1] == n and np.all(np.diff(rs.astype(np.int64)) > 0) if n else rs.tolist() == [0]
+        for j in range(rs.size - 1):
+            s, e = int(rs[j]), int(rs[j + 1])
+            natural = int(oracle.find_runs(a[s:])[0][1])  # end of the first natural run of the suffix
+            assert e - s == max(natural, min(m0, n - s)), (m0, j, s, e, natural)
+            if j + 1 < rs.size - 1:
+                assert e - s >= m0
+
+
+@pytest.mark.parametrize("m0", [2, 5, 24])
+def test_min_run_len_sort_is_stable(m0):
+    """The output is the sorted multiset and equal keys keep their input
+    order: reversal touches only strictly decreasing parts, and insertion
+    sort moves an element only past strictly larger keys."""
+    rng = np.random.default_rng(90 + m0)
+    for a in _mixed_inputs(rng, 60):
+        idx = np.arange(a.size, dtype=np.uint32)
+        res = oracle.sort(a, vals=idx, k=4, min_run_len=m0)
+        order = np.lexsort((idx, a))
+        assert np.array_equal(res["keys"], a[order])
+        assert np.array_equal(res["vals"], idx[order])
+
+
+@pytest.mark.parametrize("k,h", [(2, 8), (4, 5), (8, 3)])
+def test_min_run_len_equal_runs_give_the_complete_tree(k, h):
+    """A zigzag (natural runs of two) with minRunLen 24 and n = 24 k^h has
+    r = k^h runs of exactly 24 elements.  For equal runs, boundary i has power
+    h - v_k(i) (Def. 3.1: the only multiple of k^-p in the midpoint interval
+    can be i / r), so Alg. 1 builds the complete k-ary tree of height h and
+    every element sits at depth h: M = h n."""
+    n = 24 * k ** h
+    a = (np.arange(n, dtype=np.uint32) ^ 1).astype(np.uint32)  # 1, 0, 3, 2, ...
+    res = oracle.sort(a, k=k, min_run_len=24)
+    r = k ** h
+    assert np.array_equal(res["keys"], np.arange(n, dtype=np.uint32))
+    assert np.array_equal(res["run_starts"], np.arange(r + 1, dtype=np.uint32) * 24)
+    assert res["merge_cost"] == h * n
+    assert np.all(res["leaf_depth"] == h)
+    assert res["num_levels"] == h
+
+    def vk(i):
+        t = 0
+        while i % k == 0:
+            i //= k
+            t += 1
+        return t
+    assert [int(p) for p in res["powers"][1:r]] == [h - vk(i) for i in range(1, r)]
