@@ -26,7 +26,6 @@ enum : int {
     kCtrHbmCount = 8,   // [64] nodes per power (level merges only)
     kCtrHbmSize = 72,   // [64] elements per power (level merges only)
     kCtrHbmFill = 136,  // [64] fill counters for bucketing
-    kCtrFrontierElems = 200,  // elements inside fused subtrees
     kCtrSplits = 201,   // splitters of the current level
     kCtrIntervals = 202,  // splitter intervals of the current level (packed into units)
     kCtrMaxRun = 203,   // longest run (elements)

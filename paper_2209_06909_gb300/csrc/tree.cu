@@ -490,7 +490,6 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tm
                 // they fit: the tile carries the node's power v as a floor, so
                 // its boundaries between the siblings (power v) stay delimiters
                 // and only levels above v are merged.
-                unsigned long long fe = 0;
                 uint32_t ga = 0, ge = 0, gsz = 0;  // open group: runs [ga, ge), gsz elements
                 for (uint32_t c = 0; c <= s.d; c++) {
                     bool take = false;
@@ -505,7 +504,6 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tm
                         uint32_t fs = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
                         if (fs < fused_cap) fused_list[fs] = make_uint4(ga, ge, depth + 1, v);
                         else dev_fail(status, kDevCapacity);
-                        fe += gsz;
                         gsz = 0;
                     }
                     if (take) {
@@ -514,13 +512,11 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tm
                         gsz += cs;
                     }
                 }
-                if (fe) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), fe);
             } else if (P[L] == 0 && P[R] == 0) {
                 // a root (of the array, or of one array of a batch) that fits a fused tile
                 uint32_t fs = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontier), 1ull);
                 if (fs < fused_cap) fused_list[fs] = make_uint4(L, R, 0u, 0u);
                 else dev_fail(status, kDevCapacity);
-                atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFrontierElems), (unsigned long long)size);
             }
         }
     }
