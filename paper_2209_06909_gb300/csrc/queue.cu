@@ -304,7 +304,9 @@ void worker_main(mps_queue* q) {
             cudaError_t e = cudaEventQuery(B.done);
             if (e == cudaErrorNotReady) { i++; continue; }
             const uint32_t dev = *q->h_status[B.stream];
-            mps_status s = e == cudaSuccess ? (dev ? (dev == mps::kDevSpin ? MPS_ERR_TIMEOUT : MPS_ERR_DEVICE_CHECK) : MPS_OK) : MPS_ERR_CUDA;
+            mps_status s = MPS_ERR_CUDA;
+            if (e == cudaSuccess) s = dev == 0 ? MPS_OK : (dev == mps::kDevSpin ? MPS_ERR_TIMEOUT : MPS_ERR_DEVICE_CHECK);
+            // per-request merge costs follow the status word at byte 8
             finish_tickets(q, B.tickets, s, dev, reinterpret_cast<const uint64_t*>(q->h_status[B.stream] + 2));
             q->stream_busy[B.stream] = 0;
             release_batch(q, B);

@@ -48,7 +48,8 @@ class Request(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("device_status", ctypes.c_uint32), ("tag", ctypes.c_uint64),
-                ("merge_cost", ctypes.c_uint64), ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+                ("merge_cost", ctypes.c_uint64), ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double)]
 
 
 def _result_dict(res: "Result") -> dict:
