@@ -54,3 +54,46 @@ def test_sort_rejects_bad_fan_in_before_any_device_work(lib):
     assert lib.mps_sort_keys(None, None, 1 << 31, 0, 4, None, 0, None, None) == 2
     lib.mps_status_string.restype = ctypes.c_char_p
     assert lib.mps_status_string(3) == b"workspace too small"
+
+
+# C structs shared with the binding: (C type, ctypes class or numpy dtype name)
+_STRUCTS = [("mps_tree", "Tree"), ("mps_queue_config", "QueueConfig"), ("mps_request", "Request"),
+            ("mps_result", "Result"), ("mps_profile_entry", "ProfileEntry"), ("mps_stats", "Stats")]
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors in the binding have the header's size and field
+    offsets (compiles a probe against include/mps.h with the host compiler)."""
+    import json
+    import shutil
+    import subprocess
+
+    import numpy as np
+
+    from paper_2209_06909_gb300 import mps
+    gcc = shutil.which("gcc")
+    cuda_inc = "/usr/local/cuda/include"
+    if gcc is None or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime_api.h")):
+        pytest.skip("needs gcc and the CUDA headers")
+    lines = ['#include <stdio.h>', '#include "mps.h"', "int main(void) {", '  printf("{");']
+    first = True
+    for cname, pyname in _STRUCTS + [("mps_node", None)]:
+        fields = ([f for f, _ in getattr(mps, pyname)._fields_] if pyname else list(mps.NODE_DTYPE.names))
+        sep = "" if first else ","
+        first = False
+        lines.append(f'  printf("{sep}\\"{cname}\\": [%zu", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf(", %zu", offsetof({cname}, {f}));')
+        lines.append('  printf("]");')
+    lines += ['  printf("}\\n");', "  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(src), "-o", str(exe)])
+    got = json.loads(subprocess.check_output([str(exe)]).decode())
+    for cname, pyname in _STRUCTS:
+        cls = getattr(mps, pyname)
+        want = [ctypes.sizeof(cls)] + [getattr(cls, f).offset for f, _ in cls._fields_]
+        assert got[cname] == want, (cname, got[cname], want)
+    dt = mps.NODE_DTYPE
+    assert got["mps_node"] == [dt.itemsize] + [dt.fields[f][1] for f in dt.names]
