@@ -97,3 +97,29 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[cname] == want, (cname, got[cname], want)
     dt = mps.NODE_DTYPE
     assert got["mps_node"] == [dt.itemsize] + [dt.fields[f][1] for f in dt.names]
+
+
+def _header_prototypes():
+    txt = open(os.path.join(ROOT, "include", "mps.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(mps_[a-z_]+)\s*\(([^;{]*?)\)\s*;", txt):
+        params = " ".join(m.group(2).split())
+        protos[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return protos
+
+
+def test_binding_argument_counts_match_the_header():
+    from paper_2209_06909_gb300 import build, mps
+    build.build()
+    L = mps.lib()
+    protos = _header_prototypes()
+    assert set(mps.EXPORTS) <= set(protos)
+    checked = 0
+    for name in mps.EXPORTS:
+        argtypes = getattr(L, name).argtypes
+        if argtypes is None:
+            continue
+        assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
+        checked += 1
+    assert checked >= 20
