@@ -22,6 +22,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mps.h"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -183,11 +185,16 @@ cudaEvent_t take_event() {
     return e;
 }
 
+// One stage of a sort: an NVTX range of the stage's name around the host
+// code that queues it (always; NVTX does nothing unless a tracer attaches),
+// and, while mps_profile_enable is on, CUDA events on the stream around its
+// kernels.
 struct ProfScope {
     bool on;
     ProfRec rec;
     cudaStream_t st;
     ProfScope(const char* name, double bytes, cudaStream_t s) : on(false), st(s) {
+        nvtxRangePushA(name);
         std::lock_guard<std::mutex> lk(g_prof_mu);
         if (!g_prof_on) return;
         on = true;
@@ -198,6 +205,7 @@ struct ProfScope {
         cudaEventRecord(rec.a, st);
     }
     ~ProfScope() {
+        nvtxRangePop();
         if (!on) return;
         cudaEventRecord(rec.b, st);
         std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -406,6 +414,10 @@ mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
                       uint64_t* d_costs, bool sync_at_end, cudaStream_t st) {
     if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    struct Range {  // NVTX range around the whole batch
+        Range() { nvtxRangePushA("sort_batch"); }
+        ~Range() { nvtxRangePop(); }
+    } range;
     if (d_costs && m) MPS_CUDA(cudaMemsetAsync(d_costs, 0, (size_t)m * 8, st));
     if (n == 0) return MPS_OK;
     if (!keys_in || !keys_out || !d_off || !d_ws || m == 0) return MPS_ERR_INVALID_ARG;
