@@ -14,9 +14,11 @@
  *     never allocates or frees device memory on these paths.  Host pointers
  *     are named h_*.
  *   - Calls are enqueued on the given CUDA stream.  mps_sort_keys,
- *     mps_sort_pairs and mps_merge_tree synchronise the stream twice to size
- *     their level loop (the number of runs and the per-level node counts are
- *     data dependent); outputs are complete when the call returns MPS_OK.
+ *     mps_sort_pairs and mps_merge_tree wait on the host twice for device
+ *     counters that size their launches (the number of runs, then the
+ *     per-level node counts; the fused merges already run during the second
+ *     wait) and synchronise the stream before returning: outputs are
+ *     complete when the call returns MPS_OK.
  *   - Key types: MPS_U32 (uint32_t) or MPS_U64 (uint64_t), compared as
  *     unsigned integers; every value, including the type's maximum, is a
  *     legal key (no sentinel is reserved; cf. Sec. 4 "Sentinel values").
