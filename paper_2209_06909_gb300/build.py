@@ -26,7 +26,7 @@ def sources():
 def _stale(obj: Path, src: Path) -> bool:
     if not obj.exists():
         return True
-    deps = [src, *CSRC.glob("*.cuh"), *INCLUDE.glob("*.h")]
+    deps = [src, *CSRC.glob("*.cuh"), *CSRC.glob("*.h"), *INCLUDE.glob("*.h")]
     return obj.stat().st_mtime < max(d.stat().st_mtime for d in deps)
 
 

@@ -24,6 +24,7 @@
 
 #include "../../include/mps.h"
 #include "common.cuh"
+#include "pool_alloc.h"
 
 namespace mps {
 mps_status batch_dispatch(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out, uint64_t n,
@@ -100,52 +101,9 @@ void move_requests(bool gather, mps_key_type kt, bool vals, const ReqPtrs* tab, 
     }
 }
 
-constexpr size_t kPoolAlign = 256;
-
-size_t align_up(size_t x) { return (x + kPoolAlign - 1) / kPoolAlign * kPoolAlign; }
-
-// First-fit allocator over [0, size) of the pool.
-class PoolAllocator {
-public:
-    explicit PoolAllocator(size_t size) { free_[0] = size; }
-    bool alloc(size_t bytes, size_t* off) {
-        bytes = align_up(bytes ? bytes : 1);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                size_t rest = it->second - bytes;
-                size_t start = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[start] = rest;
-                used_ += bytes;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        bytes = align_up(bytes ? bytes : 1);
-        used_ -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t used() const { return used_; }
-
-private:
-    std::map<size_t, size_t> free_;
-    size_t used_ = 0;
-};
+using mps::align_up;
+using mps::kPoolAlign;
+using mps::PoolAllocator;
 
 struct Ticket {
     mps_request req;
