@@ -92,9 +92,9 @@ __device__ __forceinline__ uint32_t merge_path2(const K* __restrict__ A, uint32_
 }
 
 // Writes outputs [o, stop) of the stable merge of A[ia..na) and B[ib..nb)
-// (ties to A).  Branch-free: every step loads the next element of the side it
-// took.  A[na] and B[nb] are read (never used), so one element past each side
-// must be readable shared memory.
+// (ties to A).  Every step loads the next element of the side it took, under
+// a predicate (one shared-memory load per output).  A[na] and B[nb] are read
+// (never used), so one element past each side must be readable shared memory.
 template <typename K, bool V>
 __device__ __forceinline__ void serial_merge2(const K* __restrict__ A, uint32_t na, const K* __restrict__ B, uint32_t nb,
                                               const uint32_t* __restrict__ vA, const uint32_t* __restrict__ vB,
@@ -103,14 +103,16 @@ __device__ __forceinline__ void serial_merge2(const K* __restrict__ A, uint32_t 
     K ka = A[ia];
     K kb = B[ib];
     for (; o < stop; o++) {
-        const bool take_a = (ib >= nb) || (ia < na && ka <= kb);
+        const bool take_a = (ib >= nb) | ((ia < na) & (ka <= kb));
         dst[o] = take_a ? ka : kb;
         if (V) vdst[o] = take_a ? vA[ia] : vB[ib];
-        ia += take_a ? 1u : 0u;
-        ib += take_a ? 0u : 1u;
-        const K kn = take_a ? A[ia] : B[ib];
-        ka = take_a ? kn : ka;
-        kb = take_a ? kb : kn;
+        if (take_a) {
+            ++ia;
+            ka = A[ia];
+        } else {
+            ++ib;
+            kb = B[ib];
+        }
     }
 }
 
@@ -260,6 +262,10 @@ __global__ void __launch_bounds__(kFusedThreads)
     __shared__ uint32_t stmp[kFusedThreads / 32 + 1];
     __shared__ uint4 stmp4[kFusedThreads / 32 + 1];
     __shared__ __align__(8) uint64_t s_bar;
+    // strictly descending runs longer than kShortRun, reversed by the whole block
+    constexpr uint32_t kShortRun = 64, kMaxLongRuns = 96;
+    __shared__ uint32_t s_long[kMaxLongRuns];
+    __shared__ uint32_t s_nlong;
     uint32_t phase = 0;
     const uint32_t tid = threadIdx.x;
     const uint32_t F = (uint32_t)ctr[kCtrFrontier];
@@ -270,6 +276,7 @@ __global__ void __launch_bounds__(kFusedThreads)
         const uint4 fr = flist[f];
         const uint32_t L = fr.x, R = fr.y;
         const bool odd = fr.z & 1u;
+        if (tid == 0) s_nlong = 0;
         const uint32_t floor_p = fr.w;  // boundaries of power <= floor_p are never merged here
         if (L >= R) {
             if (tid == 0) dev_fail(status, kDevFusedRange);
@@ -339,28 +346,50 @@ __global__ void __launch_bounds__(kFusedThreads)
         dflag += L - da;  // dflag[q] = direction of run L + q
         __syncthreads();
 
-        // ---- reverse the strictly descending runs (kA -> kB)
+        // ---- reverse the strictly descending runs in place (kA, from lead on):
+        // each thread swaps the short runs among its own, the block the long ones
+        K* tile = kA + lead;
+        uint32_t* vtile = V ? vA + lead : nullptr;
         {
-            const uint32_t pe = odd_chunk(len);
-            const uint32_t x0 = min(len, tid * pe), x1 = min(len, x0 + pe);
-            if (x0 < x1) {
-                uint32_t lo = 0, hi = nb;  // runs before x0: boundaries with offset <= x0
-                while (lo < hi) {
-                    const uint32_t m = (lo + hi) >> 1;
-                    if (be_off(bl0[m]) <= x0) lo = m + 1; else hi = m;
+            const uint32_t per_r = odd_chunk(nruns);
+            const uint32_t r0 = min(nruns, tid * per_r), r1 = min(nruns, r0 + per_r);
+            for (uint32_t r = r0; r < r1; r++) {
+                if (!dflag[r]) continue;
+                const uint32_t a = r ? be_off(bl0[r - 1]) : 0u;
+                const uint32_t b = r + 1 < nruns ? be_off(bl0[r]) : len;
+                if (b - a > kShortRun) {
+                    const uint32_t slot = atomicAdd(&s_nlong, 1u);
+                    if (slot < kMaxLongRuns) s_long[slot] = r;
+                    continue;
                 }
-                uint32_t rho = lo;
-                uint32_t rs0 = rho ? be_off(bl0[rho - 1]) : 0u;
-                uint32_t re0 = rho < nb ? be_off(bl0[rho]) : len;
-                for (uint32_t x = x0; x < x1; x++) {
-                    while (x >= re0) {
-                        rho++;
-                        rs0 = re0;
-                        re0 = rho < nb ? be_off(bl0[rho]) : len;
+                for (uint32_t x = a, y = b - 1; x < y; x++, y--) {
+                    const K t0 = tile[x];
+                    tile[x] = tile[y];
+                    tile[y] = t0;
+                    if (V) {
+                        const uint32_t u0 = vtile[x];
+                        vtile[x] = vtile[y];
+                        vtile[y] = u0;
                     }
-                    const uint32_t src = lead + (dflag[rho] ? (rs0 + re0 - 1 - x) : x);
-                    kB[x] = kA[src];
-                    if (V) vB[x] = vA[src];
+                }
+            }
+            __syncthreads();
+            // a run longer than kShortRun of at most C elements: fewer than kMaxLongRuns
+            const uint32_t nlong = min(s_nlong, kMaxLongRuns);
+            for (uint32_t j = 0; j < nlong; j++) {
+                const uint32_t r = s_long[j];
+                const uint32_t a = r ? be_off(bl0[r - 1]) : 0u;
+                const uint32_t b = r + 1 < nruns ? be_off(bl0[r]) : len;
+                for (uint32_t x = a + tid; x < a + (b - a) / 2; x += kFusedThreads) {
+                    const uint32_t y = a + b - 1 - x;
+                    const K t0 = tile[x];
+                    tile[x] = tile[y];
+                    tile[y] = t0;
+                    if (V) {
+                        const uint32_t u0 = vtile[x];
+                        vtile[x] = vtile[y];
+                        vtile[y] = u0;
+                    }
                 }
             }
         }
@@ -380,10 +409,10 @@ __global__ void __launch_bounds__(kFusedThreads)
             pmax = t.x;
             pmin = 255u - t.y;
         }
-        K* cur = kB;
-        K* oth = kA;
-        uint32_t* vcur = vB;
-        uint32_t* voth = vA;
+        K* cur = tile;
+        K* oth = kB;
+        uint32_t* vcur = vtile;
+        uint32_t* voth = vB;
         uint32_t na = nb;
         // boundary list of the current level and the list the next level gets
         // (bl1 is free once the load and reversal are done)
