@@ -14,16 +14,23 @@
  *     never allocates or frees device memory on these paths.  Host pointers
  *     are named h_*.
  *   - Calls are enqueued on the given CUDA stream.  mps_sort_keys,
- *     mps_sort_pairs and mps_merge_tree wait on the host twice for device
- *     counters that size their launches (the number of runs, then the
- *     per-level node counts; the fused merges already run during the second
- *     wait) and synchronise the stream before returning: outputs are
- *     complete when the call returns MPS_OK.
+ *     mps_sort_pairs, mps_merge_tree, mps_sort_keys_noalloc and
+ *     mps_sort_records return as soon as their kernels are queued: every
+ *     launch is sized by bounds from n and reads the actual counts (runs,
+ *     nodes, work units) from the workspace, so no host thread waits for the
+ *     device.  Outputs are complete in stream order (synchronise the stream,
+ *     or queue later work on it, before reading them).  A device-side check
+ *     failure is recorded in the workspace's status word; mps_sync_status or
+ *     mps_last_stats (both synchronise the stream) report it.
  *   - Key types: MPS_U32 (uint32_t) or MPS_U64 (uint64_t), compared as
  *     unsigned integers; every value, including the type's maximum, is a
  *     legal key (no sentinel is reserved; cf. Sec. 4 "Sentinel values").
  *   - Fan-in k must be 2, 4 or 8.  n must be below 2^31.
- *   - Output arrays must not overlap input arrays.
+ *   - For a single array, d_keys_out may equal (or overlap) d_keys_in, and
+ *     d_vals_out d_vals_in: the sort then reads a copy of the input that it
+ *     makes in the workspace (mps_workspace_size includes room for it).  Keys
+ *     and payloads must not overlap each other.  Batch outputs must not
+ *     overlap their inputs.
  *   - Errors are returned as mps_status; a device-side invariant violation
  *     (which would indicate a library bug) is reported as MPS_ERR_DEVICE_CHECK.
  */
@@ -118,7 +125,7 @@ mps_status mps_sort_pairs(const void* d_keys_in, const uint32_t* d_vals_in, void
  * payload is then moved once through that stable permutation:
  * d_vals_out[i] = d_vals_in[perm[i]].  d_vals_in and d_vals_out must not
  * overlap.  Workspace: mps_records_workspace_size(n, kt, k) bytes (the pairs
- * workspace plus 8 bytes per key).  Synchronises the stream. */
+ * workspace plus 8 bytes per key).  Returns once its kernels are queued. */
 mps_status mps_records_workspace_size(uint64_t n, mps_key_type kt, int k, size_t* bytes);
 mps_status mps_sort_records(const void* d_keys_in, const uint64_t* d_vals_in, void* d_keys_out,
                             uint64_t* d_vals_out, uint64_t n, mps_key_type kt, int k, void* d_ws,
@@ -262,9 +269,13 @@ mps_status mps_queue_destroy(mps_queue* q);
  *   n      : at most 2^20 keys (uint32 or uint64, any k in {2,4,8});
  *            larger n returns MPS_ERR_WORKSPACE without touching the GPU.
  *   Other arguments and outputs are those of mps_sort_keys (no tree output).
+ * Like mps_sort_keys, the call returns once its kernels are queued; the host
+ * does not wait for the device.
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls on a device share the one scratch
+ * (cudaGetSymbolAddress, with that device current) and keeps it for later
+ * calls; make that first call before any stream capture.  cudaDeviceReset
+ * invalidates the kept address: after a reset, do not call this function
+ * again in the same process.  All calls on a device share the one scratch
  * array, which keeps the previous call's contents (the sort clears what it
  * needs zeroed), so calls that overlap on the GPU -- e.g. from two host
  * threads or on two streams at once -- race and must be serialised. */
@@ -285,7 +296,15 @@ typedef struct {
 void mps_profile_enable(int on);
 int mps_profile_read(mps_profile_entry* out, int cap);
 
-/* Statistics of the most recent sort on this host thread (host memory). */
+/* Synchronises `stream` and returns the device-side status of the last sort
+ * or batch that used the workspace d_ws: MPS_OK, MPS_ERR_DEVICE_CHECK (an
+ * invariant check failed; mps_last_stats gives the code) or MPS_ERR_TIMEOUT (a
+ * bounded device wait ran out).  No counterpart in the paper. */
+mps_status mps_sync_status(const void* d_ws, cudaStream_t stream);
+
+/* Statistics of the most recent sort on this host thread (host memory).  For
+ * a single-array sort the statistics live in its workspace on the device: this
+ * call synchronises that sort's stream and reads them back. */
 typedef struct {
     uint64_t n, r, merge_cost, frontier_nodes, hbm_nodes;
     uint32_t num_levels, hbm_levels;
@@ -295,7 +314,9 @@ typedef struct {
                                            2 capacity, 3 tile overflow, 11-15 work-unit / fused /
                                            lone-run ranges, 16 array longer than max_len, 17 a
                                            bounded wait ran out (returned as MPS_ERR_TIMEOUT),
-                                           18 a splitter ranked outside its node (unsorted child) */
+                                           18 a splitter ranked outside its node (unsorted child),
+                                           19 a node above the fused-tile size at a power beyond
+                                           the levels queued for it */
     uint32_t pad;
 } mps_stats;
 

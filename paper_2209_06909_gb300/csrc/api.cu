@@ -55,7 +55,7 @@ struct Plan {
     int nlv_max = 0;
     // offsets
     size_t o_ctr, o_lvloff, o_det_state, o_rs, o_rdesc, o_fused, o_canon, o_lv[kMinTreeLevels], o_info,
-        o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_ufirst, o_ptiles, o_isz, o_hist, o_ktmp, o_vtmp, total;
+        o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_ufirst, o_ptiles, o_isz, o_hist, o_ktmp, o_vtmp, o_incopy, total;
 
     uint32_t m = 0;  // arrays of a batch (0: a single array)
     size_t o_bprm = 0;
@@ -102,6 +102,9 @@ struct Plan {
         o_bprm = take((size_t)2 * std::max<uint32_t>(m, 1) * 8);
         o_ktmp = take(n * kb);
         o_vtmp = vals ? take(n * 4) : o;
+        // a single array may be sorted into the memory it is read from: room for a copy of the input
+        o_incopy = m == 0 ? take(n * kb) : o;
+        if (m == 0 && vals) take(n * 4);
         total = o;
     }
 
@@ -163,16 +166,35 @@ void set_levels(WsView& w, uint32_t r) {
 
 // ------------------------------------------------------------- profiling
 
+// Algorithmic bytes of a profiled stage.  Some are known when the stage is
+// queued; the others depend on device counters (the run count, the merge
+// cost and the per-level node sizes) and are computed from a snapshot of the
+// sort's counter block, copied to pinned host memory behind the sort's last
+// kernel, when mps_profile_read asks for them.
+enum ByteRule : int {
+    kBytesFixed = 0,   // `bytes` as given
+    kBytesFused = 1,   // 2 * b * (M - elements merged by level merges), b = `bytes`
+    kBytesLevel = 2,   // 2 * b * (elements of the nodes of power p), b = `bytes`
+    kBytesPerRun = 3,  // `bytes` * r
+};
+
 struct ProfRec {
     const char* name;
     cudaEvent_t a, b;
     double bytes;
+    int rule;
+    int p;
+    int snap;  // counter snapshot of the sort the stage belongs to (-1: none)
 };
 
+constexpr int kSnapSlots = 256;
 std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
+uint64_t* g_snap_host = nullptr;  // kSnapSlots counter blocks, pinned
+cudaEvent_t g_snap_ev[kSnapSlots];
+int g_snap_used = 0;
 
 cudaEvent_t take_event() {
     if (!g_event_pool.empty()) {
@@ -193,13 +215,16 @@ struct ProfScope {
     bool on;
     ProfRec rec;
     cudaStream_t st;
-    ProfScope(const char* name, double bytes, cudaStream_t s) : on(false), st(s) {
+    ProfScope(const char* name, double bytes, cudaStream_t s, int rule = kBytesFixed, int p = 0) : on(false), st(s) {
         nvtxRangePushA(name);
         std::lock_guard<std::mutex> lk(g_prof_mu);
         if (!g_prof_on) return;
         on = true;
         rec.name = name;
         rec.bytes = bytes;
+        rec.rule = rule;
+        rec.p = p;
+        rec.snap = -1;
         rec.a = take_event();
         rec.b = take_event();
         cudaEventRecord(rec.a, st);
@@ -213,7 +238,85 @@ struct ProfScope {
     }
 };
 
+size_t prof_mark() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    return g_prof.size();
+}
+
+// Behind the last kernel of a sort: a copy of its counter block for the
+// stages recorded since `mark` (only while profiling).
+void prof_snapshot(size_t mark, const uint64_t* d_ctr, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on || g_prof.size() <= mark || !g_snap_host || g_snap_used >= kSnapSlots) return;
+    const int slot = g_snap_used++;
+    if (cudaMemcpyAsync(g_snap_host + (size_t)slot * kCtrWords, d_ctr, kCtrWords * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return;
+    cudaEventRecord(g_snap_ev[slot], st);
+    for (size_t i = mark; i < g_prof.size(); i++) g_prof[i].snap = slot;
+}
+
+// elements merged by level merges (nodes above the fused-tile size), from a counter block
+uint64_t level_elems(const uint64_t* h) {
+    uint64_t s = 0;
+    for (int p = 1; p < kMaxLevels; p++) s += h[kCtrHbmCount + p] ? h[kCtrHbmSize + p] : 0;
+    return s;
+}
+
+double rec_bytes(const ProfRec& r) {
+    if (r.rule == kBytesFixed) return r.bytes;
+    if (r.snap < 0) return 0.0;
+    cudaEventSynchronize(g_snap_ev[r.snap]);
+    const uint64_t* h = g_snap_host + (size_t)r.snap * kCtrWords;
+    switch (r.rule) {
+        case kBytesFused: {
+            const uint64_t lv = level_elems(h);
+            return 2.0 * r.bytes * (double)(h[kCtrM] >= lv ? h[kCtrM] - lv : 0);
+        }
+        case kBytesLevel: return h[kCtrHbmCount + r.p] ? 2.0 * r.bytes * (double)h[kCtrHbmSize + r.p] : 0.0;
+        case kBytesPerRun: return r.bytes * (double)h[kCtrR];
+    }
+    return 0.0;
+}
+
+// ------------------------------------------------------------- statistics
+
+// The most recent sort on this host thread: its statistics live in its
+// workspace's counter block and are read back (after synchronising its
+// stream) only when mps_last_stats asks for them.
+struct LastSort {
+    const uint64_t* d_ctr = nullptr;
+    cudaStream_t st = nullptr;
+    double b = 4.0;           // bytes per element (key + payload)
+    bool pending = false;     // counters not read back yet
+};
+thread_local LastSort g_pending;
 thread_local mps_stats g_last{};
+
+void stats_from_counters(const uint64_t* h, double b, mps_stats& s) {
+    s.r = h[kCtrR];
+    s.merge_cost = h[kCtrM];
+    s.frontier_nodes = h[kCtrFrontier];
+    s.hbm_nodes = h[kCtrHbmTotal];
+    s.num_levels = (uint32_t)__builtin_popcountll(h[kCtrLevelBits]);
+    s.device_status = (uint32_t)h[kCtrStatus];
+    s.hbm_levels = 0;
+    for (int p = 1; p < kMaxLevels; p++) s.hbm_levels += h[kCtrHbmCount + p] ? 1u : 0u;
+    const uint64_t lv = level_elems(h);
+    s.bytes_levels = (uint64_t)(2.0 * b * (double)lv);
+    s.bytes_fused = (uint64_t)(2.0 * b * (double)(s.merge_cost >= lv ? s.merge_cost - lv : 0));
+}
+
+// Synchronises the pending sort's stream and fills g_last from its counters.
+mps_status settle_last() {
+    if (!g_pending.pending) return MPS_OK;
+    g_pending.pending = false;
+    uint64_t h[kCtrWords];
+    if (cudaMemcpyAsync(h, g_pending.d_ctr, sizeof(h), cudaMemcpyDeviceToHost, g_pending.st) != cudaSuccess ||
+        cudaStreamSynchronize(g_pending.st) != cudaSuccess)
+        return MPS_ERR_CUDA;
+    stats_from_counters(h, g_pending.b, g_last);
+    return MPS_OK;
+}
 
 bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
     if (!a || !b || !an || !bn) return false;
@@ -227,181 +330,130 @@ bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
         if (e_ != cudaSuccess) return MPS_ERR_CUDA;    \
     } while (0)
 
+// Largest power whose nodes can be larger than a fused tile (T_max elements)
+// in arrays of at most max_len elements.  Every boundary inside a node of
+// power v has power >= v, i.e. the normalised midpoints of adjacent runs agree
+// on their first (v-1) log2 k bits (Def. 3.1 with P_k = ceil(P_2 / log2 k)):
+// all run midpoints of the node lie in one interval of max_len / k^(v-1)
+// elements.  Its first and last runs each meet a boundary of power >= v, so
+// each is shorter than 2 max_len / k^(v-1).  The node is therefore smaller
+// than 3 max_len / k^(v-1), and level merges exist only for powers v with
+// T_max k^(v-1) < 3 max_len; the bound below uses 4 max_len as margin.
+int level_power_bound(uint64_t max_len, int k, uint32_t tmax) {
+    const uint64_t lim = 4 * std::max<uint64_t>(max_len, 1);
+    uint64_t span = tmax;  // T_max * k^(v-1)
+    int v = 0;
+    while (span < lim && v < kMaxLevels - 1) {
+        v++;
+        span *= (uint64_t)k;
+    }
+    return v;
+}
+
+// One array: every launch is sized by bounds from n and takes its counts from
+// the device, so the call only queues kernels on the stream and returns; no
+// host thread waits for the device.  Levels are queued for every power up to
+// the bound for n; a level without nodes costs its launches and nothing else.
 template <typename K, bool V>
 mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, uint64_t n, int k,
                      void* d_ws, size_t ws_bytes, const mps_tree* tree, bool move_keys, cudaStream_t st) {
     if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
-    g_last = mps_stats{};
-    g_last.n = n;
+    const double b = (double)sizeof(K) + (V ? 4.0 : 0.0);
     g_launches = 0;
     if (n == 0) {
         if (tree && tree->counts) MPS_CUDA(cudaMemsetAsync(tree->counts, 0, 4 * sizeof(uint64_t), st));
-        MPS_CUDA(cudaStreamSynchronize(st));
+        g_pending.pending = false;
+        g_last = mps_stats{};
         return MPS_OK;
     }
     if (!keys_in || !d_ws) return MPS_ERR_INVALID_ARG;
     if (move_keys && !keys_out) return MPS_ERR_INVALID_ARG;
+    if (tree && tree->nodes && !tree->node_first) return MPS_ERR_INVALID_ARG;  // the node table needs node_first
     if (V && move_keys && (!vals_in || !vals_out)) return MPS_ERR_INVALID_ARG;
-    if (move_keys && overlaps(keys_in, n * sizeof(K), keys_out, n * sizeof(K))) return MPS_ERR_INVALID_ARG;
-    if (V && move_keys && overlaps(vals_in, n * 4, vals_out, n * 4)) return MPS_ERR_INVALID_ARG;
+    const size_t kbytes = n * sizeof(K), vbytes = n * 4;
+    // keys and payloads must not overlap each other (an output may overlap its own input)
+    if (V && move_keys &&
+        (overlaps(keys_in, kbytes, vals_out, vbytes) || overlaps(vals_in, vbytes, keys_out, kbytes) ||
+         overlaps(keys_out, kbytes, vals_out, vbytes)))
+        return MPS_ERR_INVALID_ARG;
     Plan plan(n, sizeof(K), V, k);
     if (ws_bytes < plan.total) return MPS_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(d_ws) % 16) return MPS_ERR_INVALID_ARG;
     WsView ws = plan.view(d_ws);
     const MergeGeom& g = plan.g;
-    const double b = (double)sizeof(K) + (V ? 4.0 : 0.0);
+    const size_t mark = prof_mark();
 
-    uint64_t h_ctr[kCtrWords];
     MPS_CUDA(cudaMemsetAsync(ws.counters, 0, kCtrWords * 8, st));
+    // The merges read leaves from the input while node outputs land in
+    // keys_out, so an output that overlaps its input sorts a copy of the input
+    // (kept in the workspace).
+    if (move_keys && (overlaps(keys_in, kbytes, keys_out, kbytes) || (V && overlaps(vals_in, vbytes, vals_out, vbytes)))) {
+        K* kc = reinterpret_cast<K*>(static_cast<char*>(d_ws) + plan.o_incopy);
+        MPS_CUDA(cudaMemcpyAsync(kc, keys_in, kbytes, cudaMemcpyDeviceToDevice, st));
+        keys_in = kc;
+        if (V) {
+            uint32_t* vc = reinterpret_cast<uint32_t*>(static_cast<char*>(d_ws) + plan.o_incopy + align_up(kbytes));
+            MPS_CUDA(cudaMemcpyAsync(vc, vals_in, vbytes, cudaMemcpyDeviceToDevice, st));
+            vals_in = vc;
+        }
+    }
+    const uint32_t r_bound = (uint32_t)std::min<uint64_t>(plan.rmax, n + 1);
+    set_levels(ws, r_bound);
     {
-        ProfScope ps("detect_runs", (double)n * sizeof(K) * 2, st);
+        ProfScope ps("detect_runs", (double)kbytes, st);
         launch_detect<K>(keys_in, n, ws, st);
     }
-    MPS_CUDA(cudaGetLastError());
-    MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, (kCtrStatus + 1) * 8, cudaMemcpyDeviceToHost, st));
-    MPS_CUDA(cudaStreamSynchronize(st));
-    if ((uint32_t)h_ctr[kCtrStatus]) {
-        g_last.device_status = (uint32_t)h_ctr[kCtrStatus];
-        return device_error((uint32_t)h_ctr[kCtrStatus]);
-    }
-    const uint32_t r = (uint32_t)h_ctr[kCtrR];
-    g_last.r = r;
-
-    if (r <= 1) {
-        if (move_keys) {
-            ProfScope ps("copy_single_run", (double)n * b * 2, st);
-            launch_copy_single_run<K, V>(keys_in, vals_in, keys_out, vals_out, n, ws, st);
-        }
-        if (tree) {
-            if (tree->run_starts) MPS_CUDA(cudaMemcpyAsync(tree->run_starts, ws.run_starts, 8, cudaMemcpyDeviceToDevice, st));
-            if (tree->run_desc) MPS_CUDA(cudaMemcpyAsync(tree->run_desc, ws.run_desc, 1, cudaMemcpyDeviceToDevice, st));
-            if (tree->powers) MPS_CUDA(cudaMemsetAsync(tree->powers, 0, 2, st));
-            if (tree->node_first) MPS_CUDA(cudaMemsetAsync(tree->node_first, 0, 4, st));
-            if (tree->leaf_depth) MPS_CUDA(cudaMemsetAsync(tree->leaf_depth, 0, 1, st));
-            if (tree->counts) {
-                uint64_t c[4] = {1, 0, 0, 0};
-                MPS_CUDA(cudaMemcpyAsync(tree->counts, c, sizeof(c), cudaMemcpyHostToDevice, st));
-            }
-        }
-        MPS_CUDA(cudaGetLastError());
-        MPS_CUDA(cudaStreamSynchronize(st));
-        g_last.launches = g_launches;
-        return MPS_OK;
-    }
-
-    set_levels(ws, r);
-    {
-        ProfScope ps("powers", (double)r * 9.0, st);
-        launch_powers(n, r, k, ws, st);
+    if (move_keys) {
+        ProfScope ps("copy_single_run", 0.0, st);
+        launch_copy_single_run<K, V>(keys_in, vals_in, keys_out, vals_out, n, ws, st);
     }
     {
-        ProfScope ps("tree_scans", (double)r * 4.0, st);
-        launch_mintree(r, ws, st);
-        launch_masks(r, tree && tree->leaf_depth, tree ? tree->leaf_depth : nullptr, n, k, g.tmax, ws, st);
+        ProfScope ps("powers", 9.0, st, kBytesPerRun);
+        launch_powers(n, r_bound, k, ws, st);
     }
     {
-        ProfScope ps("node_pass", (double)r * 2.0, st);
-        launch_node_pass(r, k, g.tmax, ws, st);
+        ProfScope ps("tree_scans", 4.0, st, kBytesPerRun);
+        launch_mintree(r_bound, ws, st);
+        launch_masks(r_bound, tree && tree->leaf_depth, tree ? tree->leaf_depth : nullptr, n, k, g.tmax, ws, st);
     }
-    MPS_CUDA(cudaGetLastError());
-    MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, sizeof(h_ctr), cudaMemcpyDeviceToHost, st));
-    // The host needs the counters to queue the level merges, but the node
-    // buckets and the fused merge take their counts from the device: they are
-    // queued first, and the host waits only for the counters, so that the
-    // GPU runs the fused merge while the host reads them.
-    cudaEvent_t ev_ctr = nullptr;
-    MPS_CUDA(cudaEventCreateWithFlags(&ev_ctr, cudaEventDisableTiming));
-    const cudaError_t rec_err = cudaEventRecord(ev_ctr, st);
-    std::unique_ptr<ProfScope> ps_fused;
-    if (rec_err == cudaSuccess && move_keys) {
-        launch_bucket(plan.nodes_cap, ws, st);
-        ps_fused.reset(new ProfScope("fused_merge", 0.0, st));
-        launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, plan.fused_cap, g, ws, st);
-    }
-    const cudaError_t wait_err = rec_err == cudaSuccess ? cudaEventSynchronize(ev_ctr) : rec_err;
-    cudaEventDestroy(ev_ctr);
-    // on any early return below, nothing is left running on the stream
-    auto drain = [&](mps_status code) {
-        ps_fused.reset();
-        cudaStreamSynchronize(st);
-        return code;
-    };
-    if (wait_err != cudaSuccess) return drain(MPS_ERR_CUDA);
-    g_last.device_status = (uint32_t)h_ctr[kCtrStatus];
-    if ((uint32_t)h_ctr[kCtrStatus]) return drain(device_error((uint32_t)h_ctr[kCtrStatus]));
-    const uint64_t hbm_total = h_ctr[kCtrHbmTotal];
-    if (hbm_total > plan.nodes_cap || h_ctr[kCtrFrontier] > plan.fused_cap) return drain(MPS_ERR_DEVICE_CHECK);
-    g_last.merge_cost = h_ctr[kCtrM];
-    g_last.frontier_nodes = h_ctr[kCtrFrontier];
-    g_last.hbm_nodes = hbm_total;
-    g_last.num_levels = (uint32_t)__builtin_popcountll(h_ctr[kCtrLevelBits]);
-
-    // merge cost of the nodes above T_max (one level-merge launch per power);
-    // the rest of M belongs to the nodes merged inside fused subtrees
-    uint64_t m_levels = 0;
-    for (int p = 1; p < kMaxLevels; p++) m_levels += h_ctr[kCtrHbmCount + p] ? h_ctr[kCtrHbmSize + p] : 0;
-    const uint64_t m_fused = g_last.merge_cost >= m_levels ? g_last.merge_cost - m_levels : 0;
-    if (ps_fused) {
-        // algorithmic bytes (Sec. 2.2 cost model): one read and one write of
-        // b bytes per element per merge, i.e. 2 b M_fused; the kernel itself
-        // reads and writes each element of its subtrees once.  The scope ends
-        // here, right behind the fused launch in stream order.
-        ps_fused->rec.bytes = 2.0 * b * (double)m_fused;
-        ps_fused.reset();
+    {
+        ProfScope ps("node_pass", 2.0, st, kBytesPerRun);
+        launch_node_pass(r_bound, k, g.tmax, (uint32_t)level_power_bound(n, k, g.tmax), ws, st);
     }
     if (move_keys) {
-        uint64_t lvl_bytes = 0;
-        for (int p = kMaxLevels - 1; p >= 1; p--) {
-            const uint32_t cnt = (uint32_t)h_ctr[kCtrHbmCount + p];
-            if (!cnt) continue;
-            const uint64_t elems = h_ctr[kCtrHbmSize + p];
-            g_last.hbm_levels++;
-            lvl_bytes += (uint64_t)(2 * b * elems);
-            {
-                ProfScope ps("level_plan", (double)cnt * 64.0, st);
-                launch_level_plan<K>(p, cnt, elems, k, keys_in, keys_out, g, ws, st);
-            }
-            ProfScope ps("level_merge", 2.0 * b * (double)elems, st);
-            launch_level_merge<K, V>(cnt, elems, keys_in, vals_in, keys_out, vals_out, g, ws, st);
+        launch_bucket(plan.nodes_cap, ws, st);
+        {
+            // algorithmic bytes (Sec. 2.2 cost model): one read and one write of
+            // b bytes per element per merge inside the fused subtrees
+            ProfScope ps("fused_merge", b, st, kBytesFused);
+            launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, plan.fused_cap, g, ws, st);
         }
-        g_last.bytes_levels = lvl_bytes;
-        MPS_CUDA(cudaGetLastError());
+        const uint32_t nn_bound = (uint32_t)(n / g.tmax + 1);
+        for (int p = level_power_bound(n, k, g.tmax); p >= 1; p--) {
+            {
+                ProfScope ps("level_plan", 0.0, st);
+                launch_level_plan<K>(p, nn_bound, n, k, keys_in, keys_out, g, ws, st);
+            }
+            ProfScope ps("level_merge", b, st, kBytesLevel, p);
+            launch_level_merge<K, V>(nn_bound, n, keys_in, vals_in, keys_out, vals_out, g, ws, st);
+        }
     }
     if (tree) {
-        if (tree->run_starts)
-            MPS_CUDA(cudaMemcpyAsync(tree->run_starts, ws.run_starts, ((size_t)r + 1) * 4, cudaMemcpyDeviceToDevice, st));
-        if (tree->run_desc) MPS_CUDA(cudaMemcpyAsync(tree->run_desc, ws.run_desc, r, cudaMemcpyDeviceToDevice, st));
-        if (tree->powers) MPS_CUDA(cudaMemcpyAsync(tree->powers, ws.powers, (size_t)r + 1, cudaMemcpyDeviceToDevice, st));
-        if (tree->node_first || tree->nodes) {
-            uint32_t* nf = tree->node_first;
-            if (!nf) return MPS_ERR_INVALID_ARG;  // the node table needs node_first
-            launch_tree_dump(r, k, ws, nf, tree->nodes, nullptr, st);
-        }
-        if (tree->counts) {
-            uint64_t c[4] = {r, h_ctr[kCtrNodes], (uint64_t)__builtin_popcountll(h_ctr[kCtrLevelBits]), h_ctr[kCtrM]};
-            MPS_CUDA(cudaMemcpyAsync(tree->counts, c, sizeof(c), cudaMemcpyHostToDevice, st));
-        }
-        MPS_CUDA(cudaGetLastError());
+        if (tree->run_starts || tree->run_desc || tree->powers || tree->leaf_depth || tree->counts)
+            launch_tree_arrays(r_bound, ws, tree->run_starts, tree->run_desc, tree->powers, tree->leaf_depth, tree->counts, st);
+        if (tree->node_first) launch_tree_dump(r_bound, k, ws, tree->node_first, tree->nodes, st);
     }
-    uint32_t status = 0;
-    MPS_CUDA(cudaMemcpyAsync(&status, ws.counters + kCtrStatus, 4, cudaMemcpyDeviceToHost, st));
-    MPS_CUDA(cudaStreamSynchronize(st));
-    g_last.device_status = status;
-    if (status) return device_error(status);
-    g_last.bytes_fused = (uint64_t)(2 * b * (double)m_fused);
+    MPS_CUDA(cudaGetLastError());
+    prof_snapshot(mark, ws.counters, st);
+    g_last = mps_stats{};
+    g_last.n = n;
     g_last.launches = g_launches;
+    g_pending.d_ctr = ws.counters;
+    g_pending.st = st;
+    g_pending.b = b;
+    g_pending.pending = true;
     return MPS_OK;
-}
-
-
-// Largest power that arrays of at most max_len elements can have, plus one:
-// P_k <= ceil((ceil(log2 n) + 1) / log2 k) (Sec. 3.3 bound, squished to k).
-int power_bound(uint64_t max_len, int k) {
-    int lg = 0;
-    while ((1ull << lg) < std::max<uint64_t>(max_len, 1)) lg++;
-    const int t = k == 2 ? 1 : (k == 4 ? 2 : 3);
-    return std::min(kMaxLevels - 1, (lg + 1 + t - 1) / t + 1);
 }
 
 // Batch of m arrays laid end to end (offsets d_off[0..m], d_off[m] = n).
@@ -441,29 +493,26 @@ mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
     launch_powers(n, r_bound, k, ws, st);
     launch_mintree(r_bound, ws, st);
     launch_masks(r_bound, false, nullptr, n, k, g.tmax, ws, st);
-    launch_node_pass(r_bound, k, g.tmax, ws, st);
+    launch_node_pass(r_bound, k, g.tmax, (uint32_t)level_power_bound(max_len ? max_len : n, k, g.tmax), ws, st);
     launch_copy_lone_runs<K, V>(keys_in, vals_in, keys_out, vals_out, r_bound, ws, st);
     launch_bucket(plan.nodes_cap, ws, st);
     launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, plan.fused_cap, g, ws, st);
     const uint32_t nn_bound = (uint32_t)(n / g.tmax + 1);
-    for (int p = power_bound(max_len ? max_len : n, k); p >= 1; p--) {
+    for (int p = level_power_bound(max_len ? max_len : n, k, g.tmax); p >= 1; p--) {
         launch_level_plan<K>(p, nn_bound, n, k, keys_in, keys_out, g, ws, st);
         launch_level_merge<K, V>(nn_bound, n, keys_in, vals_in, keys_out, vals_out, g, ws, st);
     }
     MPS_CUDA(cudaGetLastError());
+    g_pending.pending = false;
     if (sync_at_end) {
-        uint64_t h_ctr[8];
+        uint64_t h_ctr[kCtrWords];
         MPS_CUDA(cudaMemcpyAsync(h_ctr, ws.counters, sizeof(h_ctr), cudaMemcpyDeviceToHost, st));
         MPS_CUDA(cudaStreamSynchronize(st));
         g_last = mps_stats{};
         g_last.n = n;
-        g_last.device_status = (uint32_t)h_ctr[kCtrStatus];
-        if ((uint32_t)h_ctr[kCtrStatus]) return device_error((uint32_t)h_ctr[kCtrStatus]);
-        g_last.r = h_ctr[kCtrR];
-        g_last.merge_cost = h_ctr[kCtrM];
-        g_last.frontier_nodes = h_ctr[kCtrFrontier];
-        g_last.hbm_nodes = h_ctr[kCtrHbmTotal];
+        stats_from_counters(h_ctr, (double)sizeof(K) + (V ? 4.0 : 0.0), g_last);
         g_last.launches = g_launches;
+        if ((uint32_t)h_ctr[kCtrStatus]) return device_error((uint32_t)h_ctr[kCtrStatus]);
     }
     return MPS_OK;
 }
@@ -719,7 +768,15 @@ void mps_profile_enable(int on) {
         g_event_pool.push_back(r.b);
     }
     g_prof.clear();
+    g_snap_used = 0;
     g_prof_on = on != 0;
+    if (g_prof_on && !g_snap_host) {
+        void* h = nullptr;
+        if (cudaMallocHost(&h, (size_t)kSnapSlots * kCtrWords * 8) == cudaSuccess) {
+            g_snap_host = static_cast<uint64_t*>(h);
+            for (int i = 0; i < kSnapSlots; i++) cudaEventCreateWithFlags(&g_snap_ev[i], cudaEventDisableTiming);
+        }
+    }
 }
 
 int mps_profile_read(mps_profile_entry* out, int cap) {
@@ -739,7 +796,7 @@ int mps_profile_read(mps_profile_entry* out, int cap) {
         }
         e->launches++;
         e->total_ms += ms;
-        e->bytes += r.bytes;
+        e->bytes += rec_bytes(r);
     }
     int m = std::min<int>(cap, (int)agg.size());
     for (int i = 0; i < m; i++) out[i] = agg[i];
@@ -748,8 +805,19 @@ int mps_profile_read(mps_profile_entry* out, int cap) {
 
 mps_status mps_last_stats(mps_stats* out) {
     if (!out) return MPS_ERR_INVALID_ARG;
+    const mps_status s = settle_last();
     *out = g_last;
-    return MPS_OK;
+    return s;
+}
+
+mps_status mps_sync_status(const void* d_ws, cudaStream_t stream) {
+    if (!d_ws) return MPS_ERR_INVALID_ARG;
+    uint32_t status = 0;
+    const uint64_t* ctr = static_cast<const uint64_t*>(d_ws);  // the counter block opens every workspace
+    if (cudaMemcpyAsync(&status, ctr + kCtrStatus, 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return MPS_ERR_CUDA;
+    return status ? device_error(status) : MPS_OK;
 }
 
 const char* mps_status_string(mps_status s) {

@@ -23,6 +23,7 @@ enum DevError : uint32_t {
     kDevMaxLen = 16,     // a batch array was longer than the caller's max_len
     kDevSpin = 17,       // a bounded wait on another block ran out
     kDevSplitSlot = 18,  // a splitter ranked outside its node's splitters (children not sorted)
+    kDevLevelBound = 19, // a node larger than a fused tile at a power above the host's level bound
 };
 
 __device__ __forceinline__ void dev_fail(uint32_t* status, uint32_t code) { atomicCAS(status, 0u, code); }

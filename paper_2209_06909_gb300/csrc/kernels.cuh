@@ -115,10 +115,16 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
 void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st);
 void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, uint64_t n, int k, uint32_t tmax, const WsView& ws,
                   cudaStream_t st);
-void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st);
+// vmax: largest power for which level merges are queued (a larger node at a
+// higher power is reported as device status kDevLevelBound)
+void launch_node_pass(uint32_t r, int k, uint32_t tmax, uint32_t vmax, const WsView& ws, cudaStream_t st);
 void launch_bucket(uint32_t total_bound, const WsView& ws, cudaStream_t st);
-void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first, void* nodes,
-                      uint64_t* counts_out, cudaStream_t st);
+// Canonical tree of the last sort (r read on the device, r <= r_bound).
+void launch_tree_dump(uint32_t r_bound, int k, const WsView& ws, uint32_t* node_first, void* nodes, cudaStream_t st);
+// Run starts, directions, powers and counts {r, nodes, levels, M} of the last
+// sort copied to the caller's tree arrays (any may be null).
+void launch_tree_arrays(uint32_t r_bound, const WsView& ws, uint32_t* run_starts, uint8_t* run_desc, uint8_t* powers,
+                        uint8_t* leaf_depth, uint64_t* counts, cudaStream_t st);
 
 // merge.cu
 template <typename K, bool V>

@@ -1080,9 +1080,13 @@ __global__ void __launch_bounds__(kLvlThreads)
     }
 }
 
+// An input that is a single run (r = 1, read on the device) is the sorted
+// output itself, reversed if strictly descending; any other input leaves at once.
 template <typename K, bool V>
 __global__ void k_copy_single_run(const K* __restrict__ in, const uint32_t* __restrict__ vin, K* __restrict__ out,
-                                  uint32_t* __restrict__ vout, uint64_t n, const uint8_t* __restrict__ rdesc) {
+                                  uint32_t* __restrict__ vout, uint64_t n, const uint8_t* __restrict__ rdesc,
+                                  const uint64_t* __restrict__ ctr) {
+    if (ctr[kCtrR] != 1) return;
     const bool rev = rdesc[0] != 0;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t s = rev ? n - 1 - i : i;
@@ -1194,7 +1198,7 @@ template <typename K, bool V>
 void launch_copy_single_run(const K* in, const uint32_t* vin, K* out, uint32_t* vout, uint64_t n, const WsView& ws,
                             cudaStream_t st) {
     uint32_t grid = (uint32_t)std::min<uint64_t>(ceil_div(n, 256), 152 * 8);
-    k_copy_single_run<K, V><<<grid, 256, 0, st>>>(in, vin, out, vout, n, ws.run_desc);
+    k_copy_single_run<K, V><<<grid, 256, 0, st>>>(in, vin, out, vout, n, ws.run_desc, ws.counters);
     g_launches += 1;
 }
 

@@ -69,7 +69,6 @@ mps_status mps_sort_records(const void* d_keys_in, const uint64_t* d_vals_in, vo
     if (s != MPS_OK) return s;
     k_gather_u64<<<grid, 256, 0, stream>>>(d_vals_in, perm, d_vals_out, n);
     if (cudaGetLastError() != cudaSuccess) return MPS_ERR_CUDA;
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return MPS_ERR_CUDA;
     return MPS_OK;
 }
 

@@ -329,8 +329,9 @@ __global__ void __launch_bounds__(kDetThreads, 4) k_detect(const K* __restrict__
 // of 255 up to the next multiple of 32, the bit set of powers that occur and
 // the longest run.  Each thread takes 16 boundaries: 16-byte loads of run
 // starts (the array is padded past r) and one 16-byte store of powers.
+template <uint32_t LOG2K, bool BATCH>
 __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run_starts, uint64_t* __restrict__ counters,
-                                                uint64_t n, uint32_t w, uint64_t magic, uint32_t log2k,
+                                                uint64_t n, uint32_t w, uint64_t magic,
                                                 const uint64_t* __restrict__ off, uint32_t m,
                                                 const uint2* __restrict__ arr_param,
                                                 uint8_t* __restrict__ powers, unsigned long long* __restrict__ level_bits) {
@@ -341,6 +342,10 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
     const uint32_t pad_end = (r + 1 + 31) / 32 * 32;
     unsigned long long bits = 0;
     uint32_t longest = 0;  // longest run seen by this thread
+    // a single array: 2n and its shift are the same for every boundary
+    const uint64_t d1 = 2 * n;
+    const bool pow2_1 = (d1 & (d1 - 1)) == 0;
+    const int sh1 = (int)w - ((int)__ffsll((long long)d1) - 1);
     for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < groups; gi += gridDim.x * blockDim.x) {
         const uint32_t i0 = gi * 16;
         uint32_t rv[20];
@@ -353,7 +358,7 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
         const uint32_t prev = i0 ? run_starts[i0 - 1] : 0u;
         // the array holding run i0 (a batch sorts each array on its own): last a with off[a] <= s
         uint32_t arr = 0;
-        if (off != nullptr) {
+        if (BATCH) {
             uint32_t lo = 0, hi = m + 1;
             const uint32_t s0 = rv[0];
             while (hi - lo > 1) {
@@ -376,7 +381,7 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
                 uint32_t ww = w;
                 uint64_t mg = magic;
                 bool arr_start = false;
-                if (off != nullptr && i >= 1 && i < r) {
+                if (BATCH && i >= 1 && i < r) {
                     while (arr < m && off[arr + 1] <= si) arr++;
                     base = off[arr];
                     nn = off[arr + 1] - base;
@@ -386,13 +391,13 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
                     mg = ((uint64_t)prm.y << 32) | arr_param[m + arr].x;
                 }
                 if (i >= 1 && i < r && !arr_start) {
-                    const uint64_t d = 2 * nn;
+                    const uint64_t d = BATCH ? 2 * nn : d1;
                     const uint32_t a2 = (sp - base) + (si - base);         // 2n * a  (< 2n <= 2^32)
                     const uint32_t b2 = (si - base) + (rv[q + 1] - base);  // 2n * b
                     uint32_t h;
-                    if ((d & (d - 1)) == 0) {
+                    if (BATCH ? (d & (d - 1)) == 0 : pow2_1) {
                         // 2n a power of two: x = a2 * 2^w / 2n is a shift, and x, y < 2^w <= 2^31
-                        const int sh = (int)ww - ((int)__ffsll((long long)d) - 1);
+                        const int sh = BATCH ? (int)ww - ((int)__ffsll((long long)d) - 1) : sh1;
                         const uint32_t x = sh >= 0 ? a2 << sh : a2 >> -sh;
                         const uint32_t y = sh >= 0 ? b2 << sh : b2 >> -sh;
                         h = 31u - (uint32_t)__clz((int)(x ^ y));
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
                         h = 63u - (uint32_t)__clzll((long long)(x ^ y));
                     }
                     const uint32_t p2 = ww - h;
-                    pk = (p2 + log2k - 1) / log2k;
+                    pk = (p2 + LOG2K - 1) / LOG2K;  // ceil(P_2 / log2 k): the power for fan-in k
                     bits |= 1ull << pk;
                 }
             }
@@ -468,9 +473,16 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
                                                                                                   ws.counters);
         g_launches += 1;
     }
-    k_powers<<<blocks, threads, 0, st>>>(ws.run_starts, ws.counters, n, w, magic, log2k, ws.batch_off, ws.batch_m,
-                                         ws.batch_prm, ws.powers,
-                                          reinterpret_cast<unsigned long long*>(ws.counters + kCtrLevelBits));
+    unsigned long long* bits = reinterpret_cast<unsigned long long*>(ws.counters + kCtrLevelBits);
+#define MPS_POWERS(L2, B)                                                                                             \
+    k_powers<L2, B><<<blocks, threads, 0, st>>>(ws.run_starts, ws.counters, n, w, magic, ws.batch_off, ws.batch_m,  \
+                                                ws.batch_prm, ws.powers, bits)
+    if (ws.batch_off) {
+        if (log2k == 1) MPS_POWERS(1, true); else if (log2k == 2) MPS_POWERS(2, true); else MPS_POWERS(3, true);
+    } else {
+        if (log2k == 1) MPS_POWERS(1, false); else if (log2k == 2) MPS_POWERS(2, false); else MPS_POWERS(3, false);
+    }
+#undef MPS_POWERS
     g_launches += 1;
 }
 

@@ -35,42 +35,54 @@ namespace {
 
 // Two levels of the min-tree at once: dst1[e] = min(src[32e .. 32e+31]) and
 // dst2[e] = min(src[1024e .. 1024e+1023]), each written up to its padded
-// length (a multiple of 32, 255 past the data).  A thread reads 16 source
-// bytes; a block covers 4096 (128 dst1 and 4 dst2 entries).
-__global__ void __launch_bounds__(256) k_mintree(const uint8_t* __restrict__ src, uint32_t src_len, uint8_t* __restrict__ dst1,
-                                                 uint32_t dst1_len, uint8_t* __restrict__ dst2, uint32_t dst2_len) {
+// length (a multiple of 32, 255 past the data).  Source level t holds
+// ceil((r + 1) / 32^t) entries, r read on the device.  A thread reads 16
+// source bytes; a block covers 4096 (128 dst1 and 4 dst2 entries) per step of
+// a grid-stride loop.
+__global__ void __launch_bounds__(256) k_mintree(const uint64_t* __restrict__ ctr, int t, const uint8_t* __restrict__ src,
+                                                 uint8_t* __restrict__ dst1, uint8_t* __restrict__ dst2) {
     __shared__ uint32_t wmin[8];
-    const uint32_t i0 = (blockIdx.x * 256u + threadIdx.x) * 16u;
-    uint32_t m = 255u;
-    if (i0 < src_len) {
-        const uint4 w = *reinterpret_cast<const uint4*>(src + i0);
-        uint32_t x = __vminu4(__vminu4(w.x, w.y), __vminu4(w.z, w.w));
-        if (i0 + 16u > src_len) {  // bytes past the data count as 255
-            const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
-            x = 0xFFFFFFFFu;
-            for (uint32_t q = 0; q < 16u && i0 + q < src_len; q++) {
-                const uint32_t b = (wd[q >> 2] >> (8 * (q & 3))) & 0xFFu;
-                x = __vminu4(x, b * 0x01010101u);
+    uint64_t len = (uint64_t)(uint32_t)ctr[kCtrR] + 1;
+    for (int q = 0; q < t; q++) len = (len + 31) / 32;
+    const uint32_t src_len = (uint32_t)len;
+    const uint32_t dst1_len = (uint32_t)(((len + 31) / 32 + 31) / 32 * 32);
+    const uint32_t dst2_len = (uint32_t)(((len + 1023) / 1024 + 31) / 32 * 32);
+    const uint32_t nblk = (src_len + 4095) / 4096;
+    for (uint32_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        const uint32_t i0 = (blk * 256u + threadIdx.x) * 16u;
+        uint32_t m = 255u;
+        if (i0 < src_len) {
+            const uint4 w = *reinterpret_cast<const uint4*>(src + i0);
+            uint32_t x = __vminu4(__vminu4(w.x, w.y), __vminu4(w.z, w.w));
+            if (i0 + 16u > src_len) {  // bytes past the data count as 255
+                const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+                x = 0xFFFFFFFFu;
+                for (uint32_t q = 0; q < 16u && i0 + q < src_len; q++) {
+                    const uint32_t b = (wd[q >> 2] >> (8 * (q & 3))) & 0xFFu;
+                    x = __vminu4(x, b * 0x01010101u);
+                }
             }
+            x = __vminu4(x, x >> 16);
+            x = __vminu4(x, x >> 8);
+            m = x & 0xFFu;
         }
-        x = __vminu4(x, x >> 16);
-        x = __vminu4(x, x >> 8);
-        m = x & 0xFFu;
+        const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+        const uint32_t m1 = min(m, __shfl_xor_sync(0xffffffffu, m, 1));  // 32 source bytes
+        const uint32_t e1 = (blk * 256u + threadIdx.x) >> 1;
+        if (!(lane & 1u) && e1 < dst1_len) dst1[e1] = (uint8_t)m1;
+        if (dst2 != nullptr) {
+            const uint32_t wm = __reduce_min_sync(0xffffffffu, m1);  // 512 source bytes
+            if (lane == 0) wmin[warp] = wm;
+            __syncthreads();
+            if (threadIdx.x < 4) {
+                const uint32_t e2 = blk * 4u + threadIdx.x;
+                if (e2 < dst2_len) dst2[e2] = (uint8_t)min(wmin[2 * threadIdx.x], wmin[2 * threadIdx.x + 1]);
+            }
+            __syncthreads();
+        }
     }
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t m1 = min(m, __shfl_xor_sync(0xffffffffu, m, 1));  // 32 source bytes
-    const uint32_t e1 = (blockIdx.x * 256u + threadIdx.x) >> 1;
-    if (!(lane & 1u) && e1 < dst1_len) dst1[e1] = (uint8_t)m1;
-    if (dst2 == nullptr) return;
-    const uint32_t wm = __reduce_min_sync(0xffffffffu, m1);  // 512 source bytes
-    if (lane == 0) wmin[warp] = wm;
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        const uint32_t e2 = blockIdx.x * 4u + threadIdx.x;
-        if (e2 < dst2_len) dst2[e2] = (uint8_t)min(wmin[2 * threadIdx.x], wmin[2 * threadIdx.x + 1]);
-    }
-    if (blockIdx.x == 0)
-        for (uint32_t q = gridDim.x * 4u + threadIdx.x; q < dst2_len; q += 256u) dst2[q] = 255;
+    if (dst2 != nullptr && blockIdx.x == 0)
+        for (uint32_t q = nblk * 4u + threadIdx.x; q < dst2_len; q += 256u) dst2[q] = 255;
 }
 
 struct MinTree {
@@ -185,7 +197,9 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask_reduce(const uint8_t* __r
     __shared__ unsigned long long tmp[kMaskThreads / 32 + 1];
     const uint32_t r = (uint32_t)ctr[kCtrR];
     const uint32_t nb = r - 1;
-    const uint32_t b0 = blockIdx.x * kMaskTile + threadIdx.x * kMaskItems;
+    const uint32_t tiles = (uint32_t)ceil_div(max(nb, 1u), kMaskTile);
+    for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const uint32_t b0 = tile * kMaskTile + threadIdx.x * kMaskItems;
     unsigned long long f = kMaskIdentity, g = kMaskIdentity;
     if (b0 < nb) {
         // powers[b0 .. b0+31] (padded past r); boundary b is j = b + 1
@@ -203,15 +217,18 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask_reduce(const uint8_t* __r
     }
     unsigned long long tot;
     block_scan_excl<kMaskThreads, false>(f, OpF(), kMaskIdentity, tmp, &tot);
-    if (threadIdx.x == 0) tf[blockIdx.x] = tot;
+    if (threadIdx.x == 0) tf[tile] = tot;
     block_scan_excl<kMaskThreads, false>(g, OpG(), kMaskIdentity, tmp, &tot);
-    if (threadIdx.x == 0) tg[blockIdx.x] = tot;
+    if (threadIdx.x == 0) tg[tile] = tot;
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_mask_scan(const unsigned long long* __restrict__ tf, const unsigned long long* __restrict__ tg,
-                                                    uint32_t tiles, unsigned long long* __restrict__ fpre,
+                                                    const uint64_t* __restrict__ ctr, unsigned long long* __restrict__ fpre,
                                                     unsigned long long* __restrict__ gsuf) {
     __shared__ unsigned long long tmp[1024 / 32 + 1];
+    const uint32_t nb = (uint32_t)ctr[kCtrR] - 1;
+    const uint32_t tiles = (uint32_t)ceil_div(max(nb, 1u), kMaskTile);
     uint32_t per = (tiles + 1023) / 1024;
     uint32_t b = threadIdx.x * per, e = min(tiles, b + per);
     unsigned long long f = kMaskIdentity, g = kMaskIdentity;
@@ -271,7 +288,9 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_mask_apply(const uint8_t* _
     __shared__ unsigned long long tmp[kMaskThreads / 32 + 1];
     const uint32_t r = (uint32_t)ctr[kCtrR];
     const uint32_t nb = r - 1;
-    const uint32_t b0 = blockIdx.x * kMaskTile + threadIdx.x * kMaskItems;
+    const uint32_t tiles = (uint32_t)ceil_div(max(nb, 1u), kMaskTile);
+    for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const uint32_t b0 = tile * kMaskTile + threadIdx.x * kMaskItems;
     const bool live = b0 < nb;
     const uint32_t vskip = small_power(n_single ? n_single : ctr[kCtrMaxLen], ctr[kCtrMaxRun], log2k, tmax);
     // powers[b0 .. b0+31] and rs[b0 .. b0+19] (both arrays are padded past r)
@@ -306,8 +325,8 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_mask_apply(const uint8_t* _
     }
     unsigned long long pf = block_scan_excl<kMaskThreads, false>(f, OpF(), kMaskIdentity, tmp, nullptr);
     unsigned long long sg = block_scan_excl<kMaskThreads, true>(g, OpGRev(), kMaskIdentity, tmp, nullptr);
-    pf = OpF()(fpre[blockIdx.x], pf);
-    sg = OpG()(sg, gsuf[blockIdx.x]);
+    pf = OpF()(fpre[tile], pf);
+    sg = OpG()(sg, gsuf[tile]);
     // bit sets of the right-side summaries per item (right to left)
     uint32_t rb[kMaskItems];
     uint32_t d0 = 0;  // depth of run 0 (thread holding boundary 1 only)
@@ -408,6 +427,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_mask_apply(const uint8_t* _
         if (cost) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrM), cost);
         if (nodes) atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrNodes), nodes);
     }
+    }
 }
 
 // ------------------------------------------------------------- node pass
@@ -442,7 +462,7 @@ __device__ __forceinline__ bool node_shape(const MinTree& T, const uint8_t* P, u
 // child that is an inner node of at most T_max elements to the list of fused
 // subtrees (its parent is large, so it is maximal); a small root is a fused
 // subtree too.
-__global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tmax,
+__global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tmax, uint32_t vmax,
                                                    const uint32_t* __restrict__ rs, const uint8_t* __restrict__ node_info,
                                                    uint64_t* __restrict__ ctr, LevelNode* __restrict__ nodes_raw, uint32_t nodes_cap,
                                                    uint4* __restrict__ fused_list, uint32_t fused_cap,
@@ -470,6 +490,9 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tm
             const uint32_t sL = rs[L], sR = rs[R];
             const uint32_t size = sR - sL;
             if (size > tmax) {
+                // level merges are queued for powers 1..vmax only (a node of
+                // power v is smaller than 3 n / k^(v-1)); anything else is a bug
+                if (v > vmax) dev_fail(status, kDevLevelBound);
                 NodeShape s;
                 if (!node_shape(T, P, j, v, k, s)) dev_fail(status, kDevDegree);
                 uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmTotal), 1ull);
@@ -555,9 +578,11 @@ __global__ void k_level_offsets(uint64_t* __restrict__ ctr, uint32_t* __restrict
 // ------------------------------------------------------------- tree dump
 
 // node_first for every boundary; canonical rank is computed by k_dump_rank.
-__global__ void __launch_bounds__(256) k_dump_node_first(MinTree T, uint32_t r, const uint8_t* __restrict__ node_info,
+__global__ void __launch_bounds__(256) k_dump_node_first(MinTree T, const uint64_t* __restrict__ ctr,
+                                                         const uint8_t* __restrict__ node_info,
                                                          uint32_t* __restrict__ node_first) {
     const uint8_t* P = T.lv[0];
+    const uint32_t r = (uint32_t)ctr[kCtrR];
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j == 0) node_first[0] = 0;
     if (j == 0 || j >= r) return;
@@ -571,8 +596,9 @@ __global__ void __launch_bounds__(256) k_dump_node_first(MinTree T, uint32_t r, 
 }
 
 // Per-tile histograms of node-start powers (tile = kMaskTile boundaries).
-__global__ void __launch_bounds__(256) k_dump_hist(const uint8_t* __restrict__ P, const uint8_t* __restrict__ node_info, uint32_t r,
-                                                   uint32_t* __restrict__ hist) {
+__global__ void __launch_bounds__(256) k_dump_hist(const uint8_t* __restrict__ P, const uint8_t* __restrict__ node_info,
+                                                   const uint64_t* __restrict__ ctr, uint32_t* __restrict__ hist) {
+    const uint32_t r = (uint32_t)ctr[kCtrR];
     __shared__ uint32_t h[kMaxLevels];
     if (threadIdx.x < kMaxLevels) h[threadIdx.x] = 0;
     __syncthreads();
@@ -608,8 +634,10 @@ __global__ void __launch_bounds__(1024) k_dump_hist_scan(uint32_t* __restrict__ 
 
 // Canonical rank of every node start: starts of power p in boundary order.
 // Within a tile, a warp walks its boundaries in order with ballots.
-__global__ void __launch_bounds__(256) k_dump_rank(const uint8_t* __restrict__ P, const uint8_t* __restrict__ node_info, uint32_t r,
-                                                   const uint32_t* __restrict__ hist, uint32_t* __restrict__ canon_idx) {
+__global__ void __launch_bounds__(256) k_dump_rank(const uint8_t* __restrict__ P, const uint8_t* __restrict__ node_info,
+                                                   const uint64_t* __restrict__ ctr, const uint32_t* __restrict__ hist,
+                                                   uint32_t* __restrict__ canon_idx) {
+    const uint32_t r = (uint32_t)ctr[kCtrR];
     __shared__ uint32_t run[kMaxLevels];
     if (threadIdx.x < kMaxLevels) run[threadIdx.x] = hist[(size_t)blockIdx.x * kMaxLevels + threadIdx.x];
     __syncthreads();
@@ -634,11 +662,12 @@ __global__ void __launch_bounds__(256) k_dump_rank(const uint8_t* __restrict__ P
     }
 }
 
-__global__ void __launch_bounds__(256) k_dump_nodes(MinTree T, uint32_t r, int k, const uint32_t* __restrict__ rs,
+__global__ void __launch_bounds__(256) k_dump_nodes(MinTree T, const uint64_t* __restrict__ ctr, int k, const uint32_t* __restrict__ rs,
                                                     const uint8_t* __restrict__ node_info, const uint32_t* __restrict__ canon_idx,
                                                     const uint32_t* __restrict__ node_first, uint32_t* __restrict__ out_nodes,
                                                     uint32_t* __restrict__ status) {
     const uint8_t* P = T.lv[0];
+    const uint32_t r = (uint32_t)ctr[kCtrR];
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x + 1;
     if (j >= r || !(node_info[j - 1] & 0x80)) return;
     uint32_t v = P[j];
@@ -658,45 +687,71 @@ __global__ void __launch_bounds__(256) k_dump_nodes(MinTree T, uint32_t r, int k
     o[3] = parent;
 }
 
+// Copies the run structure of a sort to the caller's tree arrays (r read on
+// the device): run_starts[0..r], run_desc[0..r), powers[0..r], and, for an
+// input of one run (no boundary, so no depth written by the depth scan),
+// leaf_depth[0] = 0; block 0 writes counts = {r, nodes, distinct powers, M}.
+__global__ void __launch_bounds__(256) k_tree_arrays(const uint64_t* __restrict__ ctr, const uint32_t* __restrict__ rs,
+                                                     const uint8_t* __restrict__ rdesc, const uint8_t* __restrict__ P,
+                                                     uint32_t* __restrict__ o_rs, uint8_t* __restrict__ o_rd,
+                                                     uint8_t* __restrict__ o_p, uint8_t* __restrict__ o_leaf,
+                                                     uint64_t* __restrict__ o_counts) {
+    const uint32_t r = (uint32_t)ctr[kCtrR];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= r; i += gridDim.x * blockDim.x) {
+        if (o_rs) o_rs[i] = rs[i];
+        if (o_rd && i < r) o_rd[i] = rdesc[i];
+        if (o_p) o_p[i] = P[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (o_leaf && r == 1) o_leaf[0] = 0;
+        if (o_counts) {
+            o_counts[0] = r;
+            o_counts[1] = ctr[kCtrNodes];
+            o_counts[2] = (uint64_t)__popcll((long long)ctr[kCtrLevelBits]);
+            o_counts[3] = ctr[kCtrM];
+        }
+    }
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------- launchers
 
-void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st) {
-    // level t has ws.lv_len[t] valid entries; padding of 255 up to a multiple of 32
+void launch_mintree(uint32_t r_bound, const WsView& ws, cudaStream_t st) {
+    // ws.nlv levels for up to r_bound runs; each kernel sizes its levels from r
     for (int t = 0; t + 1 < ws.nlv; t += 2) {
-        const uint32_t src_len = ws.lv_len[t];
-        const uint32_t blocks = (src_len + 4095) / 4096;
-        const uint32_t len1 = (uint32_t)((ceil_div(src_len, 32) + 31) / 32 * 32);
-        const uint32_t len2 = (uint32_t)((ceil_div(src_len, 1024) + 31) / 32 * 32);
+        const uint32_t src_bound = ws.lv_len[t];
+        const uint32_t blocks = (uint32_t)std::min<uint64_t>((src_bound + 4095) / 4096, 152 * 8);
         uint8_t* dst2 = (t + 2 < ws.nlv) ? ws.lv[t + 2] : nullptr;
-        k_mintree<<<blocks, 256, 0, st>>>(ws.lv[t], src_len, ws.lv[t + 1], len1, dst2, len2);
+        k_mintree<<<blocks, 256, 0, st>>>(ws.counters, t, ws.lv[t], ws.lv[t + 1], dst2);
         g_launches += 1;
     }
 }
 
-void launch_masks(uint32_t r, bool dump_leaf, uint8_t* leaf_depth, uint64_t n, int k, uint32_t tmax, const WsView& ws,
+void launch_masks(uint32_t r_bound, bool dump_leaf, uint8_t* leaf_depth, uint64_t n, int k, uint32_t tmax, const WsView& ws,
                   cudaStream_t st) {
-    uint32_t nb = r - 1;
-    uint32_t tiles = (uint32_t)ceil_div(nb, kMaskTile);
-    k_mask_reduce<<<tiles, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.mt_f, ws.mt_g);
-    k_mask_scan<<<1, 1024, 0, st>>>(ws.mt_f, ws.mt_g, tiles, ws.mt_fpre, ws.mt_gsuf);
+    // tiles of kMaskTile boundaries for up to r_bound runs; the kernels loop over the tiles of the actual r
+    const uint32_t nb = r_bound > 1 ? r_bound - 1 : 1;
+    const uint32_t tiles = (uint32_t)ceil_div(nb, kMaskTile);
+    const uint32_t grid = std::min<uint32_t>(tiles, 152 * 32);
+    k_mask_reduce<<<grid, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.mt_f, ws.mt_g);
+    k_mask_scan<<<1, 1024, 0, st>>>(ws.mt_f, ws.mt_g, ws.counters, ws.mt_fpre, ws.mt_gsuf);
     const uint32_t log2k = k == 2 ? 1u : (k == 4 ? 2u : 3u);
     if (ws.batch_cost)
-        k_mask_apply<true><<<tiles, kMaskThreads, 0, st>>>(
+        k_mask_apply<true><<<grid, kMaskThreads, 0, st>>>(
             ws.powers, ws.counters, ws.run_starts, ws.mt_fpre, ws.mt_gsuf, ws.node_info, dump_leaf ? leaf_depth : nullptr,
             0ull, log2k, tmax, ws.canon_idx, ws.cand_cap, ws.batch_off, ws.batch_m,
             reinterpret_cast<unsigned long long*>(ws.batch_cost));
     else
-        k_mask_apply<false><<<tiles, kMaskThreads, 0, st>>>(
+        k_mask_apply<false><<<grid, kMaskThreads, 0, st>>>(
             ws.powers, ws.counters, ws.run_starts, ws.mt_fpre, ws.mt_gsuf, ws.node_info, dump_leaf ? leaf_depth : nullptr,
             ws.batch_off ? 0ull : n, log2k, tmax, ws.canon_idx, ws.cand_cap, nullptr, 0u, nullptr);
     g_launches += 3;
 }
 
-void launch_node_pass(uint32_t r, int k, uint32_t tmax, const WsView& ws, cudaStream_t st) {
+void launch_node_pass(uint32_t r, int k, uint32_t tmax, uint32_t vmax, const WsView& ws, cudaStream_t st) {
     (void)r;
-    k_node_pass<<<152 * 4, 256, 0, st>>>(make_mintree(ws), k, tmax, ws.run_starts, ws.node_info, ws.counters, ws.nodes_raw,
+    k_node_pass<<<152 * 4, 256, 0, st>>>(make_mintree(ws), k, tmax, vmax, ws.run_starts, ws.node_info, ws.counters, ws.nodes_raw,
                                          ws.nodes_cap, ws.fused_list, ws.fused_cap, ws.canon_idx, ws.cand_cap);
     g_launches += 1;
 }
@@ -708,21 +763,28 @@ void launch_bucket(uint32_t total_bound, const WsView& ws, cudaStream_t st) {
     g_launches += 2;
 }
 
-void launch_tree_dump(uint32_t r, int k, const WsView& ws, uint32_t* node_first, void* nodes, uint64_t* counts_out,
-                      cudaStream_t st) {
-    (void)counts_out;
-    uint32_t nb = r - 1;
-    uint32_t tiles = (uint32_t)ceil_div(nb, kMaskTile);
+void launch_tree_dump(uint32_t r_bound, int k, const WsView& ws, uint32_t* node_first, void* nodes, cudaStream_t st) {
+    const uint32_t nb = r_bound > 0 ? r_bound - 1 : 0;
+    const uint32_t tiles = (uint32_t)std::max<uint64_t>(1, ceil_div(nb, kMaskTile));
     MinTree T = make_mintree(ws);
-    k_dump_node_first<<<(uint32_t)ceil_div(r, 256), 256, 0, st>>>(T, r, ws.node_info, node_first);
-    k_dump_hist<<<tiles, 256, 0, st>>>(ws.powers, ws.node_info, r, ws.hist);
+    k_dump_node_first<<<(uint32_t)ceil_div(std::max<uint32_t>(r_bound, 1), 256), 256, 0, st>>>(T, ws.counters, ws.node_info,
+                                                                                                 node_first);
+    k_dump_hist<<<tiles, 256, 0, st>>>(ws.powers, ws.node_info, ws.counters, ws.hist);
     k_dump_hist_scan<<<1, 1024, 0, st>>>(ws.hist, tiles);
-    k_dump_rank<<<tiles, 256, 0, st>>>(ws.powers, ws.node_info, r, ws.hist, ws.canon_idx);
+    k_dump_rank<<<tiles, 256, 0, st>>>(ws.powers, ws.node_info, ws.counters, ws.hist, ws.canon_idx);
     if (nodes)
-        k_dump_nodes<<<(uint32_t)ceil_div(nb, 256), 256, 0, st>>>(T, r, k, ws.run_starts, ws.node_info, ws.canon_idx, node_first,
-                                                                   reinterpret_cast<uint32_t*>(nodes),
-                                                                   reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
+        k_dump_nodes<<<(uint32_t)std::max<uint64_t>(1, ceil_div(nb, 256)), 256, 0, st>>>(
+            T, ws.counters, k, ws.run_starts, ws.node_info, ws.canon_idx, node_first, reinterpret_cast<uint32_t*>(nodes),
+            reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
     g_launches += nodes ? 5 : 4;
+}
+
+void launch_tree_arrays(uint32_t r_bound, const WsView& ws, uint32_t* run_starts, uint8_t* run_desc, uint8_t* powers,
+                        uint8_t* leaf_depth, uint64_t* counts, cudaStream_t st) {
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r_bound + 1, 256), 152 * 8);
+    k_tree_arrays<<<blocks, 256, 0, st>>>(ws.counters, ws.run_starts, ws.run_desc, ws.powers, run_starts, run_desc, powers,
+                                          leaf_depth, counts);
+    g_launches += 1;
 }
 
 }  // namespace mps

@@ -74,7 +74,7 @@ EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_t
            "mps_batch_workspace_size", "mps_sort_batch", "mps_sort_batch_pairs", "mps_batch_autotune",
            "mps_batch_graph_create", "mps_batch_graph_launch", "mps_batch_graph_destroy",
            "mps_queue_create", "mps_queue_submit", "mps_queue_poll", "mps_queue_wait", "mps_queue_pause",
-           "mps_queue_destroy", "mps_records_workspace_size", "mps_sort_records"]
+           "mps_queue_destroy", "mps_records_workspace_size", "mps_sort_records", "mps_sync_status"]
 
 # Largest n accepted by mps_sort_keys_noalloc (its scratch is compiled into the library).
 NOALLOC_MAX_N = 1 << 20
@@ -101,6 +101,8 @@ def lib():
     L.mps_profile_read.argtypes = [P, I]
     L.mps_profile_read.restype = I
     L.mps_last_stats.argtypes = [P]
+    L.mps_sync_status.argtypes = [P, P]
+    L.mps_sync_status.restype = I
     L.mps_sort_keys_noalloc.argtypes = [P, P, U64, I, I, P]
     L.mps_sort_keys_noalloc.restype = I
     U32 = ctypes.c_uint32
@@ -454,3 +456,9 @@ def to_device(a: np.ndarray, device="cuda") -> torch.Tensor:
 def to_numpy(t: torch.Tensor, dtype) -> np.ndarray:
     """Device tensor -> numpy array of the given unsigned dtype (same bits)."""
     return t.cpu().numpy().view(dtype)
+
+
+def sync_status(ws: torch.Tensor, stream=None) -> None:
+    """Waits for the stream and raises if the last sort on this workspace
+    reported a device-side failure (mps_sync_status)."""
+    _check("mps_sync_status", lib().mps_sync_status(ws.data_ptr(), _stream(stream)))

@@ -170,6 +170,41 @@ def test_argument_errors():
     with pytest.raises(mps.MpsError) as e:
         mps.sort_keys(a, k=4, ws=ws)
     assert e.value.code == 3
+    v = torch.empty(1000, dtype=torch.int32, device=DEV)
     with pytest.raises(mps.MpsError) as e:
-        mps.sort_keys(a, k=4, out=a)  # output overlapping the input
+        mps.sort_pairs(a, v, k=4, out_keys=a, out_vals=a)  # keys and payloads in the same memory
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("k", [2, 4, 8])
+def test_sort_in_place(k):
+    """d_keys_out == d_keys_in (and payloads in place): the same result as the oracle."""
+    a = inputs.random_runs_uniform_len(300001, seed=21 + k, hi=2000)
+    d = mps.to_device(a, DEV)
+    mps.sort_keys(d, k=k, out=d)
+    torch.cuda.synchronize()
+    assert np.array_equal(mps.to_numpy(d, np.uint32), oracle.sort(a, k=k)["keys"])
+    b = inputs.random_runs_loguniform(200003, seed=5, log2_hi=12.0, distinct=1024, dtype=np.uint64)
+    v = inputs.payload_index(b.size)
+    want = oracle.sort(b, v, k=k, want_tree=False)
+    dk, dv = mps.to_device(b, DEV), mps.to_device(v, DEV)
+    mps.sort_pairs(dk, dv, k=k, out_keys=dk, out_vals=dv)
+    torch.cuda.synchronize()
+    assert np.array_equal(mps.to_numpy(dk, np.uint64), want["keys"])
+    assert np.array_equal(mps.to_numpy(dv, np.uint32), want["vals"])
+
+
+def test_calls_queue_without_waiting():
+    """Several sorts queued back to back on one stream and one workspace, then
+    one synchronisation: each output is right, and the status word is clear."""
+    ws = mps.workspace(400000, 4, False, 4, DEV)
+    arrays = [inputs.random_permutation(400000, seed=s) for s in (1, 2)] + \
+             [inputs.random_runs_geometric(399999, seed=3, mean=50.0)]
+    outs = []
+    for a in arrays:
+        outs.append(mps.sort_keys(mps.to_device(a, DEV), k=4, ws=ws))
+    mps.sync_status(ws)
+    for a, o in zip(arrays, outs):
+        assert np.array_equal(mps.to_numpy(o, np.uint32), np.sort(a))
+    st = mps.last_stats()
+    assert st["device_status"] == 0 and st["r"] == oracle.find_runs(arrays[-1])[0].size - 1
