@@ -306,6 +306,11 @@ void worker_main(mps_queue* q) {
                 q->tickets[id].t_admit = now;
             }
             if (s != MPS_OK) {
+                // part of the batch may already be queued (the offsets copy,
+                // the gather, some sort kernels): let the stream drain before
+                // its pool blocks and pinned offsets are reused, and before the
+                // callers learn the result and may free their buffers
+                cudaStreamSynchronize(q->streams[sidx]);
                 release_batch(q, B);
                 finish_tickets(q, ids, s);
                 q->cv_done.notify_all();
