@@ -489,3 +489,53 @@ def test_min_run_len_equal_runs_give_the_complete_tree(k, h):
             t += 1
         return t
     assert [int(p) for p in res["powers"][1:r]] == [h - vk(i) for i in range(1, r)]
+
+
+def _powers_exact(lengths, k):
+    """Def. 3.1 with exact rationals: the power of the boundary between
+    consecutive runs, from the runs' normalised midpoints."""
+    n = sum(lengths)
+    s = [0]
+    for x in lengths:
+        s.append(s[-1] + x)
+    out = []
+    for i in range(1, len(lengths)):
+        a = Fraction(s[i - 1] + s[i], 2 * n)
+        b = Fraction(s[i] + s[i + 1], 2 * n)
+        p = 0
+        while math.floor(a * k ** p) == math.floor(b * k ** p):
+            p += 1
+        out.append(p)
+    return out
+
+
+# Final-collapse pins written out by hand (k = 4).  Every input has weakly
+# increasing powers, so Alg. 2's main loop merges nothing and the whole run
+# stack is left to the final collapse; the merge sequences are spelled out in
+# the comments (M = sum of merge result sizes, Sec. 2.2).
+TAIL_CASES = [
+    # L = 1 2 2 2 | 1, powers 1 1 1 2: stack [1 2 2 2], current 1.
+    #  kway_tree: {2}+1 = 3, then {1 2 2}+3 = 8             -> 11
+    #  pop k-1:   {2 2 2}+1 = 7, then {1}+7 = 8             -> 15
+    #  merge_down: x = 4 mod 3 = 1: {2}+1 = 3, {2 2 1}+3 = 8 -> 11
+    ((1, 2, 2, 2, 1), [1, 1, 1, 2], {"kway_tree": 11, "alg2_pop_k_minus_1": 15, "merge_down": 11}),
+    # L = 1 3 3 1 1 | 1, powers 1 1 1 2 2: stack [1 3 3 1 1], current 1.
+    #  kway_tree: {1 1}+1 = 3, then {1 3 3}+3 = 10            -> 13
+    #  pop k-1:   {1 1 3}+1 = 6, then {3 1}+6 = 10            -> 16
+    #  merge_down: x = 5 mod 3 = 2: {1 1}+1 = 3, {3 3 1}+3 = 10 -> 13
+    ((1, 3, 3, 1, 1, 1), [1, 1, 1, 2, 2], {"kway_tree": 13, "alg2_pop_k_minus_1": 16, "merge_down": 13}),
+    # L = 10 1 1 1 | 1, powers 1 2 2 2: stack [10 1 1 1], current 1.
+    #  kway_tree: {1 1 1}+1 = 4, then {10}+4 = 14             -> 18
+    #  pop k-1:   {1 1 1}+1 = 4, then {10}+4 = 14             -> 18
+    #  merge_down: x = 4 mod 3 = 1: {1}+1 = 2, {1 1 10}+2 = 14 -> 16
+    ((10, 1, 1, 1, 1), [1, 2, 2, 2], {"kway_tree": 18, "alg2_pop_k_minus_1": 18, "merge_down": 16}),
+]
+
+
+@pytest.mark.parametrize("lengths,pw,want", TAIL_CASES)
+def test_tail_policies_hand_derived(lengths, pw, want):
+    assert _powers_exact(list(lengths), 4) == pw
+    for policy, m in want.items():
+        assert oracle.merge_cost_tail(list(lengths), 4, policy) == m, policy
+    # the KwayTree tail is Alg. 1's tree: its merge cost from the canonical tree
+    assert oracle.tree_from_lengths(np.array(lengths), 4)["merge_cost"] == want["kway_tree"]
