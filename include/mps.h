@@ -119,6 +119,26 @@ mps_status mps_sort_pairs(const void* d_keys_in, const uint32_t* d_vals_in, void
                           uint32_t* d_vals_out, uint64_t n, mps_key_type kt, int k,
                           void* d_ws, size_t ws_bytes, const mps_tree* opt_tree, cudaStream_t stream);
 
+/* Multiway Powersort with a minimum run length (Sec. 5, "Minimal run
+ * length": the paper's experiments extend runs to 24 elements).  Runs are
+ * found greedily from the left as in mps_sort_keys, except that a natural run
+ * shorter than min_run_len is extended to min_run_len elements (or to the end
+ * of the array) and sorted stably; the next run is searched from the end of
+ * the extended one.  Powers, tree and merges then follow Def. 3.1 and Alg. 1
+ * on these runs.  min_run_len = 1 is mps_sort_keys; 2..32 are supported
+ * (MPS_ERR_UNSUPPORTED otherwise).  opt_tree->run_desc flags the runs whose
+ * natural part was strictly decreasing.  Workspace:
+ * mps_workspace_size_minrun(n, kt, has_payload, k, min_run_len). */
+mps_status mps_workspace_size_minrun(uint64_t n, mps_key_type kt, int has_payload, int k, uint32_t min_run_len,
+                                     size_t* bytes);
+mps_status mps_sort_keys_minrun(const void* d_keys_in, void* d_keys_out, uint64_t n, mps_key_type kt, int k,
+                                uint32_t min_run_len, void* d_ws, size_t ws_bytes, const mps_tree* opt_tree,
+                                cudaStream_t stream);
+/* Stable key-value form of mps_sort_keys_minrun. */
+mps_status mps_sort_pairs_minrun(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out,
+                                 uint32_t* d_vals_out, uint64_t n, mps_key_type kt, int k, uint32_t min_run_len,
+                                 void* d_ws, size_t ws_bytes, const mps_tree* opt_tree, cudaStream_t stream);
+
 /* Records (Sec. 5, "records" experiment: a long key and a pointer, 16 bytes):
  * stable sort of n keys each carrying a 64-bit payload.  The keys are sorted
  * with their input indices as uint32 payloads (as mps_sort_pairs), and every

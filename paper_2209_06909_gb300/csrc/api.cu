@@ -35,6 +35,7 @@ thread_local uint64_t g_launches = 0;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr uint32_t kMaxMinRun = 32;  // forced runs are sorted by one warp each
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -59,8 +60,12 @@ struct Plan {
 
     uint32_t m = 0;  // arrays of a batch (0: a single array)
     size_t o_bprm = 0;
+    // minimum run length (1: natural runs) and its buffers
+    uint32_t min_run = 1, mr_cap = 0, mr_tiles = 0;
+    size_t o_mr_g = 0, o_mr_node = 0, o_mr_tiles = 0, o_mr_desc = 0;
 
-    explicit Plan(uint64_t n_, int kb_, bool vals_, int k_, uint32_t m_ = 0) : n(n_), kb(kb_), vals(vals_), k(k_), m(m_) {
+    explicit Plan(uint64_t n_, int kb_, bool vals_, int k_, uint32_t m_ = 0, uint32_t min_run_ = 1)
+        : n(n_), kb(kb_), vals(vals_), k(k_), m(m_), min_run(min_run_) {
         g = merge_geom(kb, vals, k);
         rmax = n / 2 + m + 2;
         det_tiles = ceil_div(std::max<uint64_t>(n, 1), kDetTile);
@@ -105,7 +110,40 @@ struct Plan {
         // a single array may be sorted into the memory it is read from: room for a copy of the input
         o_incopy = m == 0 ? take(n * kb) : o;
         if (m == 0 && vals) take(n * 4);
+        if (min_run > 1) {
+            // good intervals: natural runs with >= min_run - 1 interior flags, at most n / (min_run - 1) + 1
+            mr_cap = (uint32_t)(n / (min_run - 1) + 2);
+            mr_tiles = (uint32_t)(ceil_div(std::max<uint64_t>(rmax, (uint64_t)mr_cap + 2), 4096) + 2);
+            o_mr_g = take((size_t)3 * mr_cap * 4);
+            o_mr_node = take((size_t)7 * (mr_cap + 2) * 4);
+            o_mr_tiles = take((size_t)mr_tiles * 4);
+            o_mr_desc = take(rmax + 1);
+        }
         total = o;
+    }
+
+    MinRunView min_run_view(void* base) const {
+        char* b = static_cast<char*>(base);
+        MinRunView v{};
+        v.m = min_run;
+        v.cap = mr_cap;
+        uint32_t* g = reinterpret_cast<uint32_t*>(b + o_mr_g);
+        v.gs = g;
+        v.ge = g + mr_cap;
+        v.gv = g + 2 * (size_t)mr_cap;
+        uint32_t* nd = reinterpret_cast<uint32_t*>(b + o_mr_node);
+        const size_t nn = (size_t)mr_cap + 2;
+        v.succ = nd;
+        v.hit = nd + nn;
+        v.cnt = nd + 2 * nn;
+        v.off = nd + 3 * nn;
+        v.mark = nd + 4 * nn;
+        v.jmp0 = nd + 5 * nn;
+        v.jmp1 = nd + 6 * nn;
+        v.tiles = reinterpret_cast<uint32_t*>(b + o_mr_tiles);
+        v.tiles_cap = mr_tiles;
+        v.desc_nat = reinterpret_cast<uint8_t*>(b + o_mr_desc);
+        return v;
     }
 
     WsView view(void* base) const {
@@ -356,8 +394,10 @@ int level_power_bound(uint64_t max_len, int k, uint32_t tmax) {
 // the bound for n; a level without nodes costs its launches and nothing else.
 template <typename K, bool V>
 mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, uint64_t n, int k,
-                     void* d_ws, size_t ws_bytes, const mps_tree* tree, bool move_keys, cudaStream_t st) {
+                     void* d_ws, size_t ws_bytes, const mps_tree* tree, bool move_keys, cudaStream_t st,
+                     uint32_t min_run = 1) {
     if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (min_run < 1 || min_run > kMaxMinRun) return MPS_ERR_UNSUPPORTED;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
     const double b = (double)sizeof(K) + (V ? 4.0 : 0.0);
     g_launches = 0;
@@ -377,18 +417,21 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
         (overlaps(keys_in, kbytes, vals_out, vbytes) || overlaps(vals_in, vbytes, keys_out, kbytes) ||
          overlaps(keys_out, kbytes, vals_out, vbytes)))
         return MPS_ERR_INVALID_ARG;
-    Plan plan(n, sizeof(K), V, k);
+    Plan plan(n, sizeof(K), V, k, 0, min_run);
     if (ws_bytes < plan.total) return MPS_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(d_ws) % 16) return MPS_ERR_INVALID_ARG;
     WsView ws = plan.view(d_ws);
     const MergeGeom& g = plan.g;
     const size_t mark = prof_mark();
+    const K* keys_orig = keys_in;
 
     MPS_CUDA(cudaMemsetAsync(ws.counters, 0, kCtrWords * 8, st));
     // The merges read leaves from the input while node outputs land in
     // keys_out, so an output that overlaps its input sorts a copy of the input
     // (kept in the workspace).
-    if (move_keys && (overlaps(keys_in, kbytes, keys_out, kbytes) || (V && overlaps(vals_in, vbytes, vals_out, vbytes)))) {
+    // A minimum run length sorts its short runs in the same copy.
+    if (min_run > 1 ||
+        (move_keys && (overlaps(keys_in, kbytes, keys_out, kbytes) || (V && overlaps(vals_in, vbytes, vals_out, vbytes))))) {
         K* kc = reinterpret_cast<K*>(static_cast<char*>(d_ws) + plan.o_incopy);
         MPS_CUDA(cudaMemcpyAsync(kc, keys_in, kbytes, cudaMemcpyDeviceToDevice, st));
         keys_in = kc;
@@ -402,7 +445,13 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     set_levels(ws, r_bound);
     {
         ProfScope ps("detect_runs", (double)kbytes, st);
-        launch_detect<K>(keys_in, n, ws, st);
+        launch_detect<K>(keys_orig, n, ws, st);
+    }
+    if (min_run > 1) {
+        // natural runs -> runs of at least min_run elements, the short ones sorted in the copy
+        ProfScope ps("min_run", 2.0 * (double)kbytes, st);
+        launch_min_run<K, V>(keys_orig, const_cast<K*>(keys_in), const_cast<uint32_t*>(vals_in), n,
+                             plan.min_run_view(d_ws), ws, st);
     }
     if (move_keys) {
         ProfScope ps("copy_single_run", 0.0, st);
@@ -441,7 +490,8 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     }
     if (tree) {
         if (tree->run_starts || tree->run_desc || tree->powers || tree->leaf_depth || tree->counts)
-            launch_tree_arrays(r_bound, ws, tree->run_starts, tree->run_desc, tree->powers, tree->leaf_depth, tree->counts, st);
+            launch_tree_arrays(r_bound, ws, min_run > 1 ? plan.min_run_view(d_ws).desc_nat : ws.run_desc, tree->run_starts,
+                               tree->run_desc, tree->powers, tree->leaf_depth, tree->counts, st);
         if (tree->node_first) launch_tree_dump(r_bound, k, ws, tree->node_first, tree->nodes, st);
     }
     MPS_CUDA(cudaGetLastError());
@@ -566,6 +616,41 @@ mps_status mps_merge_tree(const void* d_keys, uint64_t n, mps_key_type kt, int k
     if (kt == MPS_U64)
         return sort_impl<uint64_t, false>((const uint64_t*)d_keys, nullptr, nullptr, nullptr, n, k, d_ws, ws_bytes, out, false,
                                           stream);
+    return MPS_ERR_INVALID_ARG;
+}
+
+mps_status mps_workspace_size_minrun(uint64_t n, mps_key_type kt, int has_payload, int k, uint32_t min_run_len,
+                                     size_t* bytes) {
+    if (!bytes) return MPS_ERR_INVALID_ARG;
+    if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
+    if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (n >= (1ull << 31) || min_run_len < 1 || min_run_len > kMaxMinRun) return MPS_ERR_UNSUPPORTED;
+    Plan p(n, kt == MPS_U32 ? 4 : 8, has_payload != 0, k, 0, min_run_len);
+    *bytes = p.total;
+    return MPS_OK;
+}
+
+mps_status mps_sort_keys_minrun(const void* d_keys_in, void* d_keys_out, uint64_t n, mps_key_type kt, int k,
+                                uint32_t min_run_len, void* d_ws, size_t ws_bytes, const mps_tree* opt_tree,
+                                cudaStream_t stream) {
+    if (kt == MPS_U32)
+        return sort_impl<uint32_t, false>((const uint32_t*)d_keys_in, nullptr, (uint32_t*)d_keys_out, nullptr, n, k, d_ws,
+                                          ws_bytes, opt_tree, true, stream, min_run_len);
+    if (kt == MPS_U64)
+        return sort_impl<uint64_t, false>((const uint64_t*)d_keys_in, nullptr, (uint64_t*)d_keys_out, nullptr, n, k, d_ws,
+                                          ws_bytes, opt_tree, true, stream, min_run_len);
+    return MPS_ERR_INVALID_ARG;
+}
+
+mps_status mps_sort_pairs_minrun(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out, uint32_t* d_vals_out,
+                                 uint64_t n, mps_key_type kt, int k, uint32_t min_run_len, void* d_ws, size_t ws_bytes,
+                                 const mps_tree* opt_tree, cudaStream_t stream) {
+    if (kt == MPS_U32)
+        return sort_impl<uint32_t, true>((const uint32_t*)d_keys_in, d_vals_in, (uint32_t*)d_keys_out, d_vals_out, n, k, d_ws,
+                                         ws_bytes, opt_tree, true, stream, min_run_len);
+    if (kt == MPS_U64)
+        return sort_impl<uint64_t, true>((const uint64_t*)d_keys_in, d_vals_in, (uint64_t*)d_keys_out, d_vals_out, n, k, d_ws,
+                                         ws_bytes, opt_tree, true, stream, min_run_len);
     return MPS_ERR_INVALID_ARG;
 }
 

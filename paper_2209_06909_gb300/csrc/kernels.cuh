@@ -32,6 +32,7 @@ enum : int {
     kCtrMaxLen = 204,   // longest array of a batch (elements)
     kCtrDetTile = 205,  // next run-detection tile to take
     kCtrCand = 206,     // node-pass candidates listed by the mask pass
+    kCtrMrGood = 207,   // minimum run length: good intervals (natural runs of >= m-1 interior flags)
     kCtrWords = 256
 };
 
@@ -91,6 +92,30 @@ struct WsView {
     uint2* batch_prm;              // [2m] per-array power parameters
 };
 
+// Buffers of the minimum-run-length partition (Sec. 5, "Minimal run length").
+// A good interval j is the set [gs[j], ge[j]) of positions from which the
+// natural run is at least m long; all of them end their run at v[j].  Node 0
+// is position 0, node j + 1 the position v[j]; every node knows the node its
+// run progression reaches next (succ), the start of the natural run that ends
+// the progression (hit, n if none), and how many runs it contributes (cnt).
+struct MinRunView {
+    uint32_t m;            // minimum run length, 2..32
+    uint32_t cap;          // capacity of the good-interval and node arrays
+    uint32_t* gs;
+    uint32_t* ge;
+    uint32_t* gv;
+    uint32_t* succ;
+    uint32_t* hit;
+    uint32_t* cnt;
+    uint32_t* off;         // run index of each node's first run (marked nodes)
+    uint32_t* mark;        // node on the chain from position 0
+    uint32_t* jmp0;        // pointer-jumping buffers
+    uint32_t* jmp1;
+    uint32_t* tiles;       // per-tile counts and offsets of the two scans
+    uint32_t tiles_cap;
+    uint8_t* desc_nat;     // direction of each run's natural part (tree output)
+};
+
 // Sizes of the merge stages for one key/payload type.
 struct MergeGeom {
     uint32_t c_fused;   // elements of shared memory per fused tile
@@ -121,10 +146,10 @@ void launch_node_pass(uint32_t r, int k, uint32_t tmax, uint32_t vmax, const WsV
 void launch_bucket(uint32_t total_bound, const WsView& ws, cudaStream_t st);
 // Canonical tree of the last sort (r read on the device, r <= r_bound).
 void launch_tree_dump(uint32_t r_bound, int k, const WsView& ws, uint32_t* node_first, void* nodes, cudaStream_t st);
-// Run starts, directions, powers and counts {r, nodes, levels, M} of the last
-// sort copied to the caller's tree arrays (any may be null).
-void launch_tree_arrays(uint32_t r_bound, const WsView& ws, uint32_t* run_starts, uint8_t* run_desc, uint8_t* powers,
-                        uint8_t* leaf_depth, uint64_t* counts, cudaStream_t st);
+// Run starts, directions (from desc_src), powers and counts {r, nodes,
+// levels, M} of the last sort copied to the caller's tree arrays (any may be null).
+void launch_tree_arrays(uint32_t r_bound, const WsView& ws, const uint8_t* desc_src, uint32_t* run_starts, uint8_t* run_desc,
+                        uint8_t* powers, uint8_t* leaf_depth, uint64_t* counts, cudaStream_t st);
 
 // merge.cu
 template <typename K, bool V>
@@ -138,6 +163,15 @@ void launch_level_plan(int p, uint32_t nn_bound, uint64_t elems_bound, int k, co
 template <typename K, bool V>
 void launch_level_merge(uint32_t nn_bound, uint64_t elems_bound, const K* leaf_keys, const uint32_t* leaf_vals, K* out,
                         uint32_t* vout, const MergeGeom& g, const WsView& ws, cudaStream_t st);
+// minrun.cu: replaces the natural run partition in ws (run_starts, run
+// direction, r) by the minimum-run-length partition; `copy` holds a copy of
+// the keys (and payloads) into which every run of at most m elements is
+// sorted stably.  ws.run_desc then flags only the natural runs longer than m
+// that are strictly descending (read backwards by the merges).
+template <typename K, bool V>
+void launch_min_run(const K* keys, K* copy, uint32_t* vcopy, uint64_t n, const MinRunView& mr, const WsView& ws,
+                    cudaStream_t st);
+
 template <typename K, bool V>
 void launch_copy_single_run(const K* in, const uint32_t* vin, K* out, uint32_t* vout, uint64_t n,
                             const WsView& ws, cudaStream_t st);

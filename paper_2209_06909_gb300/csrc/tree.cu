@@ -779,10 +779,10 @@ void launch_tree_dump(uint32_t r_bound, int k, const WsView& ws, uint32_t* node_
     g_launches += nodes ? 5 : 4;
 }
 
-void launch_tree_arrays(uint32_t r_bound, const WsView& ws, uint32_t* run_starts, uint8_t* run_desc, uint8_t* powers,
-                        uint8_t* leaf_depth, uint64_t* counts, cudaStream_t st) {
+void launch_tree_arrays(uint32_t r_bound, const WsView& ws, const uint8_t* desc_src, uint32_t* run_starts,
+                        uint8_t* run_desc, uint8_t* powers, uint8_t* leaf_depth, uint64_t* counts, cudaStream_t st) {
     const uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r_bound + 1, 256), 152 * 8);
-    k_tree_arrays<<<blocks, 256, 0, st>>>(ws.counters, ws.run_starts, ws.run_desc, ws.powers, run_starts, run_desc, powers,
+    k_tree_arrays<<<blocks, 256, 0, st>>>(ws.counters, ws.run_starts, desc_src, ws.powers, run_starts, run_desc, powers,
                                           leaf_depth, counts);
     g_launches += 1;
 }

@@ -74,7 +74,8 @@ EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_t
            "mps_batch_workspace_size", "mps_sort_batch", "mps_sort_batch_pairs", "mps_batch_autotune",
            "mps_batch_graph_create", "mps_batch_graph_launch", "mps_batch_graph_destroy",
            "mps_queue_create", "mps_queue_submit", "mps_queue_poll", "mps_queue_wait", "mps_queue_pause",
-           "mps_queue_destroy", "mps_records_workspace_size", "mps_sort_records", "mps_sync_status"]
+           "mps_queue_destroy", "mps_records_workspace_size", "mps_sort_records", "mps_sync_status",
+           "mps_workspace_size_minrun", "mps_sort_keys_minrun", "mps_sort_pairs_minrun"]
 
 # Largest n accepted by mps_sort_keys_noalloc (its scratch is compiled into the library).
 NOALLOC_MAX_N = 1 << 20
@@ -103,6 +104,11 @@ def lib():
     L.mps_last_stats.argtypes = [P]
     L.mps_sync_status.argtypes = [P, P]
     L.mps_sync_status.restype = I
+    L.mps_workspace_size_minrun.argtypes = [U64, I, I, I, ctypes.c_uint32, ctypes.POINTER(ctypes.c_size_t)]
+    L.mps_sort_keys_minrun.argtypes = [P, P, U64, I, I, ctypes.c_uint32, P, ctypes.c_size_t, P, P]
+    L.mps_sort_pairs_minrun.argtypes = [P, P, P, P, U64, I, I, ctypes.c_uint32, P, ctypes.c_size_t, P, P]
+    for fn in ("mps_workspace_size_minrun", "mps_sort_keys_minrun", "mps_sort_pairs_minrun"):
+        getattr(L, fn).restype = I
     L.mps_sort_keys_noalloc.argtypes = [P, P, U64, I, I, P]
     L.mps_sort_keys_noalloc.restype = I
     U32 = ctypes.c_uint32
@@ -462,3 +468,42 @@ def sync_status(ws: torch.Tensor, stream=None) -> None:
     """Waits for the stream and raises if the last sort on this workspace
     reported a device-side failure (mps_sync_status)."""
     _check("mps_sync_status", lib().mps_sync_status(ws.data_ptr(), _stream(stream)))
+
+
+def workspace_minrun(n: int, key_bytes: int, has_payload: bool = False, k: int = 4, min_run_len: int = 24,
+                     device="cuda") -> torch.Tensor:
+    """Workspace for the minimum-run-length sorts (mps_workspace_size_minrun)."""
+    b = ctypes.c_size_t(0)
+    kt = 0 if key_bytes == 4 else 1
+    _check("mps_workspace_size_minrun", lib().mps_workspace_size_minrun(n, kt, int(has_payload), k, min_run_len,
+                                                                        ctypes.byref(b)))
+    return torch.empty(max(b.value, 16), dtype=torch.uint8, device=device)
+
+
+def sort_keys_minrun(keys: torch.Tensor, min_run_len: int = 24, k: int = 4, out: torch.Tensor | None = None,
+                     ws: torch.Tensor | None = None, tree: TreeBuffers | None = None, stream=None) -> torch.Tensor:
+    """Sort with runs extended to min_run_len (mps_sort_keys_minrun)."""
+    n = keys.numel()
+    out = torch.empty_like(keys) if out is None else out
+    if ws is None:
+        ws = workspace_minrun(n, keys.element_size(), False, k, min_run_len, keys.device)
+    ts = ctypes.byref(tree.struct()) if tree is not None else None
+    _check("mps_sort_keys_minrun", lib().mps_sort_keys_minrun(keys.data_ptr(), out.data_ptr(), n, _key_type(keys), k,
+                                                              min_run_len, ws.data_ptr(), ws.numel(), ts,
+                                                              _stream(stream)))
+    return out
+
+
+def sort_pairs_minrun(keys: torch.Tensor, vals: torch.Tensor, min_run_len: int = 24, k: int = 4, out_keys=None,
+                      out_vals=None, ws=None, tree: TreeBuffers | None = None, stream=None):
+    """Stable key/value sort with runs extended to min_run_len (mps_sort_pairs_minrun)."""
+    n = keys.numel()
+    out_keys = torch.empty_like(keys) if out_keys is None else out_keys
+    out_vals = torch.empty_like(vals) if out_vals is None else out_vals
+    if ws is None:
+        ws = workspace_minrun(n, keys.element_size(), True, k, min_run_len, keys.device)
+    ts = ctypes.byref(tree.struct()) if tree is not None else None
+    _check("mps_sort_pairs_minrun", lib().mps_sort_pairs_minrun(keys.data_ptr(), vals.data_ptr(), out_keys.data_ptr(),
+                                                                out_vals.data_ptr(), n, _key_type(keys), k, min_run_len,
+                                                                ws.data_ptr(), ws.numel(), ts, _stream(stream)))
+    return out_keys, out_vals
