@@ -160,24 +160,52 @@ def time_sorts(mps, torch, d_in, d_out, ws, k, steps, warmup, stream, barrier=No
     return start.elapsed_time(end) / steps
 
 
-def cpu_baseline(n_sample, seed):
-    """The oracle as it stands (single thread), timed on a bounded sample of the
-    same workload (a random permutation of n_sample keys, k = 4)."""
+def cpu_baseline(n_sample, seed, reps=5):
+    """The oracle as it stands (single thread, pinned to one host core), timed
+    on a bounded sample of the same workload (a random permutation of n_sample
+    keys, k = 4): the median of `reps` runs, with std::stable_sort on the same
+    core and input beside it as a second reference."""
     import oracle
     a = gen_input("perm", n_sample, seed)
     oracle.sort(a[:4096], k=4, want_tree=False)
-    t0 = time.perf_counter()
-    res = oracle.sort(a, k=4, want_tree=False)
-    dt = time.perf_counter() - t0
-    assert np.array_equal(res["keys"], np.arange(n_sample, dtype=np.uint32))
+    oracle.std_stable_sort(a[:4096])
+    pinned = hasattr(os, "sched_setaffinity")
+    if pinned:
+        old_aff = os.sched_getaffinity(0)
+        os.sched_setaffinity(0, {min(old_aff)})
+    try:
+        t_or, t_std = [], []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            res = oracle.sort(a, k=4, want_tree=False)
+            t_or.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            ref = oracle.std_stable_sort(a)
+            t_std.append(time.perf_counter() - t0)
+    finally:
+        if pinned:
+            os.sched_setaffinity(0, old_aff)
+    want = np.arange(n_sample, dtype=np.uint32)
+    assert np.array_equal(res["keys"], want) and np.array_equal(ref, want)
+    dt, ds = float(np.median(t_or)), float(np.median(t_std))
     return {"value": n_sample / dt / 1e9, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
-            "sample": f"one sort of a random permutation of 2^{int(math.log2(n_sample))} uint32 keys, k=4, "
-                      f"{dt:.1f} s on one host core (nproc={os.cpu_count()})"}
+            "sample": f"median of {reps} sorts of a random permutation of 2^{int(math.log2(n_sample))} uint32 keys, "
+                      f"k=4, {dt:.2f} s each on one pinned host core (nproc={os.cpu_count()})",
+            "std_stable_sort": {"value": n_sample / ds / 1e9, "unit": "GKeys/s", "seconds": ds},
+            "pinned_core": pinned}
 
 
 # ------------------------------------------------------------------ sections
 
-def bench_pairs(mps, torch, dev, stream, steps=5):
+def sort_frac(bytes_per_key, n, merge_cost, ms, peaks):
+    """B_alg = b (n + 2M) over the sort time, against the measured copy
+    bandwidth and the nominal 8 TB/s."""
+    b_alg = bytes_per_key * (n + 2.0 * merge_cost)
+    gbs = b_alg / (ms * 1e-3) / 1e9
+    return {"b_alg_bytes": b_alg, "frac_of_measured": gbs / peaks["hbm_gbs"], "frac_of_8tbs": gbs / NOMINAL_HBM_GBS}
+
+
+def bench_pairs(mps, torch, dev, stream, peaks, steps=5):
     """n = 2^27 uint64 keys from 2^16 distinct values, runs log-uniform in
     [2, 2^16], uint32 payload = index; stable order checked on samples."""
     from paper_2209_06909_gb300 import inputs
@@ -210,10 +238,10 @@ def bench_pairs(mps, torch, dev, stream, steps=5):
     st = mps.last_stats()
     return {"workload": "n=2^27 uint64 keys (2^16 distinct) + uint32 index payload, runs log-uniform [2,2^16], k=4",
             "ms": ms, "gkeys_s": n / (ms * 1e-3) / 1e9, "merge_cost_per_n": st["merge_cost"] / n,
-            "stable_sample_checked": int(idx.size)}
+            "stable_sample_checked": int(idx.size), "sort_roofline": sort_frac(12.0, n, st["merge_cost"], ms, peaks)}
 
 
-def bench_records(mps, torch, dev, stream, steps=5):
+def bench_records(mps, torch, dev, stream, peaks, steps=5):
     """Records (Sec. 5): n = 2^26 uint64 keys with uint64 payloads (16 bytes),
     random runs of geometric mean sqrt(n); mps_sort_records, payloads checked
     on a sample against the stable order of the keys."""
@@ -242,10 +270,12 @@ def bench_records(mps, torch, dev, stream, steps=5):
     assert np.array_equal(vals[: 1 << 16], v[order])
     return {"workload": "n=2^26 records: uint64 key + uint64 payload, geometric runs of mean sqrt(n), k=4",
             "ms": ms, "gkeys_s": n / (ms * 1e-3) / 1e9, "merge_cost_per_n": st["merge_cost"] / n,
-            "payload_sample_checked": 1 << 16}
+            "payload_sample_checked": 1 << 16,
+            # the records model: every merge reads and writes 16-byte records
+            "sort_roofline": sort_frac(16.0, n, st["merge_cost"], ms, peaks)}
 
 
-def bench_batch(mps, torch, dev, stream, steps=5):
+def bench_batch(mps, torch, dev, stream, peaks, steps=5):
     """4096 uint32 arrays, sizes log-uniform [2^4, 2^20]: one graph-captured
     batched sort (autotuned k) against one plain mps_sort_keys per array."""
     from paper_2209_06909_gb300 import inputs
@@ -259,8 +289,10 @@ def bench_batch(mps, torch, dev, stream, steps=5):
     out = torch.empty_like(d_in)
     ws = mps.batch_workspace(n, m, 4, False, 0, dev)
     best_k = mps.batch_autotune(d_in, d_off, out, ws, max_len=int(sizes.max()), stream=stream)
-    g = mps.BatchGraph(d_in, d_off, out, ws, k=best_k, max_len=int(sizes.max()), stream=stream)
+    costs = torch.zeros(m, dtype=torch.int64, device=dev)
+    g = mps.BatchGraph(d_in, d_off, out, ws, k=best_k, max_len=int(sizes.max()), stream=stream, merge_costs=costs)
     g.launch(stream=stream, check=True)
+    merge_cost = int(costs.sum().item())
     got = mps.to_numpy(out, np.uint32)
     for a in range(0, m, 97):  # sampled arrays against numpy
         lo, hi = int(offsets[a]), int(offsets[a + 1])
@@ -294,7 +326,10 @@ def bench_batch(mps, torch, dev, stream, steps=5):
             "n_keys": int(n), "k_autotuned": best_k,
             "batched_graph_ms": batched_ms, "batched_gkeys_s": n / (batched_ms * 1e-3) / 1e9,
             "plain_per_array_ms": plain_s * 1e3, "plain_gkeys_s": n / plain_s / 1e9,
-            "speedup_vs_plain": plain_s * 1e3 / batched_ms}
+            "plain_form": "one mps_sort_keys per array, queued back to back on one stream (no host waits)",
+            "speedup_vs_plain": plain_s * 1e3 / batched_ms,
+            "merge_cost_per_n": merge_cost / n,
+            "sort_roofline": sort_frac(4.0, n, merge_cost, batched_ms, peaks)}
 
 
 def bench_serve(mps, torch, dev, stream, nreq=160):
@@ -305,11 +340,10 @@ def bench_serve(mps, torch, dev, stream, nreq=160):
     import threading
     from paper_2209_06909_gb300 import inputs
     reqs = inputs.request_stream(nreq, 5, rate_per_s=1.0)
-    tmpl = []
-    for r in reqs[:24]:
+    jobs = []
+    for r in reqs:
         kk, vv = inputs.request_keys(r)
-        tmpl.append((r["kind"], mps.to_device(kk, dev), mps.to_device(vv, dev) if vv is not None else None))
-    jobs = [tmpl[i % len(tmpl)] for i in range(nreq)]
+        jobs.append((r["kind"], mps.to_device(kk, dev), mps.to_device(vv, dev) if vv is not None else None))
     outs = [(torch.empty_like(k), torch.empty_like(v) if v is not None else None) for (_, k, v) in jobs]
     total_keys = sum(k.numel() for (_, k, _) in jobs)
     ws_plain = {4: mps.workspace(1 << 24, 4, False, 4, dev), 8: mps.workspace(1 << 24, 8, True, 4, dev)}
@@ -329,6 +363,8 @@ def bench_serve(mps, torch, dev, stream, nreq=160):
         run_plain_one(j)
     torch.cuda.synchronize()
     serial_s = time.perf_counter() - t0
+    # every plain result, kept to check the queue's results against
+    refs = [(ok.clone(), ov.clone() if ov is not None else None) for (ok, ov) in outs]
     cap = nreq / serial_s  # requests per second the serial server sustains
     pool = torch.empty(64 << 30, dtype=torch.uint8, device=dev)
     sweep = []
@@ -376,19 +412,15 @@ def bench_serve(mps, torch, dev, stream, nreq=160):
                                        "p50_ms": float(np.percentile(lat, 50)) * 1e3,
                                        "p99_ms": float(np.percentile(lat, 99)) * 1e3}})
     del pool
-    # results of the queue equal the plain results (last sweep point): spot check
-    kind, k, v = jobs[0]
-    ok, _ = outs[0]
-    ref = torch.empty_like(k)
-    if kind == "keys":
-        mps.sort_keys(k, k=4, out=ref, stream=stream)
-    else:
-        mps.sort_pairs(k, v, k=4, out_keys=ref, stream=stream)
-    torch.cuda.synchronize()
-    assert torch.equal(ref, ok)
+    # every result of the queue (last sweep point) equals the request sorted alone
+    for j in range(nreq):
+        assert torch.equal(outs[j][0], refs[j][0]), f"request {j}: keys differ from the plain sort"
+        if refs[j][1] is not None:
+            assert torch.equal(outs[j][1], refs[j][1]), f"request {j}: payloads differ from the plain sort"
     return {"workload": "Poisson requests, sizes log-uniform [2^10,2^24], 50% uint32 keys / 50% uint64+uint32 "
                         "pairs, 64 GB admission budget, max_inflight 3, max_batch 64",
-            "requests": nreq, "serial_back_to_back_gkeys_s": total_keys / serial_s / 1e9, "sweep": sweep,
+            "requests": nreq, "distinct_requests": nreq, "results_checked": nreq,
+            "serial_back_to_back_gkeys_s": total_keys / serial_s / 1e9, "sweep": sweep,
             "throughput_ratio_at_max_rate": sweep[-1]["queue"]["gkeys_s"] / sweep[-1]["serial_plain"]["gkeys_s"]}
 
 
@@ -559,13 +591,34 @@ def run_mps(args):
                                      "geometric runs, mean 2^14", "k": kk, "ms": vms,
                                      "gkeys_s": n / (vms * 1e-3) / 1e9, "merge_cost_per_n": st["merge_cost"] / n,
                                      "levels": st["num_levels"],
-                                     "sort_frac_of_measured": ba / (vms * 1e-3) / 1e9 / peaks["hbm_gbs"]})
+                                     "sort_roofline": sort_frac(b, n, st["merge_cost"], vms, peaks)})
+            # minimum run length 24 (Sec. 5, the paper's experimental setting), k = 4
+            for kind, dsrc in (("perm", d_in), ("runs", d_runs)):
+                wmr = mps.workspace_minrun(n, 4, False, k, 24, dev)
+                for _ in range(3):
+                    mps.sort_keys_minrun(dsrc, min_run_len=24, k=k, out=d_out, ws=wmr, stream=stream)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                for _ in range(8):
+                    mps.sort_keys_minrun(dsrc, min_run_len=24, k=k, out=d_out, ws=wmr, stream=stream)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                vms = ev0.elapsed_time(ev1) / 8
+                st = mps.last_stats()
+                if kind == "perm":
+                    assert torch.equal(d_out, torch.arange(n, dtype=torch.int32, device=dev))
+                variants.append({"input": ("random permutation" if kind == "perm" else "geometric runs, mean 2^14")
+                                 + ", min_run_len 24", "k": k, "ms": vms, "gkeys_s": n / (vms * 1e-3) / 1e9,
+                                 "runs": st["r"], "merge_cost_per_n": st["merge_cost"] / n, "levels": st["num_levels"],
+                                 "sort_roofline": sort_frac(b, n, st["merge_cost"], vms, peaks)})
+                del wmr
             line["variants"] = variants
             del d_runs, ws_k
         del d_tmp
-        for name, fn, flag in (("pairs", lambda: bench_pairs(mps, torch, dev, stream), args.no_variants),
-                               ("records", lambda: bench_records(mps, torch, dev, stream), args.no_variants),
-                               ("batch", lambda: bench_batch(mps, torch, dev, stream), args.no_batch),
+        for name, fn, flag in (("pairs", lambda: bench_pairs(mps, torch, dev, stream, peaks), args.no_variants),
+                               ("records", lambda: bench_records(mps, torch, dev, stream, peaks), args.no_variants),
+                               ("batch", lambda: bench_batch(mps, torch, dev, stream, peaks), args.no_batch),
                                ("serve", lambda: bench_serve(mps, torch, dev, stream, args.serve_requests),
                                 args.no_serve)):
             if flag:
@@ -576,7 +629,7 @@ def run_mps(args):
                 line[name] = {"error": f"{type(exc).__name__}: {exc}"}
             torch.cuda.empty_cache()
         if not args.no_cpu:
-            line["cpu_baseline"] = cpu_baseline(1 << 24, 1234)
+            line["cpu_baseline"] = cpu_baseline(1 << 23, 1234)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier(device_ids=[local])

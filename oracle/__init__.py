@@ -35,15 +35,46 @@ NODE_DTYPE = np.dtype([("first_run", "<u4"), ("end_run", "<u4"), ("power", "u1")
 assert NODE_DTYPE.itemsize == 16
 
 
+_REF_SO = _BUILD / "libstd_stable_sort.so"
+_REF_SRC = _HERE / "std_stable_sort.cpp"
+
+
 def build(force: bool = False) -> Path:
-    """Compiles the oracle with gcc (portable flags: runs on x86 and Arm)."""
+    """Compiles the oracle with gcc (portable flags: runs on x86 and Arm), and
+    the std::stable_sort reference used by the CPU baseline with g++."""
     _BUILD.mkdir(exist_ok=True)
     if force or not _SO.exists() or _SO.stat().st_mtime < _SRC.stat().st_mtime:
         tmp = _SO.with_suffix(f".{os.getpid()}.tmp")
         subprocess.check_call(["gcc", "-O3", "-std=c11", "-shared", "-fPIC", "-Wall",
                                "-o", str(tmp), str(_SRC)])
         os.replace(tmp, _SO)
+    if force or not _REF_SO.exists() or _REF_SO.stat().st_mtime < _REF_SRC.stat().st_mtime:
+        tmp = _REF_SO.with_suffix(f".{os.getpid()}.tmp")
+        subprocess.check_call(["g++", "-O3", "-std=c++17", "-shared", "-fPIC", "-Wall",
+                               "-o", str(tmp), str(_REF_SRC)])
+        os.replace(tmp, _REF_SO)
     return _SO
+
+
+_ref_lib = None
+
+
+def std_stable_sort(keys):
+    """std::stable_sort of a copy of ``keys`` (uint32 or uint64) on one host
+    thread: the second CPU reference of the baseline (not part of the oracle's
+    method; sorted keys are unique, so it also cross-checks the oracle)."""
+    global _ref_lib
+    if _ref_lib is None:
+        build()
+        _ref_lib = ctypes.CDLL(str(_REF_SO))
+    a = np.array(keys, copy=True)
+    if a.dtype == np.uint32:
+        _ref_lib.ref_stable_sort_u32(ctypes.c_void_p(a.ctypes.data), ctypes.c_uint64(a.size))
+    elif a.dtype == np.uint64:
+        _ref_lib.ref_stable_sort_u64(ctypes.c_void_p(a.ctypes.data), ctypes.c_uint64(a.size))
+    else:
+        raise TypeError("keys must be uint32 or uint64")
+    return a
 
 
 _lib = None

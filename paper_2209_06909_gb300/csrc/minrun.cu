@@ -18,10 +18,13 @@
 // on its own; pointer jumping then marks the chain that starts at position 0,
 // a scan numbers its runs, and one pass writes them.
 //
-// Runs of at most m elements are sorted stably by one warp each (rank of every
-// element under (key, position)) in a copy of the input; longer runs are
-// natural runs, read forwards or (strictly descending) backwards by the merges.
+// Runs of at most m elements are sorted stably in a copy of the input, one
+// thread each, by a sorting network on (key, position) pairs (any stable sort
+// gives the same run; the paper extends runs with insertion sort); longer
+// runs are natural runs, read forwards or (strictly descending) backwards by
+// the merges.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -34,20 +37,33 @@ constexpr int kMrThreads = 256;
 constexpr int kMrItems = 16;
 constexpr uint32_t kMrTile = kMrThreads * kMrItems;
 
-// Run i of the natural partition has at least m-1 interior flags: its start
-// positions from u-1 to e-m take the natural run to e.
+// Run [s, e) of the natural partition has at least m-1 interior flags: its
+// start positions from u-1 to e-m take the natural run to e.  The flag at s
+// belongs to the run's stretch when it has the run's direction (u = s), else
+// u = s + 1; it matters only for a run of exactly m-1 elements (a longer run
+// is good either way, a shorter one never), so the two keys at s are read
+// only then, or when u itself is wanted.
 template <typename K>
-__device__ __forceinline__ bool good_run(const K* __restrict__ keys, const uint32_t* __restrict__ rs,
-                                         const uint8_t* __restrict__ rdesc, uint32_t i, uint32_t m, uint32_t* u_out,
-                                         uint32_t* e_out) {
-    const uint32_t s = rs[i], e = rs[i + 1];
-    const uint32_t dir = rdesc[i];
-    // the flag at s belongs to the stretch when it has the run's direction
+__device__ __forceinline__ uint32_t stretch_start(const K* __restrict__ keys, uint32_t s, uint32_t dir) {
     const uint32_t lt_s = s > 0 && keys[s] < keys[s - 1] ? 1u : 0u;
-    const uint32_t u = s + ((s > 0 && lt_s == dir) ? 0u : 1u);
-    *u_out = u;
-    *e_out = e;
-    return e >= u && e - u + 1 >= m;
+    return s + ((s > 0 && lt_s == dir) ? 0u : 1u);
+}
+template <typename K>
+__device__ __forceinline__ bool good_run(const K* __restrict__ keys, uint32_t s, uint32_t e, uint32_t dir, uint32_t m) {
+    const uint32_t len = e - s;
+    if (len >= m) return true;
+    if (len + 1 < m) return false;
+    return stretch_start(keys, s, dir) == s;
+}
+// rs[i0 .. i0 + 16] (the run-start array is padded past r for 16-byte loads)
+__device__ __forceinline__ void load_starts17(const uint32_t* __restrict__ rs, uint32_t i0, uint32_t (&v)[17]) {
+    const uint4* r4 = reinterpret_cast<const uint4*>(rs + i0);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const uint4 x = r4[q];
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+    v[16] = rs[i0 + 16];
 }
 
 // Per tile of kMrTile natural runs: the number of good runs.
@@ -62,9 +78,12 @@ __global__ void __launch_bounds__(kMrThreads) k_mr_good_count(const uint64_t* __
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint32_t i0 = tile * kMrTile + threadIdx.x * kMrItems;
         uint32_t c = 0;
-        for (uint32_t q = 0; q < (uint32_t)kMrItems; q++) {
-            uint32_t u, e;
-            if (i0 + q < r && good_run(keys, rs, rdesc, i0 + q, m, &u, &e)) c++;
+        if (i0 < r) {
+            uint32_t v[17];
+            load_starts17(rs, i0, v);
+#pragma unroll
+            for (uint32_t q = 0; q < (uint32_t)kMrItems; q++)
+                if (i0 + q < r && good_run(keys, v[q], v[q + 1], rdesc[i0 + q], m)) c++;
         }
         uint32_t tot;
         block_sum_excl<kMrThreads>(c, tmp, &tot);
@@ -111,16 +130,19 @@ __global__ void __launch_bounds__(kMrThreads) k_mr_good_write(const uint64_t* __
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint32_t i0 = tile * kMrTile + threadIdx.x * kMrItems;
         uint32_t flags = 0;
-        for (uint32_t q = 0; q < (uint32_t)kMrItems; q++) {
-            uint32_t u, e;
-            if (i0 + q < r && good_run(keys, rs, rdesc, i0 + q, m, &u, &e)) flags |= 1u << q;
+        uint32_t v[17];
+        if (i0 < r) {
+            load_starts17(rs, i0, v);
+#pragma unroll
+            for (uint32_t q = 0; q < (uint32_t)kMrItems; q++)
+                if (i0 + q < r && good_run(keys, v[q], v[q + 1], rdesc[i0 + q], m)) flags |= 1u << q;
         }
         uint32_t at = tiles[tile] + block_sum_excl<kMrThreads>((uint32_t)__popc(flags), tmp, nullptr);
         while (flags) {
             const uint32_t q = __ffs(flags) - 1;
             flags &= flags - 1;
-            uint32_t u, e;
-            good_run(keys, rs, rdesc, i0 + q, m, &u, &e);
+            const uint32_t sq = rs[i0 + q], e = rs[i0 + q + 1];
+            const uint32_t u = stretch_start(keys, sq, (uint32_t)rdesc[i0 + q]);
             if (at < mr.cap) {
                 mr.gs[at] = u - 1;
                 mr.ge[at] = e - m + 1;
@@ -271,31 +293,95 @@ __global__ void __launch_bounds__(kMrThreads) k_mr_write_runs(uint64_t* __restri
     }
 }
 
-// One warp per run of at most m <= 32 elements: every element's rank under
-// (key, position), i.e. its place in the stable sort of the run; the run is
-// rewritten in place in the copy.
+// (key, position) as one 64-bit word for 32-bit keys: comparing the words
+// compares keys, then positions, so sorting them is a stable sort of the keys.
+struct ShortItem32 {
+    unsigned long long kp;
+    __device__ __forceinline__ bool before(const ShortItem32& o) const { return kp < o.kp; }
+};
+struct ShortItem64 {
+    uint64_t key;
+    uint32_t pos;
+    __device__ __forceinline__ bool before(const ShortItem64& o) const {
+        return key < o.key || (key == o.key && pos < o.pos);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void cswap(T& a, T& b, uint32_t& va, uint32_t& vb) {
+    const bool sw = b.before(a);
+    const T lo = sw ? b : a, hi = sw ? a : b;
+    const uint32_t vlo = sw ? vb : va, vhi = sw ? va : vb;
+    a = lo;
+    b = hi;
+    va = vlo;
+    vb = vhi;
+}
+
+// Batcher's odd-even merge sort network on 32 inputs: 191 compare-exchanges
+// (i, j), i < j, in order (table below).
+constexpr int kNet32Len = 191;
+
+// The network on 32 items held in registers: the loop is unrolled, so every
+// index is a compile-time constant.
+template <typename T>
+__device__ __forceinline__ void sort_net32(T (&x)[32], uint32_t (&v)[32]) {
+    constexpr uint8_t net[kNet32Len][2] = {
+    {0, 1}, {2, 3}, {4, 5}, {6, 7}, {8, 9}, {10, 11}, {12, 13}, {14, 15}, {16, 17}, {18, 19}, {20, 21}, {22, 23},
+    {24, 25}, {26, 27}, {28, 29}, {30, 31}, {0, 2}, {1, 3}, {4, 6}, {5, 7}, {8, 10}, {9, 11}, {12, 14}, {13, 15},
+    {16, 18}, {17, 19}, {20, 22}, {21, 23}, {24, 26}, {25, 27}, {28, 30}, {29, 31}, {1, 2}, {5, 6}, {9, 10}, {13, 14},
+    {17, 18}, {21, 22}, {25, 26}, {29, 30}, {0, 4}, {1, 5}, {2, 6}, {3, 7}, {8, 12}, {9, 13}, {10, 14}, {11, 15},
+    {16, 20}, {17, 21}, {18, 22}, {19, 23}, {24, 28}, {25, 29}, {26, 30}, {27, 31}, {2, 4}, {3, 5}, {10, 12}, {11, 13},
+    {18, 20}, {19, 21}, {26, 28}, {27, 29}, {1, 2}, {3, 4}, {5, 6}, {9, 10}, {11, 12}, {13, 14}, {17, 18}, {19, 20},
+    {21, 22}, {25, 26}, {27, 28}, {29, 30}, {0, 8}, {1, 9}, {2, 10}, {3, 11}, {4, 12}, {5, 13}, {6, 14}, {7, 15},
+    {16, 24}, {17, 25}, {18, 26}, {19, 27}, {20, 28}, {21, 29}, {22, 30}, {23, 31}, {4, 8}, {5, 9}, {6, 10}, {7, 11},
+    {20, 24}, {21, 25}, {22, 26}, {23, 27}, {2, 4}, {3, 5}, {6, 8}, {7, 9}, {10, 12}, {11, 13}, {18, 20}, {19, 21},
+    {22, 24}, {23, 25}, {26, 28}, {27, 29}, {1, 2}, {3, 4}, {5, 6}, {7, 8}, {9, 10}, {11, 12}, {13, 14}, {17, 18},
+    {19, 20}, {21, 22}, {23, 24}, {25, 26}, {27, 28}, {29, 30}, {0, 16}, {1, 17}, {2, 18}, {3, 19}, {4, 20}, {5, 21},
+    {6, 22}, {7, 23}, {8, 24}, {9, 25}, {10, 26}, {11, 27}, {12, 28}, {13, 29}, {14, 30}, {15, 31}, {8, 16}, {9, 17},
+    {10, 18}, {11, 19}, {12, 20}, {13, 21}, {14, 22}, {15, 23}, {4, 8}, {5, 9}, {6, 10}, {7, 11}, {12, 16}, {13, 17},
+    {14, 18}, {15, 19}, {20, 24}, {21, 25}, {22, 26}, {23, 27}, {2, 4}, {3, 5}, {6, 8}, {7, 9}, {10, 12}, {11, 13},
+    {14, 16}, {15, 17}, {18, 20}, {19, 21}, {22, 24}, {23, 25}, {26, 28}, {27, 29}, {1, 2}, {3, 4}, {5, 6}, {7, 8},
+    {9, 10}, {11, 12}, {13, 14}, {15, 16}, {17, 18}, {19, 20}, {21, 22}, {23, 24}, {25, 26}, {27, 28}, {29, 30},
+    };
+#pragma unroll
+    for (int c = 0; c < kNet32Len; c++) cswap(x[net[c][0]], x[net[c][1]], v[net[c][0]], v[net[c][1]]);
+}
+
+// One thread per run of at most m <= 32 elements: the run is loaded into
+// registers (padded with items that sort last), sorted stably by (key,
+// position), and rewritten in place in the copy.
 template <typename K, bool V>
 __global__ void __launch_bounds__(kMrThreads) k_mr_sort_short(const uint64_t* __restrict__ ctr, const uint32_t* __restrict__ rs,
                                                              uint32_t m, K* __restrict__ copy, uint32_t* __restrict__ vcopy,
                                                              uint32_t r_cap) {
+    using T = typename std::conditional<sizeof(K) == 4, ShortItem32, ShortItem64>::type;
     const uint32_t r = min((uint32_t)ctr[kCtrR], r_cap);
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t q = warp; q < r; q += nwarps) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < r; q += gridDim.x * blockDim.x) {
         const uint32_t s = rs[q], len = rs[q + 1] - s;
         if (len > m || len < 2) continue;
-        const K key = lane < len ? copy[s + lane] : K(0);
-        const uint32_t val = (V && lane < len) ? vcopy[s + lane] : 0u;
-        uint32_t rank = 0;
-        for (uint32_t t = 0; t < len; t++) {
-            const K kt = __shfl_sync(0xffffffffu, key, t);
-            rank += (kt < key || (kt == key && t < lane)) ? 1u : 0u;
+        T x[32];
+        uint32_t v[32];
+#pragma unroll
+        for (uint32_t i = 0; i < 32; i++) {
+            const bool in = i < len;
+            const K key = in ? copy[s + i] : ~K(0);
+            if constexpr (sizeof(K) == 4) {
+                x[i].kp = ((unsigned long long)key << 32) | (in ? i : 32u + i);
+            } else {
+                x[i].key = key;
+                x[i].pos = in ? i : 32u + i;
+            }
+            v[i] = (V && in) ? vcopy[s + i] : 0u;
         }
-        __syncwarp();
-        if (lane < len) {
-            copy[s + rank] = key;
-            if (V) vcopy[s + rank] = val;
+        sort_net32(x, v);
+#pragma unroll
+        for (uint32_t i = 0; i < 32; i++) {
+            if (i < len) {
+                if constexpr (sizeof(K) == 4) copy[s + i] = (K)(x[i].kp >> 32);
+                else copy[s + i] = x[i].key;
+                if (V) vcopy[s + i] = v[i];
+            }
         }
     }
 }
@@ -336,7 +422,7 @@ void launch_min_run(const K* keys, K* copy, uint32_t* vcopy, uint64_t n, const M
     const uint32_t run_grid = (uint32_t)std::min<uint64_t>(ceil_div(r_bound, kMrThreads), 152 * 16);
     k_mr_write_runs<K><<<run_grid, kMrThreads, 0, st>>>(ws.counters, keys, n, mr, ws.run_starts, ws.run_desc, r_bound);
     // the copy: every run of at most m elements sorted in place
-    k_mr_sort_short<K, V><<<(uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r_bound * 32, kMrThreads), 152 * 32), kMrThreads, 0,
+    k_mr_sort_short<K, V><<<(uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r_bound, kMrThreads), 152 * 16), kMrThreads, 0,
                             st>>>(ws.counters, ws.run_starts, mr.m, copy, vcopy, r_bound);
     g_launches += 9 + rounds;
 }
