@@ -575,10 +575,11 @@ def run_mps(args):
             variants = []
             b_runs = gen_input("runs", n, 2000)
             d_runs = mps.to_device(b_runs, dev)
-            # fan-in study: k = 2 (the paper's baseline), 4 (the headline), 8
+            # fan-in study: k = 2 (the paper's baseline), 4 (the headline), 8 and
+            # 16 (Sec. 6 leaves open whether k > 4 pays off)
             ws_k = {k: ws, 2: ws2}
             for kind, dsrc in (("perm", d_in), ("runs", d_runs)):
-                for kk in sorted({k, 2, 8}):
+                for kk in sorted({k, 2, 8, 16}):
                     if kind == "perm" and kk == k:
                         continue
                     if kk not in ws_k:

@@ -25,7 +25,8 @@
  *   - Key types: MPS_U32 (uint32_t) or MPS_U64 (uint64_t), compared as
  *     unsigned integers; every value, including the type's maximum, is a
  *     legal key (no sentinel is reserved; cf. Sec. 4 "Sentinel values").
- *   - Fan-in k must be 2, 4 or 8.  n must be below 2^31.
+ *   - Fan-in k must be 2, 4, 8 or 16 (Sec. 3's k-way powers for k a power of
+ *     two; Sec. 6 leaves k > 4 open).  n must be below 2^31.
  *   - For a single array, d_keys_out may equal (or overlap) d_keys_in, and
  *     d_vals_out d_vals_in: the sort then reads a copy of the input that it
  *     makes in the workspace (mps_workspace_size includes room for it).  Keys
@@ -175,7 +176,7 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
  *   max_len : an upper bound on the longest array (sizes the level loop);
  *             0 means n.  An array longer than max_len is detected on the
  *             device and reported as MPS_ERR_DEVICE_CHECK (status 16).
- *   k       : 2, 4, 8, or 0 for the fan-in chosen by mps_batch_autotune for
+ *   k       : 2, 4, 8, 16, or 0 for the fan-in chosen by mps_batch_autotune for
  *             this key type and mean array size (4 until tuned).
  * n must be below 2^31.  Workspace: mps_batch_workspace_size(n, m, kt,
  * has_payload, k); k = 0 asks for the largest over k in {2, 4, 8}.
@@ -236,7 +237,7 @@ typedef struct {
     uint32_t max_inflight;  /* batches (streams) in flight, 0 -> 2 */
     uint32_t max_batch;     /* requests per batch, 0 -> 256 */
     uint32_t timeout_ms;    /* reserved for bounded waits, 0 -> 10000 */
-    int k;                  /* fan-in 2, 4 or 8; 0 -> 4 */
+    int k;                  /* fan-in 2, 4, 8 or 16; 0 -> 4 */
 } mps_queue_config;
 
 typedef struct {
@@ -286,7 +287,7 @@ mps_status mps_queue_destroy(mps_queue* q);
  * its input and output arrays; the workspace is a 32 MiB scratch array
  * compiled into the library, which every GPU that loads the library holds
  * until the process exits.
- *   n      : at most 2^20 keys (uint32 or uint64, any k in {2,4,8});
+ *   n      : at most 2^20 keys (uint32 or uint64, any k in {2,4,8,16});
  *            larger n returns MPS_ERR_WORKSPACE without touching the GPU.
  *   Other arguments and outputs are those of mps_sort_keys (no tree output).
  * Like mps_sort_keys, the call returns once its kernels are queued; the host

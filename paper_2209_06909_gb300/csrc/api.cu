@@ -99,7 +99,7 @@ struct Plan {
         o_nodes_lvl = take((size_t)nodes_cap * sizeof(LevelNode));
         o_unit_node = take((size_t)unit_cap * 4);
         o_split = take((size_t)(unit_cap + 1) * k * 4);
-        o_udesc = take((size_t)unit_cap * 128);
+        o_udesc = take((size_t)unit_cap * kUnitDescBytes);
         o_ufirst = take((size_t)unit_cap * 4);
         o_ptiles = take((size_t)(unit_cap / kPackTile + 2) * 4);
         o_isz = take((size_t)(unit_cap + 64) * 4);  // padded for 16-byte loads past the last interval
@@ -396,7 +396,7 @@ template <typename K, bool V>
 mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, uint64_t n, int k,
                      void* d_ws, size_t ws_bytes, const mps_tree* tree, bool move_keys, cudaStream_t st,
                      uint32_t min_run = 1) {
-    if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (!fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
     if (min_run < 1 || min_run > kMaxMinRun) return MPS_ERR_UNSUPPORTED;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
     const double b = (double)sizeof(K) + (V ? 4.0 : 0.0);
@@ -514,7 +514,7 @@ template <typename K, bool V>
 mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, uint64_t n,
                       const uint64_t* d_off, uint32_t m, uint64_t max_len, int k, void* d_ws, size_t ws_bytes,
                       uint64_t* d_costs, bool sync_at_end, cudaStream_t st) {
-    if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (!fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
     struct Range {  // NVTX range around the whole batch
         Range() { nvtxRangePushA("sort_batch"); }
@@ -577,7 +577,7 @@ extern "C" {
 mps_status mps_workspace_size(uint64_t n, mps_key_type kt, int has_payload, int k, size_t* bytes) {
     if (!bytes) return MPS_ERR_INVALID_ARG;
     if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
-    if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (!fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
     Plan p(n, kt == MPS_U32 ? 4 : 8, has_payload != 0, k);
     *bytes = p.total;
@@ -623,7 +623,7 @@ mps_status mps_workspace_size_minrun(uint64_t n, mps_key_type kt, int has_payloa
                                      size_t* bytes) {
     if (!bytes) return MPS_ERR_INVALID_ARG;
     if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
-    if (k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (!fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
     if (n >= (1ull << 31) || min_run_len < 1 || min_run_len > kMaxMinRun) return MPS_ERR_UNSUPPORTED;
     Plan p(n, kt == MPS_U32 ? 4 : 8, has_payload != 0, k, 0, min_run_len);
     *bytes = p.total;
@@ -730,7 +730,7 @@ extern "C" {
 mps_status mps_batch_workspace_size(uint64_t n, uint32_t m, mps_key_type kt, int has_payload, int k, size_t* bytes) {
     if (!bytes) return MPS_ERR_INVALID_ARG;
     if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
-    if (k != 0 && k != 2 && k != 4 && k != 8) return MPS_ERR_UNSUPPORTED;
+    if (k != 0 && !fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
     size_t best = 0;
     for (int kk : {2, 4, 8}) {

@@ -36,6 +36,12 @@ enum : int {
     kCtrWords = 256
 };
 
+// Largest fan-in k (and node degree) the kernels take: k in {2, 4, 8, 16}.
+constexpr int kMaxFanIn = 16;
+inline bool fan_in_ok(int k) { return k == 2 || k == 4 || k == 8 || k == 16; }
+// bytes of one level-merge work-unit descriptor
+constexpr size_t kUnitDescBytes = 192;
+
 // A node executed by the level-merge kernels (more than T_max elements).
 // Children c = 0..d-1 cover runs [b[c], b[c+1]); b[0] and b[d] are the node's
 // delimiting boundaries (nearest boundaries of smaller power).
@@ -43,12 +49,12 @@ struct __align__(16) LevelNode {
     uint32_t sL, sR;          // element range of the node
     uint32_t unit_off;        // first work unit of this node (per level)
     uint32_t nunits;          // number of work units
-    uint32_t b[9];            // child boundaries (run indices)
+    uint32_t b[kMaxFanIn + 1];  // child boundaries (run indices)
     uint8_t power, depth, degree, pad;
     uint32_t split_off;       // first splitter of this node (per level)
     uint32_t nsplit;          // number of splitters
 };
-static_assert(sizeof(LevelNode) == 64, "LevelNode layout");
+static_assert(sizeof(LevelNode) == 96, "LevelNode layout");
 
 struct WsView {
     uint64_t n;                    // keys being sorted (all arrays of a batch)

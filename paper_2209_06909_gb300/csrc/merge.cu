@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(kFusedThreads)
                 const uint32_t v = blc[e];
                 if (be_pow(v) == p) {
                     uint32_t q = 1;
-                    while (q < 8u && e >= q && be_pow(blc[e - q]) == p) q++;
+                    while (q < (uint32_t)kMaxFanIn && e >= q && be_pow(blc[e - q]) == p) q++;
                     const uint32_t rd = min((uint32_t)__ffs(q) - 1u, T - 1u);
                     blc[e] = (v & 0x00FFFFFFu) | (rd << 24);
                     rmask |= 1u << rd;
@@ -635,17 +635,18 @@ __global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict
 }
 
 // One work unit of a level: a contiguous slice of each child of one node
-// (128 bytes, copied to shared memory with cp.async one unit ahead).
+// (192 bytes, read into shared memory one unit ahead).
 struct __align__(16) UnitDesc {
-    uint32_t out_base;     // first output element
-    uint32_t total;        // elements in the unit
-    uint32_t d;            // number of children
-    uint32_t flags;        // bit c: slice c is a leaf; bit 8+c: read backwards; bit 31: odd depth
-    uint32_t off[9];       // slice offsets in shared memory (off[d] = total)
-    uint32_t src[8];       // element of the slice's source that lands at off[c]
+    uint32_t out_base;               // first output element
+    uint32_t total;                  // elements in the unit
+    uint32_t d;                      // bits 0..7: number of children; bit 31: odd depth
+    uint32_t flags;                  // bit c: slice c is a leaf; bit 16+c: read backwards
+    uint32_t off[kMaxFanIn + 1];     // slice offsets in shared memory (off[d] = total)
+    uint32_t src[kMaxFanIn];         // element of the slice's source that lands at off[c]
     uint32_t pad[11];
 };
-static_assert(sizeof(UnitDesc) == 128, "UnitDesc layout");
+static_assert(sizeof(UnitDesc) == kUnitDescBytes, "UnitDesc layout");
+constexpr int kUnitDescVec = (int)(sizeof(UnitDesc) / 16);  // 16-byte words per descriptor
 
 // Splitter intervals are packed into work units greedily: walking a run of
 // consecutive intervals, a unit starts at the first interval of a node, at
@@ -774,7 +775,7 @@ __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict_
     if (v >= nn) {
         dev_fail(status, kDevUnitNode);
         UnitDesc Z;
-        for (int q = 0; q < 32; q++) reinterpret_cast<uint32_t*>(&Z)[q] = 0;
+        for (int q = 0; q < (int)(sizeof(UnitDesc) / 4); q++) reinterpret_cast<uint32_t*>(&Z)[q] = 0;
         out[u] = Z;
         continue;
     }
@@ -788,8 +789,8 @@ __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict_
     }
     const bool first = i0 == nd.unit_off, last = i1 == node_end;
     UnitDesc D;
-    uint32_t acc = 0, ob = nd.sL, flags = (nd.depth & 1u) << 31;
-    for (uint32_t c = 0; c < 8; c++) {
+    uint32_t acc = 0, ob = nd.sL, flags = 0;
+    for (uint32_t c = 0; c < (uint32_t)kMaxFanIn; c++) {
         if (c < d) {
             const uint32_t a = nd.b[c], b = nd.b[c + 1];
             const uint32_t base = rs[a], len = rs[b] - base;
@@ -798,7 +799,7 @@ __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict_
             const uint32_t leaf = (b == a + 1);
             const uint32_t rev = leaf ? rdesc[a] : 0u;
             D.src[c] = rev ? base + len - 1 - st : base + st;
-            flags |= (leaf << c) | (rev << (8 + c));
+            flags |= (leaf << c) | (rev << (16 + c));
             D.off[c] = acc;
             acc += en - st;
             ob += st;
@@ -807,10 +808,10 @@ __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict_
             D.off[c] = acc;
         }
     }
-    D.off[8] = acc;
+    D.off[kMaxFanIn] = acc;
     D.out_base = ob;
     D.total = acc;
-    D.d = d;
+    D.d = d | ((nd.depth & 1u) << 31);
     D.flags = flags;
     for (int q = 0; q < 11; q++) D.pad[q] = 0;
     out[u] = D;
@@ -818,7 +819,10 @@ __global__ void __launch_bounds__(256) k_level_desc(const LevelNode* __restrict_
 }
 
 constexpr int kLvlThreads = 256;
-constexpr uint32_t kLvlPad = 64;  // elements of slack per level-merge buffer
+// elements of slack per level-merge buffer: each of up to kMaxFanIn slices
+// starts on its source's 16-byte grid and ends rounded up to it (at most 6
+// elements of gap per slice for 4-byte keys), plus the output shift
+constexpr uint32_t kLvlPad = 128;
 
 // Block-wide copy of src[0..total) (shared memory) to dst[0..total) (global),
 // where src + q and dst + q share their offset within 16 bytes (src sits
@@ -934,7 +938,7 @@ __global__ void __launch_bounds__(kLvlThreads)
     uint32_t* vLa = V ? reinterpret_cast<uint32_t*>(Lb + CP) : nullptr;
     uint32_t* vLb = V ? vLa + CP : nullptr;
     __shared__ UnitDesc ring[2];
-    __shared__ uint32_t s_pos[8];
+    __shared__ uint32_t s_pos[kMaxFanIn];
     __shared__ __align__(8) uint64_t s_bar;
     uint32_t phase = 0;
     if (threadIdx.x == 0) mbar_init(&s_bar, 1);
@@ -943,23 +947,23 @@ __global__ void __launch_bounds__(kLvlThreads)
     const uint32_t per = (total_units + gridDim.x - 1) / gridDim.x;
     const uint32_t u0 = blockIdx.x * per;
     const uint32_t u1 = min(total_units, u0 + per);
-    if (u0 < u1 && threadIdx.x < 8)
+    if (u0 < u1 && threadIdx.x < kUnitDescVec)
         reinterpret_cast<uint4*>(&ring[0])[threadIdx.x] = reinterpret_cast<const uint4*>(udesc + u0)[threadIdx.x];
     for (uint32_t u = u0; u < u1; u++) {
         const UnitDesc& D = ring[(u - u0) & 1];
         // the next unit's descriptor is read while this unit is merged
         uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
-        if (u + 1 < u1 && threadIdx.x < 8) nxt = reinterpret_cast<const uint4*>(udesc + u + 1)[threadIdx.x];
+        if (u + 1 < u1 && threadIdx.x < kUnitDescVec) nxt = reinterpret_cast<const uint4*>(udesc + u + 1)[threadIdx.x];
         __syncthreads();
-        const uint32_t total = D.total, d = D.d;
+        const uint32_t total = D.total, d = D.d & 0xFFu;
         if (total > C) {
             if (threadIdx.x == 0) dev_fail(status, kDevRange);
             return;
         }
-        bool bad = d > 8 || (uint64_t)D.out_base + total > n;
+        bool bad = d > (uint32_t)kMaxFanIn || (uint64_t)D.out_base + total > n;
         for (uint32_t c = 0; c < d && !bad; c++) {
             const uint32_t m0 = D.off[c + 1] - D.off[c];
-            const bool rv = (D.flags >> (8 + c)) & 1u;
+            const bool rv = (D.flags >> (16 + c)) & 1u;
             bad = m0 > total || (rv ? (m0 > 0 && (D.src[c] >= n || D.src[c] + 1 < m0))
                                     : (uint64_t)D.src[c] + m0 > n);
         }
@@ -968,7 +972,7 @@ __global__ void __launch_bounds__(kLvlThreads)
             __syncthreads();
             continue;
         }
-        const bool odd = D.flags >> 31;
+        const bool odd = D.d >> 31;
         const K* inner = odd ? buf0 : buf1;                 // children sit at depth + 1
         const uint32_t* vinner = odd ? vbuf0 : vbuf1;
         constexpr uint32_t VK = 16 / sizeof(K);
@@ -980,7 +984,7 @@ __global__ void __launch_bounds__(kLvlThreads)
             uint32_t P = 0, tx = 0;
             for (uint32_t c = 0; c < d; c++) {
                 const uint32_t m = D.off[c + 1] - D.off[c];
-                const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (8 + c)) & 1u;
+                const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (16 + c)) & 1u;
                 const K* src = (lf ? leaf : inner) + D.src[c];
                 const uint32_t lead = rv ? 0u : (uint32_t)((reinterpret_cast<uintptr_t>(src) & 15u) / sizeof(K));
                 s_pos[c] = P + lead;
@@ -994,7 +998,7 @@ __global__ void __launch_bounds__(kLvlThreads)
             mbar_arrive_expect_tx(&s_bar, tx);
             for (uint32_t c = 0; c < d; c++) {
                 const uint32_t m = D.off[c + 1] - D.off[c];
-                const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (8 + c)) & 1u;
+                const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (16 + c)) & 1u;
                 if (rv) continue;
                 const K* src = (lf ? leaf : inner) + D.src[c];
                 const uint32_t lead = s_pos[c] % VK;
@@ -1006,7 +1010,7 @@ __global__ void __launch_bounds__(kLvlThreads)
         __syncthreads();
         for (uint32_t c = 0; c < d; c++) {
             const uint32_t m = D.off[c + 1] - D.off[c], s0 = D.src[c], pc = s_pos[c];
-            const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (8 + c)) & 1u;
+            const bool lf = (D.flags >> c) & 1u, rv = (D.flags >> (16 + c)) & 1u;
             const K* srck = lf ? leaf : inner;
             const uint32_t* srcv = lf ? vleaf : vinner;
             if (rv) {
@@ -1075,7 +1079,7 @@ __global__ void __launch_bounds__(kLvlThreads)
                 if (V) vout[ob + q] = vcur[q];
             }
         }
-        if (u + 1 < u1 && threadIdx.x < 8) reinterpret_cast<uint4*>(&ring[(u + 1 - u0) & 1])[threadIdx.x] = nxt;
+        if (u + 1 < u1 && threadIdx.x < kUnitDescVec) reinterpret_cast<uint4*>(&ring[(u + 1 - u0) & 1])[threadIdx.x] = nxt;
         __syncthreads();
     }
 }

@@ -336,7 +336,7 @@ extern "C" {
 
 mps_status mps_queue_create(const mps_queue_config* cfg, mps_queue** out) {
     if (!cfg || !out || !cfg->d_pool || !cfg->pool_bytes) return MPS_ERR_INVALID_ARG;
-    if (cfg->k != 0 && cfg->k != 2 && cfg->k != 4 && cfg->k != 8) return MPS_ERR_UNSUPPORTED;
+    if (cfg->k != 0 && cfg->k != 2 && cfg->k != 4 && cfg->k != 8 && cfg->k != 16) return MPS_ERR_UNSUPPORTED;
     mps_queue* q = new mps_queue();
     q->cfg = *cfg;
     if (!q->cfg.max_inflight) q->cfg.max_inflight = 2;

@@ -464,7 +464,7 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
     uint32_t w = 0;
     while ((1ull << w) < n) w++;
     uint64_t magic = ~0ull / (2 * n);
-    uint32_t log2k = k == 2 ? 1 : (k == 4 ? 2 : 3);
+    const uint32_t log2k = (uint32_t)__builtin_ctz((unsigned)k);
     uint32_t threads = 256;
     uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(ceil_div((uint64_t)r + 1, 16), threads), 152 * 16);
     if (ws.batch_off) {
@@ -478,9 +478,9 @@ void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t
     k_powers<L2, B><<<blocks, threads, 0, st>>>(ws.run_starts, ws.counters, n, w, magic, ws.batch_off, ws.batch_m,  \
                                                 ws.batch_prm, ws.powers, bits)
     if (ws.batch_off) {
-        if (log2k == 1) MPS_POWERS(1, true); else if (log2k == 2) MPS_POWERS(2, true); else MPS_POWERS(3, true);
+        if (log2k == 1) MPS_POWERS(1, true); else if (log2k == 2) MPS_POWERS(2, true); else if (log2k == 3) MPS_POWERS(3, true); else MPS_POWERS(4, true);
     } else {
-        if (log2k == 1) MPS_POWERS(1, false); else if (log2k == 2) MPS_POWERS(2, false); else MPS_POWERS(3, false);
+        if (log2k == 1) MPS_POWERS(1, false); else if (log2k == 2) MPS_POWERS(2, false); else if (log2k == 3) MPS_POWERS(3, false); else MPS_POWERS(4, false);
     }
 #undef MPS_POWERS
     g_launches += 1;

@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_mask_apply(const uint8_t* _
 
 struct NodeShape {
     uint32_t L, R, d;
-    uint32_t b[9];
+    uint32_t b[kMaxFanIn + 1];
 };
 
 __device__ __forceinline__ bool node_shape(const MinTree& T, const uint8_t* P, uint32_t j, uint32_t v, int k,
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tm
                     LevelNode nd;
                     nd.sL = sL; nd.sR = sR; nd.unit_off = 0; nd.nunits = 0;
 #pragma unroll
-                    for (int c = 0; c < 9; c++) nd.b[c] = c <= (int)s.d ? s.b[c] : 0u;
+                    for (int c = 0; c <= kMaxFanIn; c++) nd.b[c] = c <= (int)s.d ? s.b[c] : 0u;
                     nd.power = (uint8_t)v; nd.depth = (uint8_t)depth; nd.degree = (uint8_t)s.d; nd.pad = 0;
                     nd.split_off = nd.nsplit = 0;
                     nodes_raw[slot] = nd;
@@ -736,7 +736,7 @@ void launch_masks(uint32_t r_bound, bool dump_leaf, uint8_t* leaf_depth, uint64_
     const uint32_t grid = std::min<uint32_t>(tiles, 152 * 32);
     k_mask_reduce<<<grid, kMaskThreads, 0, st>>>(ws.powers, ws.counters, ws.mt_f, ws.mt_g);
     k_mask_scan<<<1, 1024, 0, st>>>(ws.mt_f, ws.mt_g, ws.counters, ws.mt_fpre, ws.mt_gsuf);
-    const uint32_t log2k = k == 2 ? 1u : (k == 4 ? 2u : 3u);
+    const uint32_t log2k = (uint32_t)__builtin_ctz((unsigned)k);
     if (ws.batch_cost)
         k_mask_apply<true><<<grid, kMaskThreads, 0, st>>>(
             ws.powers, ws.counters, ws.run_starts, ws.mt_fpre, ws.mt_gsuf, ws.node_info, dump_leaf ? leaf_depth : nullptr,

@@ -4,7 +4,7 @@ times (GPU): default workspace, k as timed, inputs from the same generators.
 The oracle's sort is O(n log r) C, so it runs whole at these sizes except for
 the 4096-array batch, where it sorts a sample of arrays and every array's
 tree is still checked through its merge cost:
-  * random permutation of 0..n-1 (n = 2^28, k = 4 and 2): the output is
+  * random permutation of 0..n-1 (n = 2^28, k = 4, 2, 8 and 16): the output is
     exactly 0..n-1; runs, powers, node table, leaf depths and merge cost equal
     the oracle's run scan and tree from run lengths;
   * geometric random runs (n = 2^28, mean 2^14, k = 4 and 2): keys and tree
@@ -54,7 +54,7 @@ def check_tree(t, a, k):
     assert t["num_levels"] == want["num_levels"] and t["merge_cost"] == want["merge_cost"]
 
 
-@pytest.mark.parametrize("k", [4, 2])
+@pytest.mark.parametrize("k", [4, 2, 8, 16])
 def test_permutation_2e28(k):
     a = inputs.random_permutation(N, 1000 + k)
     tb = mps.TreeBuffers.alloc(N, DEV)

@@ -52,13 +52,13 @@ def edge_arrays(m):
 
 
 @pytest.mark.parametrize("m", [2, 5, 24, 32])
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 def test_minrun_edges(k, m):
     for a in edge_arrays(m):
         check_minrun(a, k, m)
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 @pytest.mark.parametrize("m", [7, 24])
 def test_minrun_permutation(k, m):
     check_minrun(inputs.random_permutation(300007, seed=m + k), k, m)

@@ -56,36 +56,36 @@ def check_pairs(a: np.ndarray, k: int):
     assert np.array_equal(mps.to_numpy(ov, np.uint32), want["vals"])
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 @pytest.mark.parametrize("n", [2, 3, 17, 1000, 4097, 65536 + 123, 300001])
 def test_random_runs_uniform(n, k):
     check_keys_and_tree(inputs.random_runs_uniform_len(n, seed=n + k, hi=min(2000, max(2, n // 8))), k)
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 def test_config1_shape_full(k):
     """n = 2^20 uint32, run lengths U[1, 2000], half strictly descending."""
     check_keys_and_tree(inputs.random_runs_uniform_len(1 << 20, seed=11), k)
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 @pytest.mark.parametrize("n", [5000, 100003, 1 << 20])
 def test_permutation(n, k):
     check_keys_and_tree(inputs.random_permutation(n, seed=n % 97 + k), k)
 
 
-@pytest.mark.parametrize("k", [2, 4])
+@pytest.mark.parametrize("k", [2, 4, 16])
 @pytest.mark.parametrize("mean", [3.0, 64.0, 4096.0])
 def test_geometric_runs(mean, k):
     check_keys_and_tree(inputs.random_runs_geometric(400000, seed=int(mean) + k, mean=mean), k)
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 def test_u64_keys_duplicates(k):
     check_keys_and_tree(inputs.random_runs_loguniform(200000, seed=3 + k, log2_hi=12.0, distinct=1 << 10), k)
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
 def test_pairs_stable(k, dtype):
     a = inputs.random_runs_loguniform(150001, seed=5 + k, log2_hi=11.0, distinct=300, dtype=dtype)
@@ -111,7 +111,7 @@ def edge_arrays():
     yield "two_runs", np.concatenate([np.arange(70000), np.arange(70000)]).astype(np.uint32)
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 def test_edge_cases(k):
     for name, a in edge_arrays():
         check_keys_and_tree(a, k)
@@ -176,7 +176,7 @@ def test_argument_errors():
     assert e.value.code == 1
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 def test_sort_in_place(k):
     """d_keys_out == d_keys_in (and payloads in place): the same result as the oracle."""
     a = inputs.random_runs_uniform_len(300001, seed=21 + k, hi=2000)

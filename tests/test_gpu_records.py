@@ -34,7 +34,7 @@ def check_records(a: np.ndarray, k: int, seed: int = 1):
     assert np.array_equal(mps.to_numpy(ov, np.uint64), vals[want["vals"]])
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 @pytest.mark.parametrize("n", [1, 2, 17, 1000, 100003, 1 << 20])
 def test_records_geometric_sqrt_n(n, k):
     mean = max(1.0, float(np.sqrt(n)))

@@ -129,7 +129,7 @@ def test_fig3_single_boundary():
 
 # ------------------------------------------------------------ powers ---
 
-@pytest.mark.parametrize("k", [2, 3, 4, 8])
+@pytest.mark.parametrize("k", [2, 3, 4, 8, 16])
 def test_powers_exhaustive_small_against_def31(k):
     """Every composition of n <= 11 into runs: oracle powers == Def. 3.1."""
     for n in range(2, 12):
@@ -149,7 +149,7 @@ def test_powers_exhaustive_small_against_def31(k):
                 assert got[i] == power_def31(L, i, k), (L, i, k)
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 def test_powers_random_against_def31(k):
     rng = random.Random(7 + k)
     for _ in range(40):
@@ -160,21 +160,24 @@ def test_powers_random_against_def31(k):
 
 
 def test_squish_identity():
-    """Sec. 3.1: P4 = floor((P2 - 1)/2) + 1; likewise P8 = ceil(P2 / 3)."""
+    """Sec. 3.1: P4 = floor((P2 - 1)/2) + 1; likewise P8 = ceil(P2 / 3) and
+    P16 = ceil(P2 / 4)."""
     rng = np.random.default_rng(3)
     for _ in range(30):
         L = rng.integers(1, 3000, rng.integers(2, 400))
         p2 = oracle.tree_from_lengths(L, 2)["powers"][1:L.size].astype(int)
         p4 = oracle.tree_from_lengths(L, 4)["powers"][1:L.size].astype(int)
         p8 = oracle.tree_from_lengths(L, 8)["powers"][1:L.size].astype(int)
+        p16 = oracle.tree_from_lengths(L, 16)["powers"][1:L.size].astype(int)
         assert np.array_equal(p4, (p2 - 1) // 2 + 1)
         assert np.array_equal(p8, -(-p2 // 3))
+        assert np.array_equal(p16, -(-p2 // 4))
 
 
 def test_power_range_bound():
     """1 <= P_i <= ceil(log_k n + 1) (Sec. 3.3, proof of the stack bound)."""
     rng = np.random.default_rng(11)
-    for k in (2, 4, 8):
+    for k in (2, 4, 8, 16):
         for _ in range(20):
             L = rng.integers(1, 100000, rng.integers(2, 300))
             n = int(L.sum())
@@ -214,7 +217,7 @@ def test_run_detection_edge_cases():
 
 # -------------------------------------------------------------- trees ---
 
-@pytest.mark.parametrize("k", [2, 3, 4, 8])
+@pytest.mark.parametrize("k", [2, 3, 4, 8, 16])
 def test_stack_tree_equals_kway_tree(k):
     """Alg. 2 (with the power-rule final collapse) builds Alg. 1's tree: the
     oracle's stack builder, its recursive builder and a Python Alg. 1 agree."""
@@ -237,7 +240,7 @@ def test_tree_invariants():
     """Degree in [2, k], Fact 3.2 depth(m(B_j)) <= P_j - 1, node_first
     consistency, and M = sum d_i L_i."""
     rng = np.random.default_rng(5)
-    for k in (2, 4, 8):
+    for k in (2, 4, 8, 16):
         for _ in range(40):
             L = rng.integers(1, 500, int(rng.integers(2, 200)))
             t = oracle.tree_from_lengths(L, k)
@@ -308,7 +311,7 @@ def test_table1_merge_cost_statistical():
 
 # ------------------------------------------------------------ sorting ---
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 def test_sort_keys_closed_form(k):
     gens = [
         lambda s: inputs.random_runs_uniform_len(5000, s, hi=200),
@@ -327,7 +330,7 @@ def test_sort_keys_closed_form(k):
         assert np.array_equal(t["nodes"], res["nodes"]) and t["merge_cost"] == res["merge_cost"]
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 def test_sort_pairs_is_stable(k):
     """Payload = original index: output must equal the lexicographic order of
     (key, index), the unique stable sort."""

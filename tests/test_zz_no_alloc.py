@@ -36,7 +36,7 @@ def _noalloc(L, d_in, d_out, k):
     return L.mps_sort_keys_noalloc(d_in.data_ptr(), d_out.data_ptr(), d_in.numel(), kt, k, stream)
 
 
-@pytest.mark.parametrize("k", [2, 4, 8])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
 def test_noalloc_matches_sort_keys_two_calls(L, k):
     arrays = [inputs.random_permutation(mps.NOALLOC_MAX_N, seed=21 + k),
               inputs.random_runs_uniform_len(300001, seed=22 + k, hi=700),
