@@ -103,6 +103,8 @@ def _load():
         lib.mpso_tree_from_lengths.restype = ctypes.c_int
         lib.mpso_merge_cost_tail.argtypes = [P, U64, ctypes.c_uint32, ctypes.c_int, P]
         lib.mpso_merge_cost_tail.restype = ctypes.c_int
+        lib.mpso_tree_tail.argtypes = [P, U64, ctypes.c_uint32, ctypes.c_int, P, P, P, P]
+        lib.mpso_tree_tail.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -222,3 +224,22 @@ def merge_cost_tail(lengths, k, policy):
     out = np.zeros(1, np.uint64)
     _check(_load().mpso_merge_cost_tail(_ptr(ln), ln.size, k, TAIL_POLICIES[policy], _ptr(out)))
     return int(out[0])
+
+
+def tree_tail(lengths, k, policy):
+    """The full tree of Alg. 2's run stack on run lengths alone, with the stack
+    left after the last run emptied by ``policy`` (as in ``merge_cost_tail``).
+    Same outputs as ``tree_from_lengths`` minus the powers; a node made by the
+    final collapse of "alg2_pop_k_minus_1" or "merge_down" carries the smallest
+    power among its boundaries."""
+    ln = np.ascontiguousarray(lengths, dtype=np.uint64)
+    r = ln.size
+    m = max(r, 1)
+    nodes = np.zeros(m, NODE_DTYPE)
+    nf = np.zeros(m + 1, np.uint32)
+    ld = np.zeros(m + 1, np.uint8)
+    counts = np.zeros(4, np.uint64)
+    _check(_load().mpso_tree_tail(_ptr(ln), r, k, TAIL_POLICIES[policy], _ptr(nodes), _ptr(nf), _ptr(ld), _ptr(counts)))
+    nn = int(counts[1])
+    return {"nodes": nodes[:nn].copy(), "node_first": nf[:r].copy(), "leaf_depth": ld[:r].copy(), "r": r,
+            "num_nodes": nn, "merge_cost": int(counts[3])}

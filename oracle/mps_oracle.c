@@ -512,6 +512,94 @@ out:
 }
 
 /* ------------------------------------------------------------------------- */
+/* Final-collapse variants: the full tree.                                    */
+/* ------------------------------------------------------------------------- */
+
+/* Pops exactly cnt stack entries, whatever their powers, and merges them with
+ * the current segment *cur into one node (the last loop of Alg. 2 and the
+ * appendix's merge_down pop by count, not by power).  The node's power label
+ * is the smallest power among its boundaries, which is the power of the
+ * lowest popped entry (powers never decrease up the stack). */
+static int collapse_count(stack_entry* st, uint64_t* sp, stack_entry* cur, raw_tree* t, uint64_t cnt, uint32_t k) {
+    if (cnt == 0 || cnt > *sp || cnt + 1 > k || cnt + 1 > 64) return MPSO_ERR_INVARIANT;
+    *sp -= cnt;
+    const uint64_t id = t->count++;
+    raw_node* nv = &t->v[id];
+    nv->first_run = st[*sp].first_run;
+    nv->end_run = cur->end_run;
+    nv->power = st[*sp].power;
+    nv->degree = (uint32_t)cnt + 1;
+    nv->parent = -1;
+    nv->min_boundary = st[*sp].boundary;
+    for (uint64_t c = 0; c < cnt; c++) {
+        const stack_entry* ch = &st[*sp + c];
+        t->boundary_node[ch->boundary] = (int64_t)id;
+        if (ch->node >= 0) t->v[ch->node].parent = (int64_t)id;
+        else t->leaf_parent[ch->first_run] = (int64_t)id;
+    }
+    if (cur->node >= 0) t->v[cur->node].parent = (int64_t)id;
+    else t->leaf_parent[cur->first_run] = (int64_t)id;
+    cur->b = st[*sp].b;
+    cur->first_run = st[*sp].first_run;
+    cur->node = (int64_t)id;
+    return MPSO_OK;
+}
+
+/*
+ * The tree that Alg. 2's run stack builds on run lengths alone when the stack
+ * left after the last run is emptied by `policy` (0, 1 or 2 as for
+ * mpso_merge_cost_tail below); the main loop is Alg. 2's in all three.  The
+ * nodes made by the main loop carry the power of their boundaries; a node of
+ * the final collapse under policy 1 or 2 carries the smallest power among its
+ * boundaries (its children need not share one).  Outputs as for
+ * mpso_tree_from_lengths (canonical order (power label, first run)).
+ */
+int mpso_tree_tail(const uint64_t* lengths, uint64_t r, uint32_t k, int policy,
+                   mpso_node* nodes, uint32_t* node_first, uint8_t* leaf_depth, uint64_t* counts) {
+    if (k < 2 || policy < 0 || policy > 2) return MPSO_ERR_ARG;
+    uint32_t* starts = (uint32_t*)malloc((r + 1) * sizeof(uint32_t));
+    uint8_t* pw = (uint8_t*)calloc(r + 1, 1);
+    stack_entry* st = (stack_entry*)malloc((64 * (uint64_t)k + 8) * sizeof(stack_entry));
+    raw_tree t;
+    int rc = raw_tree_init(&t, r);
+    if (!starts || !pw || !st || rc != MPSO_OK) { rc = MPSO_ERR_NOMEM; goto out; }
+    mpso_powers_from_lengths(lengths, r, k, pw, starts);
+    uint64_t sp = 0;
+    if (r > 0) {
+        stack_entry cur = {starts[0], starts[1], 0, 1, -1, 0, 0};
+        for (uint64_t i = 1; i < r; i++) {
+            const uint32_t P = pw[i];
+            while (sp > 0 && st[sp - 1].power > P)
+                if ((rc = collapse_top(st, &sp, &cur, &t, NULL, NULL, NULL, NULL, k)) != MPSO_OK) goto out;
+            cur.power = P;
+            cur.boundary = (uint32_t)i;
+            if (sp >= 64 * (uint64_t)k + 8) { rc = MPSO_ERR_INVARIANT; goto out; }
+            st[sp++] = cur;
+            stack_entry nxt = {starts[i], starts[i + 1], (uint32_t)i, (uint32_t)i + 1, -1, 0, 0};
+            cur = nxt;
+        }
+        if (policy == 0) {
+            while (sp > 0)
+                if ((rc = collapse_top(st, &sp, &cur, &t, NULL, NULL, NULL, NULL, k)) != MPSO_OK) goto out;
+        } else {
+            /* policy 2 first merges x = (entries) mod (k - 1) entries, so that
+             * every later node has k children; policy 1 takes k - 1 each time */
+            const uint64_t x = policy == 2 ? sp % (k - 1) : 0;
+            if (x > 0 && (rc = collapse_count(st, &sp, &cur, &t, x, k)) != MPSO_OK) goto out;
+            while (sp > 0) {
+                const uint64_t cnt = sp < (uint64_t)(k - 1) ? sp : (uint64_t)(k - 1);
+                if ((rc = collapse_count(st, &sp, &cur, &t, cnt, k)) != MPSO_OK) goto out;
+            }
+        }
+    }
+    rc = emit_canonical(&t, starts, r, nodes, node_first, leaf_depth, counts);
+out:
+    free(starts); free(pw); free(st);
+    raw_tree_free(&t);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Final-collapse variants (merge cost only).                                 */
 /* ------------------------------------------------------------------------- */
 

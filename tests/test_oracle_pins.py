@@ -542,3 +542,53 @@ def test_tail_policies_hand_derived(lengths, pw, want):
         assert oracle.merge_cost_tail(list(lengths), 4, policy) == m, policy
     # the KwayTree tail is Alg. 1's tree: its merge cost from the canonical tree
     assert oracle.tree_from_lengths(np.array(lengths), 4)["merge_cost"] == want["kway_tree"]
+
+
+# The trees of the same three inputs, node by node (first run, end run,
+# degree), from the merge sequences written out above.
+TAIL_SHAPES = [
+    {"kway_tree": {(3, 5, 2), (0, 5, 4)}, "alg2_pop_k_minus_1": {(1, 5, 4), (0, 5, 2)},
+     "merge_down": {(3, 5, 2), (0, 5, 4)}},
+    {"kway_tree": {(3, 6, 3), (0, 6, 4)}, "alg2_pop_k_minus_1": {(2, 6, 4), (0, 6, 3)},
+     "merge_down": {(3, 6, 3), (0, 6, 4)}},
+    {"kway_tree": {(1, 5, 4), (0, 5, 2)}, "alg2_pop_k_minus_1": {(1, 5, 4), (0, 5, 2)},
+     "merge_down": {(3, 5, 2), (0, 5, 4)}},
+]
+
+
+def _shape(nodes):
+    return {(int(x["first_run"]), int(x["end_run"]), int(x["degree"])) for x in nodes}
+
+
+@pytest.mark.parametrize("case", range(len(TAIL_CASES)))
+def test_tail_trees_hand_derived(case):
+    lengths, _, want = TAIL_CASES[case]
+    for policy, shape in TAIL_SHAPES[case].items():
+        t = oracle.tree_tail(np.array(lengths), 4, policy)
+        assert _shape(t["nodes"]) == shape, policy
+        assert t["merge_cost"] == want[policy], policy
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 8, 16])
+def test_tail_trees_against_cost_loop(k):
+    """The tree builder's merge cost (sum of node sizes, cross-checked inside
+    against sum_i depth_i L_i) equals the separate cost-only loop for every
+    policy; policy "kway_tree" is Alg. 1's tree node for node; the nodes made
+    before the last run (end run < r) are the same under every policy, and a
+    final-collapse node has at most k children."""
+    rng = np.random.default_rng(90 + k)
+    for _ in range(150):
+        L = _random_lengths(rng, int(rng.integers(1, 120)), int(rng.choice([3, 50, 2000])))
+        r = L.size
+        base = oracle.tree_from_lengths(L, k)
+        main = {x for x in _shape(base["nodes"]) if x[1] < r}
+        for policy in oracle.TAIL_POLICIES:
+            t = oracle.tree_tail(L, k, policy)
+            assert t["merge_cost"] == oracle.merge_cost_tail(L, k, policy), policy
+            sh = _shape(t["nodes"])
+            assert {x for x in sh if x[1] < r} == main
+            assert all(2 <= x[2] <= k for x in sh)
+            if policy == "kway_tree":
+                assert np.array_equal(t["nodes"], base["nodes"])
+                assert np.array_equal(t["leaf_depth"], base["leaf_depth"])
+                assert np.array_equal(t["node_first"], base["node_first"])
