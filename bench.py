@@ -141,9 +141,10 @@ def job_value(n_per_rank: int, world: int, ms: float) -> float:
     return world * n_per_rank / (ms * 1e-3) / 1e9
 
 
-def time_sorts(mps, torch, d_in, d_out, ws, k, steps, warmup, stream, barrier=None):
+def time_sorts(mps, torch, d_in, d_out, ws, k, steps, warmup, stream, barrier=None, sort=None):
+    sort = sort or (lambda: mps.sort_keys(d_in, k=k, out=d_out, ws=ws, stream=stream))
     for _ in range(warmup):
-        mps.sort_keys(d_in, k=k, out=d_out, ws=ws, stream=stream)
+        sort()
     torch.cuda.synchronize()
     if barrier:
         barrier()
@@ -152,7 +153,7 @@ def time_sorts(mps, torch, d_in, d_out, ws, k, steps, warmup, stream, barrier=No
     torch.cuda.synchronize()
     start.record(stream)
     for _ in range(steps):
-        mps.sort_keys(d_in, k=k, out=d_out, ws=ws, stream=stream)
+        sort()
     end.record(stream)
     torch.cuda.synchronize()
     if barrier:
@@ -614,6 +615,19 @@ def run_mps(args):
                                  "runs": st["r"], "merge_cost_per_n": st["merge_cost"] / n, "levels": st["num_levels"],
                                  "sort_roofline": sort_frac(b, n, st["merge_cost"], vms, peaks)})
                 del wmr
+            # final-collapse variants of Alg. 2 (the printed last loop and the
+            # appendix's merge_down), k = 4
+            for kind, dsrc in (("perm", d_in), ("runs", d_runs)):
+                for policy in ("alg2_pop_k_minus_1", "merge_down"):
+                    vms = time_sorts(mps, torch, dsrc, d_out, ws, k, 8, 3, stream,
+                                     sort=lambda: mps.sort_keys_tail(dsrc, policy, k=k, out=d_out, ws=ws, stream=stream))
+                    st = mps.last_stats()
+                    if kind == "perm":
+                        assert torch.equal(d_out, torch.arange(n, dtype=torch.int32, device=dev))
+                    variants.append({"input": ("random permutation" if kind == "perm" else "geometric runs, mean 2^14")
+                                     + ", final collapse " + policy, "k": k, "ms": vms,
+                                     "gkeys_s": n / (vms * 1e-3) / 1e9, "merge_cost_per_n": st["merge_cost"] / n,
+                                     "sort_roofline": sort_frac(b, n, st["merge_cost"], vms, peaks)})
             line["variants"] = variants
             del d_runs, ws_k
         del d_tmp

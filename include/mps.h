@@ -140,6 +140,27 @@ mps_status mps_sort_pairs_minrun(const void* d_keys_in, const uint32_t* d_vals_i
                                  uint32_t* d_vals_out, uint64_t n, mps_key_type kt, int k, uint32_t min_run_len,
                                  void* d_ws, size_t ws_bytes, const mps_tree* opt_tree, cudaStream_t stream);
 
+/* Multiway Powersort whose run stack is emptied after the last run by a
+ * policy other than the power rule (Alg. 2's main loop is unchanged):
+ *   tail_policy 0: the power rule against a final power 0 -- Alg. 1's tree,
+ *                  exactly mps_sort_keys;
+ *   tail_policy 1: Alg. 2's last loop as printed: pop up to k-1 stack entries
+ *                  per merge with the current run;
+ *   tail_policy 2: the appendix's merge_down (written for k = 4, here for any
+ *                  k): first merge the top (entries mod (k-1)) entries with the
+ *                  current run, then k-1 entries per merge.
+ * For k = 2 the three build the same tree.  The sorted keys are those of
+ * mps_sort_keys; the tree (opt_tree: node table, node_first, leaf depths,
+ * counts with the merge cost M of Sec. 2.2) is the policy's.  opt_tree->powers
+ * receives the powers of Def. 3.1; the node table's power field holds the
+ * labels the tree was built from: each final-collapse node is numbered from
+ * the root (1, 2, ...) and every other power is raised by the number of
+ * final-collapse nodes.  Workspace: mps_workspace_size(n, kt, 0, k).  Device
+ * status 20 if the relabelled powers would exceed 32 (n near 2^31 at k = 4).
+ * tail_policy outside 0..2: MPS_ERR_INVALID_ARG. */
+mps_status mps_sort_keys_tail(const void* d_keys_in, void* d_keys_out, uint64_t n, mps_key_type kt, int k, int tail_policy,
+                              void* d_ws, size_t ws_bytes, const mps_tree* opt_tree, cudaStream_t stream);
+
 /* Records (Sec. 5, "records" experiment: a long key and a pointer, 16 bytes):
  * stable sort of n keys each carrying a 64-bit payload.  The keys are sorted
  * with their input indices as uint32 payloads (as mps_sort_pairs), and every
@@ -325,7 +346,8 @@ mps_status mps_sync_status(const void* d_ws, cudaStream_t stream);
 
 /* Statistics of the most recent sort on this host thread (host memory).  For
  * a single-array sort the statistics live in its workspace on the device: this
- * call synchronises that sort's stream and reads them back. */
+ * call synchronises that sort's stream and reads them back, so that workspace
+ * must still be allocated, and not handed to another call, until then. */
 typedef struct {
     uint64_t n, r, merge_cost, frontier_nodes, hbm_nodes;
     uint32_t num_levels, hbm_levels;
@@ -337,7 +359,8 @@ typedef struct {
                                            bounded wait ran out (returned as MPS_ERR_TIMEOUT),
                                            18 a splitter ranked outside its node (unsorted child),
                                            19 a node above the fused-tile size at a power beyond
-                                           the levels queued for it */
+                                           the levels queued for it, 20 final-collapse relabelling
+                                           out of range (mps_sort_keys_tail) */
     uint32_t pad;
 } mps_stats;
 

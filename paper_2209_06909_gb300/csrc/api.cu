@@ -56,7 +56,8 @@ struct Plan {
     int nlv_max = 0;
     // offsets
     size_t o_ctr, o_lvloff, o_det_state, o_rs, o_rdesc, o_fused, o_canon, o_lv[kMinTreeLevels], o_info,
-        o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_ufirst, o_ptiles, o_isz, o_hist, o_ktmp, o_vtmp, o_incopy, total;
+        o_mt, o_nodes_raw, o_nodes_lvl, o_unit_node, o_split, o_udesc, o_ufirst, o_ptiles, o_isz, o_hist, o_tail, o_ktmp, o_vtmp,
+        o_incopy, total;
 
     uint32_t m = 0;  // arrays of a batch (0: a single array)
     size_t o_bprm = 0;
@@ -104,6 +105,7 @@ struct Plan {
         o_ptiles = take((size_t)(unit_cap / kPackTile + 2) * 4);
         o_isz = take((size_t)(unit_cap + 64) * 4);  // padded for 16-byte loads past the last interval
         o_hist = take(mask_tiles * kMaxLevels * 4);
+        o_tail = take(kTailCap * 4);
         o_bprm = take((size_t)2 * std::max<uint32_t>(m, 1) * 8);
         o_ktmp = take(n * kb);
         o_vtmp = vals ? take(n * 4) : o;
@@ -178,6 +180,7 @@ struct Plan {
         w.canon_idx = reinterpret_cast<uint32_t*>(b + o_canon);
         w.cand_cap = (uint32_t)(rmax + 1);
         w.hist = reinterpret_cast<uint32_t*>(b + o_hist);
+        w.tail_list = reinterpret_cast<uint32_t*>(b + o_tail);
         w.keys_tmp = b + o_ktmp;
         w.vals_tmp = vals ? reinterpret_cast<uint32_t*>(b + o_vtmp) : nullptr;
         w.batch_off = nullptr;
@@ -377,6 +380,15 @@ bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
 // each is shorter than 2 max_len / k^(v-1).  The node is therefore smaller
 // than 3 max_len / k^(v-1), and level merges exist only for powers v with
 // T_max k^(v-1) < 3 max_len; the bound below uses 4 max_len as margin.
+// Bound on the largest power of any boundary of an array of n elements:
+// P_k <= ceil(log_k n + 1) (Sec. 3.3), plus one as margin.
+int max_power_bound(uint64_t n, int k) {
+    int lg = 0;
+    while ((1ull << lg) < std::max<uint64_t>(n, 1)) lg++;
+    const int t = __builtin_ctz((unsigned)k);
+    return (lg + t - 1) / t + 2;
+}
+
 int level_power_bound(uint64_t max_len, int k, uint32_t tmax) {
     const uint64_t lim = 4 * std::max<uint64_t>(max_len, 1);
     uint64_t span = tmax;  // T_max * k^(v-1)
@@ -395,9 +407,12 @@ int level_power_bound(uint64_t max_len, int k, uint32_t tmax) {
 template <typename K, bool V>
 mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, uint64_t n, int k,
                      void* d_ws, size_t ws_bytes, const mps_tree* tree, bool move_keys, cudaStream_t st,
-                     uint32_t min_run = 1) {
+                     uint32_t min_run = 1, int tail = 0) {
     if (!fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
     if (min_run < 1 || min_run > kMaxMinRun) return MPS_ERR_UNSUPPORTED;
+    if (tail < 0 || tail > 2) return MPS_ERR_INVALID_ARG;
+    // for k = 2 every final-collapse node has one boundary: all policies build the same tree
+    const bool relabel = tail != 0 && k > 2;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
     const double b = (double)sizeof(K) + (V ? 4.0 : 0.0);
     g_launches = 0;
@@ -461,6 +476,11 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
         ProfScope ps("powers", 9.0, st, kBytesPerRun);
         launch_powers(n, r_bound, k, ws, st);
     }
+    if (relabel) {
+        // the stack's final collapse by count: relabelled powers, original ones to the tree output
+        ProfScope ps("tail_relabel", 0.0, st);
+        launch_tail(r_bound, k, tail, tree ? tree->powers : nullptr, ws, st);
+    }
     {
         ProfScope ps("tree_scans", 4.0, st, kBytesPerRun);
         launch_mintree(r_bound, ws, st);
@@ -479,7 +499,9 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
             launch_fused<K, V>(keys_in, vals_in, keys_out, vals_out, plan.fused_cap, g, ws, st);
         }
         const uint32_t nn_bound = (uint32_t)(n / g.tmax + 1);
-        for (int p = level_power_bound(n, k, g.tmax); p >= 1; p--) {
+        // relabelled powers rise by the number of final-collapse nodes, at most the largest power
+        const int ptop = level_power_bound(n, k, g.tmax) + (relabel ? max_power_bound(n, k) : 0);
+        for (int p = ptop; p >= 1; p--) {
             {
                 ProfScope ps("level_plan", 0.0, st);
                 launch_level_plan<K>(p, nn_bound, n, k, keys_in, keys_out, g, ws, st);
@@ -491,7 +513,7 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     if (tree) {
         if (tree->run_starts || tree->run_desc || tree->powers || tree->leaf_depth || tree->counts)
             launch_tree_arrays(r_bound, ws, min_run > 1 ? plan.min_run_view(d_ws).desc_nat : ws.run_desc, tree->run_starts,
-                               tree->run_desc, tree->powers, tree->leaf_depth, tree->counts, st);
+                               tree->run_desc, relabel ? nullptr : tree->powers, tree->leaf_depth, tree->counts, st);
         if (tree->node_first) launch_tree_dump(r_bound, k, ws, tree->node_first, tree->nodes, st);
     }
     MPS_CUDA(cudaGetLastError());
@@ -639,6 +661,17 @@ mps_status mps_sort_keys_minrun(const void* d_keys_in, void* d_keys_out, uint64_
     if (kt == MPS_U64)
         return sort_impl<uint64_t, false>((const uint64_t*)d_keys_in, nullptr, (uint64_t*)d_keys_out, nullptr, n, k, d_ws,
                                           ws_bytes, opt_tree, true, stream, min_run_len);
+    return MPS_ERR_INVALID_ARG;
+}
+
+mps_status mps_sort_keys_tail(const void* d_keys_in, void* d_keys_out, uint64_t n, mps_key_type kt, int k, int tail_policy,
+                              void* d_ws, size_t ws_bytes, const mps_tree* opt_tree, cudaStream_t stream) {
+    if (kt == MPS_U32)
+        return sort_impl<uint32_t, false>((const uint32_t*)d_keys_in, nullptr, (uint32_t*)d_keys_out, nullptr, n, k, d_ws,
+                                          ws_bytes, opt_tree, true, stream, 1u, tail_policy);
+    if (kt == MPS_U64)
+        return sort_impl<uint64_t, false>((const uint64_t*)d_keys_in, nullptr, (uint64_t*)d_keys_out, nullptr, n, k, d_ws,
+                                          ws_bytes, opt_tree, true, stream, 1u, tail_policy);
     return MPS_ERR_INVALID_ARG;
 }
 

@@ -24,6 +24,7 @@ enum DevError : uint32_t {
     kDevSpin = 17,       // a bounded wait on another block ran out
     kDevSplitSlot = 18,  // a splitter ranked outside its node's splitters (children not sorted)
     kDevLevelBound = 19, // a node larger than a fused tile at a power above the host's level bound
+    kDevTail = 20,       // final-collapse variant: too many stack boundaries, or relabelled powers above 32
 };
 
 __device__ __forceinline__ void dev_fail(uint32_t* status, uint32_t code) { atomicCAS(status, 0u, code); }

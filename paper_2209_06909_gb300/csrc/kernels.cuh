@@ -33,6 +33,8 @@ enum : int {
     kCtrDetTile = 205,  // next run-detection tile to take
     kCtrCand = 206,     // node-pass candidates listed by the mask pass
     kCtrMrGood = 207,   // minimum run length: good intervals (natural runs of >= m-1 interior flags)
+    kCtrTailCount = 208,  // final-collapse variant: boundaries left on the run stack after the last run
+    kCtrTailShift = 209,  // final-collapse variant: number of final-collapse nodes (added to every other power)
     kCtrWords = 256
 };
 
@@ -88,6 +90,7 @@ struct WsView {
                                    // node pass's candidate list (boundary indices)
     uint32_t cand_cap;             // entries of canon_idx
     uint32_t* hist;                // dump: per-tile power histograms
+    uint32_t* tail_list;           // final-collapse variant: boundaries left on the run stack (kTailCap)
     void* keys_tmp;
     uint32_t* vals_tmp;
     // batch of arrays laid end to end (nullptr for a single array)
@@ -141,6 +144,14 @@ extern thread_local uint64_t g_launches;
 // runs.cu
 template <typename K> void launch_detect(const K* keys, uint64_t n, const WsView& ws, cudaStream_t st);
 void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t st);
+
+// tail.cu: a final collapse other than the power rule (policy 1: Alg. 2's
+// last loop as printed, pop k-1 runs per merge; policy 2: the appendix's
+// merge_down) by relabelling ws.powers so that the power rule builds that
+// tree.  orig_powers, if given, receives the powers before relabelling (r+1
+// entries).  Sets ctr[kCtrTailShift].
+constexpr uint32_t kTailCap = 512;
+void launch_tail(uint32_t r_bound, int k, int policy, uint8_t* orig_powers, const WsView& ws, cudaStream_t st);
 
 // tree.cu
 void launch_mintree(uint32_t r, const WsView& ws, cudaStream_t st);

@@ -292,7 +292,9 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_mask_apply(const uint8_t* _
     for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const uint32_t b0 = tile * kMaskTile + threadIdx.x * kMaskItems;
     const bool live = b0 < nb;
-    const uint32_t vskip = small_power(n_single ? n_single : ctr[kCtrMaxLen], ctr[kCtrMaxRun], log2k, tmax);
+    // a final-collapse variant raised every power outside the final collapse by ctr[kCtrTailShift]
+    const uint32_t vskip = small_power(n_single ? n_single : ctr[kCtrMaxLen], ctr[kCtrMaxRun], log2k, tmax) +
+                           (uint32_t)ctr[kCtrTailShift];
     // powers[b0 .. b0+31] and rs[b0 .. b0+19] (both arrays are padded past r)
     uint32_t pw[8], rv[20];
     if (live) {
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__(256) k_node_pass(MinTree T, int k, uint32_t tm
             if (size > tmax) {
                 // level merges are queued for powers 1..vmax only (a node of
                 // power v is smaller than 3 n / k^(v-1)); anything else is a bug
-                if (v > vmax) dev_fail(status, kDevLevelBound);
+                if (v > vmax + (uint32_t)ctr[kCtrTailShift]) dev_fail(status, kDevLevelBound);
                 NodeShape s;
                 if (!node_shape(T, P, j, v, k, s)) dev_fail(status, kDevDegree);
                 uint32_t slot = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrHbmTotal), 1ull);

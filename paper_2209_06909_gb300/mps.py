@@ -75,7 +75,7 @@ EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_t
            "mps_batch_graph_create", "mps_batch_graph_launch", "mps_batch_graph_destroy",
            "mps_queue_create", "mps_queue_submit", "mps_queue_poll", "mps_queue_wait", "mps_queue_pause",
            "mps_queue_destroy", "mps_records_workspace_size", "mps_sort_records", "mps_sync_status",
-           "mps_workspace_size_minrun", "mps_sort_keys_minrun", "mps_sort_pairs_minrun"]
+           "mps_workspace_size_minrun", "mps_sort_keys_minrun", "mps_sort_pairs_minrun", "mps_sort_keys_tail"]
 
 # Largest n accepted by mps_sort_keys_noalloc (its scratch is compiled into the library).
 NOALLOC_MAX_N = 1 << 20
@@ -107,6 +107,8 @@ def lib():
     L.mps_workspace_size_minrun.argtypes = [U64, I, I, I, ctypes.c_uint32, ctypes.POINTER(ctypes.c_size_t)]
     L.mps_sort_keys_minrun.argtypes = [P, P, U64, I, I, ctypes.c_uint32, P, ctypes.c_size_t, P, P]
     L.mps_sort_pairs_minrun.argtypes = [P, P, P, P, U64, I, I, ctypes.c_uint32, P, ctypes.c_size_t, P, P]
+    L.mps_sort_keys_tail.argtypes = [P, P, U64, I, I, I, P, ctypes.c_size_t, P, P]
+    L.mps_sort_keys_tail.restype = I
     for fn in ("mps_workspace_size_minrun", "mps_sort_keys_minrun", "mps_sort_pairs_minrun"):
         getattr(L, fn).restype = I
     L.mps_sort_keys_noalloc.argtypes = [P, P, U64, I, I, P]
@@ -233,6 +235,7 @@ def sort_keys(keys: torch.Tensor, k: int = 4, out: torch.Tensor | None = None, w
     ts = ctypes.byref(tree.struct()) if tree is not None else None
     _check("mps_sort_keys", lib().mps_sort_keys(keys.data_ptr(), out.data_ptr(), n, kt, k, ws.data_ptr(),
                                                 ws.numel(), ts, _stream(stream)))
+    _hold(ws)
     return out
 
 
@@ -251,6 +254,7 @@ def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, k: int = 4, out_keys=None
     _check("mps_sort_pairs", lib().mps_sort_pairs(keys.data_ptr(), vals.data_ptr(), out_keys.data_ptr(),
                                                   out_vals.data_ptr(), n, kt, k, ws.data_ptr(), ws.numel(), ts,
                                                   _stream(stream)))
+    _hold(ws)
     return out_keys, out_vals
 
 
@@ -275,6 +279,7 @@ def sort_records(keys: torch.Tensor, vals: torch.Tensor, k: int = 4, out_keys=No
     _check("mps_sort_records", lib().mps_sort_records(keys.data_ptr(), vals.data_ptr(), out_keys.data_ptr(),
                                                       out_vals.data_ptr(), n, kt, k, ws.data_ptr(), ws.numel(),
                                                       _stream(stream)))
+    _hold(ws)
     return out_keys, out_vals
 
 
@@ -287,6 +292,7 @@ def merge_tree(keys: torch.Tensor, k: int = 4, ws=None, stream=None) -> TreeBuff
     t = tb.struct()
     _check("mps_merge_tree", lib().mps_merge_tree(keys.data_ptr(), n, _key_type(keys), k, ctypes.byref(t),
                                                   ws.data_ptr(), ws.numel(), _stream(stream)))
+    _hold(ws)
     return tb
 
 
@@ -315,6 +321,18 @@ def batch_workspace(n: int, m: int, key_bytes: int, has_payload: bool = False, k
     return torch.empty(max(out.value, 16), dtype=torch.uint8, device=device)
 
 
+# The calls return once their kernels are queued, and the statistics of a
+# single-array sort stay in its workspace until mps_last_stats reads them: the
+# workspace of the most recent call is kept alive here until the next call, so
+# that one allocated inside a call is not reused before its sort has finished.
+_held = None
+
+
+def _hold(ws):
+    global _held
+    _held = ws
+
+
 def _ptr(t: torch.Tensor | None):
     return t.data_ptr() if t is not None else None
 
@@ -331,6 +349,7 @@ def sort_batch(keys: torch.Tensor, offsets: torch.Tensor, k: int = 0, out: torch
     _check("mps_sort_batch", lib().mps_sort_batch(keys.data_ptr(), out.data_ptr(), offsets.data_ptr(), m, n, max_len,
                                                   _key_type(keys), k, ws.data_ptr(), ws.numel(), _ptr(merge_costs),
                                                   _stream(stream)))
+    _hold(ws)
     return out
 
 
@@ -344,6 +363,7 @@ def sort_batch_pairs(keys: torch.Tensor, vals: torch.Tensor, offsets: torch.Tens
                                                               out_vals.data_ptr(), offsets.data_ptr(), m, n, max_len,
                                                               _key_type(keys), k, ws.data_ptr(), ws.numel(),
                                                               _ptr(merge_costs), _stream(stream)))
+    _hold(ws)
     return out_keys, out_vals
 
 
@@ -491,6 +511,25 @@ def sort_keys_minrun(keys: torch.Tensor, min_run_len: int = 24, k: int = 4, out:
     _check("mps_sort_keys_minrun", lib().mps_sort_keys_minrun(keys.data_ptr(), out.data_ptr(), n, _key_type(keys), k,
                                                               min_run_len, ws.data_ptr(), ws.numel(), ts,
                                                               _stream(stream)))
+    _hold(ws)
+    return out
+
+
+TAIL_POLICIES = {"kway_tree": 0, "alg2_pop_k_minus_1": 1, "merge_down": 2}
+
+
+def sort_keys_tail(keys: torch.Tensor, policy: str, k: int = 4, out: torch.Tensor | None = None,
+                   ws: torch.Tensor | None = None, tree: TreeBuffers | None = None, stream=None) -> torch.Tensor:
+    """Sort whose run stack is emptied by a final-collapse policy (mps_sort_keys_tail)."""
+    n = keys.numel()
+    out = torch.empty_like(keys) if out is None else out
+    if ws is None:
+        ws = workspace(n, keys.element_size(), False, k, keys.device)
+    ts = ctypes.byref(tree.struct()) if tree is not None else None
+    _check("mps_sort_keys_tail", lib().mps_sort_keys_tail(keys.data_ptr(), out.data_ptr(), n, _key_type(keys), k,
+                                                          TAIL_POLICIES[policy], ws.data_ptr(), ws.numel(), ts,
+                                                          _stream(stream)))
+    _hold(ws)
     return out
 
 
@@ -506,4 +545,5 @@ def sort_pairs_minrun(keys: torch.Tensor, vals: torch.Tensor, min_run_len: int =
     _check("mps_sort_pairs_minrun", lib().mps_sort_pairs_minrun(keys.data_ptr(), vals.data_ptr(), out_keys.data_ptr(),
                                                                 out_vals.data_ptr(), n, _key_type(keys), k, min_run_len,
                                                                 ws.data_ptr(), ws.numel(), ts, _stream(stream)))
+    _hold(ws)
     return out_keys, out_vals
