@@ -278,7 +278,8 @@ def bench_records(mps, torch, dev, stream, peaks, steps=5):
 
 def bench_batch(mps, torch, dev, stream, peaks, steps=5):
     """4096 uint32 arrays, sizes log-uniform [2^4, 2^20]: one graph-captured
-    batched sort (autotuned k) against one plain mps_sort_keys per array."""
+    batched sort (fan-in and tile sizes autotuned) against one plain
+    mps_sort_keys per array."""
     from paper_2209_06909_gb300 import inputs
     stream = torch.cuda.Stream(dev)  # graph capture needs a stream other than the legacy default
     torch.cuda.synchronize()
@@ -290,8 +291,9 @@ def bench_batch(mps, torch, dev, stream, peaks, steps=5):
     out = torch.empty_like(d_in)
     ws = mps.batch_workspace(n, m, 4, False, 0, dev)
     best_k = mps.batch_autotune(d_in, d_off, out, ws, max_len=int(sizes.max()), stream=stream)
+    tuned = mps.batch_tuned_config(4, False, n, m)
     costs = torch.zeros(m, dtype=torch.int64, device=dev)
-    g = mps.BatchGraph(d_in, d_off, out, ws, k=best_k, max_len=int(sizes.max()), stream=stream, merge_costs=costs)
+    g = mps.BatchGraph(d_in, d_off, out, ws, k=0, max_len=int(sizes.max()), stream=stream, merge_costs=costs)
     g.launch(stream=stream, check=True)
     merge_cost = int(costs.sum().item())
     got = mps.to_numpy(out, np.uint32)
@@ -324,7 +326,7 @@ def bench_batch(mps, torch, dev, stream, peaks, steps=5):
     assert np.array_equal(mps.to_numpy(out, np.uint32)[: int(offsets[64])],
                           np.concatenate([np.sort(keys[int(offsets[a]):int(offsets[a + 1])]) for a in range(64)]))
     return {"workload": "4096 uint32 arrays, sizes log-uniform [2^4,2^20] (permutation or sqrt-length runs)",
-            "n_keys": int(n), "k_autotuned": best_k,
+            "n_keys": int(n), "k_autotuned": best_k, "tuned": tuned,
             "batched_graph_ms": batched_ms, "batched_gkeys_s": n / (batched_ms * 1e-3) / 1e9,
             "plain_per_array_ms": plain_s * 1e3, "plain_gkeys_s": n / plain_s / 1e9,
             "plain_form": "one mps_sort_keys per array, queued back to back on one stream (no host waits)",

@@ -197,10 +197,12 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
  *   max_len : an upper bound on the longest array (sizes the level loop);
  *             0 means n.  An array longer than max_len is detected on the
  *             device and reported as MPS_ERR_DEVICE_CHECK (status 16).
- *   k       : 2, 4, 8, 16, or 0 for the fan-in chosen by mps_batch_autotune for
- *             this key type and mean array size (4 until tuned).
+ *   k       : 2, 4, 8 or 16 with the default tiles, or 0 for the configuration
+ *             (fan-in and tile sizes) chosen by mps_batch_autotune or set by
+ *             mps_batch_set_config for this key type and mean array size
+ *             (k = 4, default tiles until then).
  * n must be below 2^31.  Workspace: mps_batch_workspace_size(n, m, kt,
- * has_payload, k); k = 0 asks for the largest over k in {2, 4, 8}.
+ * has_payload, k); k = 0 asks for the largest over every configuration.
  *   d_merge_costs : NULL, or device memory for m uint64 values that receives
  *             each array's merge cost M = sum_i depth(run i) * L_i (Sec. 2.2)
  *             in its own tree, the same value as sorting the array alone (0
@@ -220,12 +222,27 @@ mps_status mps_sort_batch_pairs(const void* d_keys_in, const uint32_t* d_vals_in
                                 uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes,
                                 uint64_t* d_merge_costs, cudaStream_t stream);
 
-/* Times the batch with k = 2, 4 and 8 (keys only; the output buffer is
- * overwritten) and records the fastest for this key type and mean array
- * size; later calls with k = 0 use it.  *best_k receives the choice. */
+/* Times the batch (keys only; the output buffer is overwritten) for every
+ * fan-in k in {2, 4, 8} and every tile choice, and records the fastest pair
+ * for this key type and mean array size (log2 of n / m); later calls with
+ * k = 0 use it.  *best_k receives the fan-in; mps_batch_tuned_config reports
+ * the tile sizes.  A tile choice sets the fused-subtree tile (elements merged
+ * in one block's shared memory; items per thread = tile / 256) and the
+ * level-merge work unit: choice 0 is the default (6144 and 9216 elements for
+ * uint32 keys), 1 and 2 are smaller tiles with more blocks per SM.  The
+ * workspace must be sized with k = 0. */
 mps_status mps_batch_autotune(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m,
                               uint64_t n, uint64_t max_len, mps_key_type kt, void* d_ws, size_t ws_bytes,
                               cudaStream_t stream, int* best_k);
+
+/* The configuration that k = 0 selects for batches of this key type,
+ * payload flag and mean array size n / m: fan-in, fused-subtree tile and
+ * level-merge unit (elements). */
+mps_status mps_batch_tuned_config(mps_key_type kt, int has_payload, uint64_t n, uint32_t m, int* k, uint32_t* c_fused,
+                                  uint32_t* c_level);
+/* Sets that configuration by hand: k in {2, 4, 8, 16}, tile in 0..2 (0: the
+ * default tiles; 1, 2: smaller). */
+mps_status mps_batch_set_config(mps_key_type kt, int has_payload, uint64_t n, uint32_t m, int k, int tile);
 
 /* A batch sort captured once into a CUDA graph for the given buffers (the
  * graph replays the whole kernel sequence; the buffers must stay valid).

@@ -65,9 +65,9 @@ struct Plan {
     uint32_t min_run = 1, mr_cap = 0, mr_tiles = 0;
     size_t o_mr_g = 0, o_mr_node = 0, o_mr_tiles = 0, o_mr_desc = 0;
 
-    explicit Plan(uint64_t n_, int kb_, bool vals_, int k_, uint32_t m_ = 0, uint32_t min_run_ = 1)
+    explicit Plan(uint64_t n_, int kb_, bool vals_, int k_, uint32_t m_ = 0, uint32_t min_run_ = 1, int tile_ = 0)
         : n(n_), kb(kb_), vals(vals_), k(k_), m(m_), min_run(min_run_) {
-        g = merge_geom(kb, vals, k);
+        g = merge_geom(kb, vals, k, tile_);
         rmax = n / 2 + m + 2;
         det_tiles = ceil_div(std::max<uint64_t>(n, 1), kDetTile);
         mask_tiles = ceil_div(rmax, kMaskTile);
@@ -535,8 +535,9 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
 template <typename K, bool V>
 mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, uint64_t n,
                       const uint64_t* d_off, uint32_t m, uint64_t max_len, int k, void* d_ws, size_t ws_bytes,
-                      uint64_t* d_costs, bool sync_at_end, cudaStream_t st) {
+                      uint64_t* d_costs, bool sync_at_end, cudaStream_t st, int tile) {
     if (!fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
+    if (tile < 0 || tile >= kTileChoices) return MPS_ERR_INVALID_ARG;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
     struct Range {  // NVTX range around the whole batch
         Range() { nvtxRangePushA("sort_batch"); }
@@ -548,7 +549,7 @@ mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
     if (V && (!vals_in || !vals_out)) return MPS_ERR_INVALID_ARG;
     if (overlaps(keys_in, n * sizeof(K), keys_out, n * sizeof(K))) return MPS_ERR_INVALID_ARG;
     if (V && overlaps(vals_in, n * 4, vals_out, n * 4)) return MPS_ERR_INVALID_ARG;
-    Plan plan(n, sizeof(K), V, k, m);
+    Plan plan(n, sizeof(K), V, k, m, 1, tile);
     if (ws_bytes < plan.total) return MPS_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(d_ws) % 16) return MPS_ERR_INVALID_ARG;
     WsView ws = plan.view(d_ws);
@@ -707,45 +708,56 @@ namespace mps {
 namespace {
 
 std::mutex g_tune_mu;
-int g_tuned_k[2][2][64];  // [key type][payload][log2 of mean array size]; 0 = not tuned
+// Batch configuration chosen by k = 0: fan-in and tile choice per key type,
+// payload flag and log2 of the mean array size (k = 0: not tuned).
+struct TunedCfg {
+    int k = 0, tile = 0;
+};
+TunedCfg g_tuned[2][2][64];
 
-int tuned_k(mps_key_type kt, bool vals, uint64_t n, uint32_t m) {
-    uint64_t mean = m ? n / m : n;
+int size_bucket(uint64_t n, uint32_t m) {
+    const uint64_t mean = m ? n / m : n;
     int b = 0;
     while ((1ull << (b + 1)) <= std::max<uint64_t>(mean, 1) && b < 63) b++;
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    int kk = g_tuned_k[kt == MPS_U64][vals][b];
-    return kk ? kk : 4;
+    return b;
 }
 
-void set_tuned_k(mps_key_type kt, bool vals, uint64_t n, uint32_t m, int kk) {
-    uint64_t mean = m ? n / m : n;
-    int b = 0;
-    while ((1ull << (b + 1)) <= std::max<uint64_t>(mean, 1) && b < 63) b++;
+TunedCfg tuned_cfg(mps_key_type kt, bool vals, uint64_t n, uint32_t m) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned_k[kt == MPS_U64][vals][b] = kk;
+    TunedCfg c = g_tuned[kt == MPS_U64][vals][size_bucket(n, m)];
+    if (!c.k) c = TunedCfg{4, 0};
+    return c;
+}
+
+void set_tuned_cfg(mps_key_type kt, bool vals, uint64_t n, uint32_t m, TunedCfg c) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[kt == MPS_U64][vals][size_bucket(n, m)] = c;
 }
 
 }  // namespace
 
 mps_status batch_dispatch(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out, uint64_t n,
                           const uint64_t* d_off, uint32_t m, uint64_t max_len, mps_key_type kt, int k, void* d_ws,
-                          size_t ws_bytes, uint64_t* d_costs, bool sync_at_end, cudaStream_t st) {
+                          size_t ws_bytes, uint64_t* d_costs, bool sync_at_end, cudaStream_t st, int tile) {
     const bool vals = vals_in != nullptr || vals_out != nullptr;
-    if (k == 0) k = tuned_k(kt, vals, n, m);
+    if (k == 0) {
+        const TunedCfg c = tuned_cfg(kt, vals, n, m);
+        k = c.k;
+        tile = c.tile;
+    }
     if (kt == MPS_U32) {
         if (vals)
             return batch_impl<uint32_t, true>((const uint32_t*)keys_in, vals_in, (uint32_t*)keys_out, vals_out, n, d_off, m,
-                                              max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st);
+                                              max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st, tile);
         return batch_impl<uint32_t, false>((const uint32_t*)keys_in, nullptr, (uint32_t*)keys_out, nullptr, n, d_off, m,
-                                           max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st);
+                                           max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st, tile);
     }
     if (kt == MPS_U64) {
         if (vals)
             return batch_impl<uint64_t, true>((const uint64_t*)keys_in, vals_in, (uint64_t*)keys_out, vals_out, n, d_off, m,
-                                              max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st);
+                                              max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st, tile);
         return batch_impl<uint64_t, false>((const uint64_t*)keys_in, nullptr, (uint64_t*)keys_out, nullptr, n, d_off, m,
-                                           max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st);
+                                           max_len, k, d_ws, ws_bytes, d_costs, sync_at_end, st, tile);
     }
     return MPS_ERR_INVALID_ARG;
 }
@@ -765,11 +777,16 @@ mps_status mps_batch_workspace_size(uint64_t n, uint32_t m, mps_key_type kt, int
     if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
     if (k != 0 && !fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
     if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    // k = 0 (the tuned configuration): the largest over fan-ins 2, 4, 8 (and 16
+    // if set by mps_batch_set_config) and every tile choice
     size_t best = 0;
-    for (int kk : {2, 4, 8}) {
+    for (int kk : {2, 4, 8, 16}) {
         if (k != 0 && kk != k) continue;
-        Plan p(n, kt == MPS_U32 ? 4 : 8, has_payload != 0, kk, m);
-        best = std::max(best, p.total);
+        for (int tile = 0; tile < kTileChoices; tile++) {
+            if (k != 0 && tile != 0) continue;
+            Plan p(n, kt == MPS_U32 ? 4 : 8, has_payload != 0, kk, m, 1, tile);
+            best = std::max(best, p.total);
+        }
     }
     *bytes = best;
     return MPS_OK;
@@ -779,7 +796,7 @@ mps_status mps_sort_batch(const void* d_keys_in, void* d_keys_out, const uint64_
                           uint64_t max_len, mps_key_type kt, int k, void* d_ws, size_t ws_bytes, uint64_t* d_merge_costs,
                           cudaStream_t stream) {
     return batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes,
-                          d_merge_costs, true, stream);
+                          d_merge_costs, true, stream, 0);
 }
 
 mps_status mps_sort_batch_pairs(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out, uint32_t* d_vals_out,
@@ -787,36 +804,59 @@ mps_status mps_sort_batch_pairs(const void* d_keys_in, const uint32_t* d_vals_in
                                 void* d_ws, size_t ws_bytes, uint64_t* d_merge_costs, cudaStream_t stream) {
     if (!d_vals_in || !d_vals_out) return n ? MPS_ERR_INVALID_ARG : MPS_OK;
     return batch_dispatch(d_keys_in, d_vals_in, d_keys_out, d_vals_out, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes,
-                          d_merge_costs, true, stream);
+                          d_merge_costs, true, stream, 0);
 }
 
 mps_status mps_batch_autotune(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m, uint64_t n,
                               uint64_t max_len, mps_key_type kt, void* d_ws, size_t ws_bytes, cudaStream_t stream,
                               int* best_k) {
+    // every (fan-in, tile) pair: one checked run, then two timed runs
     float best_ms = 0.f;
-    int best = 0;
+    TunedCfg best;
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return MPS_ERR_CUDA;
     mps_status s = MPS_OK;
     for (int kk : {2, 4, 8}) {
-        s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, kk, d_ws, ws_bytes,
-                           nullptr, true, stream);
+        for (int tile = 0; tile < kTileChoices && s == MPS_OK; tile++) {
+            s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, kk, d_ws, ws_bytes,
+                               nullptr, true, stream, tile);
+            if (s != MPS_OK) break;
+            cudaEventRecord(a, stream);
+            for (int rep = 0; rep < 2; rep++)
+                batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, kk, d_ws, ws_bytes,
+                               nullptr, false, stream, tile);
+            cudaEventRecord(b, stream);
+            if (cudaEventSynchronize(b) != cudaSuccess) { s = MPS_ERR_CUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (!best.k || ms < best_ms) { best = TunedCfg{kk, tile}; best_ms = ms; }
+        }
         if (s != MPS_OK) break;
-        cudaEventRecord(a, stream);
-        for (int rep = 0; rep < 2; rep++)
-            batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, kk, d_ws, ws_bytes,
-                           nullptr, false, stream);
-        cudaEventRecord(b, stream);
-        if (cudaEventSynchronize(b) != cudaSuccess) { s = MPS_ERR_CUDA; break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        if (!best || ms < best_ms) { best = kk; best_ms = ms; }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (s != MPS_OK) return s;
-    set_tuned_k(kt, false, n, m, best);
-    if (best_k) *best_k = best;
+    set_tuned_cfg(kt, false, n, m, best);
+    if (best_k) *best_k = best.k;
+    return MPS_OK;
+}
+
+mps_status mps_batch_tuned_config(mps_key_type kt, int has_payload, uint64_t n, uint32_t m, int* k, uint32_t* c_fused,
+                                  uint32_t* c_level) {
+    if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
+    const TunedCfg c = tuned_cfg(kt, has_payload != 0, n, m);
+    const MergeGeom g = merge_geom(kt == MPS_U32 ? 4 : 8, has_payload != 0, c.k, c.tile);
+    if (k) *k = c.k;
+    if (c_fused) *c_fused = g.c_fused;
+    if (c_level) *c_level = g.c_level;
+    return MPS_OK;
+}
+
+mps_status mps_batch_set_config(mps_key_type kt, int has_payload, uint64_t n, uint32_t m, int k, int tile) {
+    if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
+    if (!fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
+    if (tile < 0 || tile >= kTileChoices) return MPS_ERR_INVALID_ARG;
+    set_tuned_cfg(kt, has_payload != 0, n, m, TunedCfg{k, tile});
     return MPS_OK;
 }
 
@@ -827,7 +867,7 @@ mps_status mps_batch_graph_create(const void* d_keys_in, void* d_keys_out, const
     *out = nullptr;
     // one direct run validates the arguments and sets kernel attributes
     mps_status s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes,
-                                  d_merge_costs, true, stream);
+                                  d_merge_costs, true, stream, 0);
     if (s != MPS_OK) return s;
     mps_batch_graph* g = new mps_batch_graph();
     g->counters = reinterpret_cast<uint64_t*>(d_ws);
@@ -836,7 +876,7 @@ mps_status mps_batch_graph_create(const void* d_keys_in, void* d_keys_out, const
         return MPS_ERR_CUDA;
     }
     s = batch_dispatch(d_keys_in, nullptr, d_keys_out, nullptr, n, d_offsets, m, max_len, kt, k, d_ws, ws_bytes,
-                       d_merge_costs, false, stream);
+                       d_merge_costs, false, stream, 0);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(stream, &graph);
     if (s != MPS_OK || e != cudaSuccess || !graph) {

@@ -136,7 +136,11 @@ struct MergeGeom {
     uint32_t fused_grid;  // blocks of the persistent fused-subtree kernel
 };
 
-MergeGeom merge_geom(int key_bytes, bool vals, int k);
+// Tile choices for the merge stages of one key/payload type: 0 is the
+// default (largest tiles); 1 and 2 halve and third the fused tile, so that
+// more blocks share an SM (items per thread = c_fused / 256).
+constexpr int kTileChoices = 3;
+MergeGeom merge_geom(int key_bytes, bool vals, int k, int tile = 0);
 
 // Number of kernels launched by this thread since the counter was last reset.
 extern thread_local uint64_t g_launches;

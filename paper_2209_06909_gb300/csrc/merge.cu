@@ -1129,11 +1129,16 @@ __global__ void k_copy_lone_runs(const K* __restrict__ in, const uint32_t* __res
 
 // ----------------------------------------------------------------- launchers
 
-MergeGeom merge_geom(int key_bytes, bool vals, int k) {
+MergeGeom merge_geom(int key_bytes, bool vals, int k, int tile) {
+    // {fused tile, level unit} elements per choice
+    static const uint32_t kKeys4[kTileChoices][2] = {{6144, 9216}, {3072, 6144}, {2048, 4096}};
+    static const uint32_t kMid[kTileChoices][2] = {{4096, 4096}, {2048, 3072}, {1536, 2048}};
+    static const uint32_t kKeys8Vals[kTileChoices][2] = {{3072, 4096}, {2048, 3072}, {1024, 2048}};
+    const uint32_t(*t)[2] = (key_bytes == 4 && !vals) ? kKeys4 : ((key_bytes == 8 && vals) ? kKeys8Vals : kMid);
+    const int c = tile < 0 || tile >= kTileChoices ? 0 : tile;
     MergeGeom g;
-    if (key_bytes == 4 && !vals) { g.c_fused = 6144; g.c_level = 9216; }
-    else if (key_bytes == 8 && vals) { g.c_fused = 3072; g.c_level = 4096; }
-    else { g.c_fused = 4096; g.c_level = 4096; }
+    g.c_fused = t[c][0];
+    g.c_level = t[c][1];
     g.tmax = g.c_fused;
     g.ts = g.c_level / (2u * (uint32_t)k);
     g.k = k;

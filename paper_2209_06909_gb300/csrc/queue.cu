@@ -29,7 +29,7 @@
 namespace mps {
 mps_status batch_dispatch(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out, uint64_t n,
                           const uint64_t* d_off, uint32_t m, uint64_t max_len, mps_key_type kt, int k, void* d_ws,
-                          size_t ws_bytes, uint64_t* d_costs, bool sync_at_end, cudaStream_t st);
+                          size_t ws_bytes, uint64_t* d_costs, bool sync_at_end, cudaStream_t st, int tile = 0);
 }
 
 namespace {

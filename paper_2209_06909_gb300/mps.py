@@ -75,7 +75,8 @@ EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_t
            "mps_batch_graph_create", "mps_batch_graph_launch", "mps_batch_graph_destroy",
            "mps_queue_create", "mps_queue_submit", "mps_queue_poll", "mps_queue_wait", "mps_queue_pause",
            "mps_queue_destroy", "mps_records_workspace_size", "mps_sort_records", "mps_sync_status",
-           "mps_workspace_size_minrun", "mps_sort_keys_minrun", "mps_sort_pairs_minrun", "mps_sort_keys_tail"]
+           "mps_workspace_size_minrun", "mps_sort_keys_minrun", "mps_sort_pairs_minrun", "mps_sort_keys_tail",
+           "mps_batch_tuned_config", "mps_batch_set_config"]
 
 # Largest n accepted by mps_sort_keys_noalloc (its scratch is compiled into the library).
 NOALLOC_MAX_N = 1 << 20
@@ -109,6 +110,10 @@ def lib():
     L.mps_sort_pairs_minrun.argtypes = [P, P, P, P, U64, I, I, ctypes.c_uint32, P, ctypes.c_size_t, P, P]
     L.mps_sort_keys_tail.argtypes = [P, P, U64, I, I, I, P, ctypes.c_size_t, P, P]
     L.mps_sort_keys_tail.restype = I
+    L.mps_batch_tuned_config.argtypes = [I, I, U64, ctypes.c_uint32, P, P, P]
+    L.mps_batch_tuned_config.restype = I
+    L.mps_batch_set_config.argtypes = [I, I, U64, ctypes.c_uint32, I, I]
+    L.mps_batch_set_config.restype = I
     for fn in ("mps_workspace_size_minrun", "mps_sort_keys_minrun", "mps_sort_pairs_minrun"):
         getattr(L, fn).restype = I
     L.mps_sort_keys_noalloc.argtypes = [P, P, U64, I, I, P]
@@ -454,6 +459,19 @@ class Queue:
         except Exception:
             pass
 
+
+
+def batch_tuned_config(key_bytes: int, has_payload: bool, n: int, m: int) -> dict:
+    """Configuration chosen by k = 0 for such batches (mps_batch_tuned_config)."""
+    k, cf, cl = ctypes.c_int(0), ctypes.c_uint32(0), ctypes.c_uint32(0)
+    _check("mps_batch_tuned_config", lib().mps_batch_tuned_config(0 if key_bytes == 4 else 1, int(has_payload), n, m,
+                                                                  ctypes.byref(k), ctypes.byref(cf), ctypes.byref(cl)))
+    return {"k": k.value, "c_fused": cf.value, "c_level": cl.value, "items_per_thread": cf.value // 256}
+
+
+def batch_set_config(key_bytes: int, has_payload: bool, n: int, m: int, k: int, tile: int) -> None:
+    """Sets the configuration k = 0 selects (mps_batch_set_config)."""
+    _check("mps_batch_set_config", lib().mps_batch_set_config(0 if key_bytes == 4 else 1, int(has_payload), n, m, k, tile))
 
 def profile_enable(on: bool = True) -> None:
     lib().mps_profile_enable(int(on))

@@ -83,6 +83,37 @@ def test_batch_keys(k):
     assert mps.last_stats()["merge_cost"] == int(want_costs.sum())
 
 
+@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("k", [2, 4, 8, 16])
+def test_batch_tile_choices(k, tile):
+    """Every (fan-in, tile) configuration that k = 0 can select gives the
+    per-array sorts and merge costs, keys and pairs; arrays up to 2^17 cross
+    every tile size, so both fused subtrees and level merges run."""
+    arrays, offsets = make_batch(40 + tile + 3 * k, 150, max_log2=17)
+    keys = np.concatenate(arrays)
+    n, m = keys.size, len(arrays)
+    mps.batch_set_config(4, False, n, m, k, tile)
+    mps.batch_set_config(4, True, n, m, k, tile)
+    cfg = mps.batch_tuned_config(4, False, n, m)
+    assert cfg["k"] == k and cfg["c_fused"] * cfg["items_per_thread"] > 0
+    d_in = mps.to_device(keys, DEV)
+    d_off = torch.from_numpy(offsets.view(np.int64)).to(DEV)
+    costs = cost_buffer(m)
+    ws = mps.batch_workspace(n, m, 4, True, 0, DEV)
+    out = mps.sort_batch(d_in, d_off, k=0, ws=ws, merge_costs=costs)
+    torch.cuda.synchronize()
+    assert np.array_equal(mps.to_numpy(out, np.uint32), np.concatenate([np.sort(a) for a in arrays]))
+    assert np.array_equal(costs.cpu().numpy(), oracle_costs(arrays, k))
+    v = inputs.payload_index(n)
+    ok, ov = mps.sort_batch_pairs(d_in, mps.to_device(v, DEV), d_off, k=0, ws=ws)
+    torch.cuda.synchronize()
+    want_v = []
+    for i, a in enumerate(arrays):
+        idx = np.arange(offsets[i], offsets[i + 1], dtype=np.uint32)
+        want_v.append(idx[np.lexsort((idx, a))])
+    assert np.array_equal(mps.to_numpy(ov, np.uint32), np.concatenate(want_v))
+
+
 def test_batch_large_arrays_level_merges():
     """Arrays larger than a fused tile exercise the level merges of a batch."""
     arrays, offsets = make_batch(77, 16, max_log2=19)
@@ -184,6 +215,8 @@ def test_batch_graph_and_autotune():
     ws = mps.batch_workspace(keys.size, len(arrays), 4, False, 0, DEV)
     best = mps.batch_autotune(d_in, d_off, out, ws)
     assert best in (2, 4, 8)
+    cfg = mps.batch_tuned_config(4, False, keys.size, len(arrays))
+    assert cfg["k"] == best and cfg["c_fused"] in (6144, 3072, 2048)
     stream = torch.cuda.Stream()
     costs = cost_buffer(len(arrays))
     want_costs = oracle_costs(arrays, best)
