@@ -96,3 +96,26 @@ def test_minrun_rejects_unsupported_lengths():
     with pytest.raises(mps.MpsError) as e:
         mps.sort_keys_minrun(a, min_run_len=33, k=4, ws=torch.empty(1 << 20, dtype=torch.uint8, device=DEV))
     assert e.value.code == 2
+
+
+def test_minrun_permutation_2e28():
+    """The bench's min-run variant at full size (n = 2^28 permutation, m = 24,
+    k = 4): the output is 0..n-1; runs, directions, powers, node table, leaf
+    depths and merge cost equal the oracle's run scan and tree from run lengths."""
+    n = 1 << 28
+    a = inputs.random_permutation(n, 1004)
+    tb = mps.TreeBuffers.alloc(n, DEV)
+    out = mps.sort_keys_minrun(mps.to_device(a, DEV), min_run_len=24, k=4, tree=tb)
+    torch.cuda.synchronize()
+    assert torch.equal(out, torch.arange(n, dtype=torch.int32, device=DEV))
+    del out
+    t = tb.to_numpy()
+    rs, rd = oracle.find_runs(a, min_run_len=24)
+    want = oracle.tree_from_lengths(np.diff(rs.astype(np.int64)), 4)
+    assert t["r"] == rs.size - 1
+    assert np.array_equal(t["run_starts"], rs) and np.array_equal(t["run_desc"], rd)
+    assert np.array_equal(t["powers"], want["powers"])
+    assert t["num_nodes"] == want["num_nodes"] and np.array_equal(t["nodes"], want["nodes"])
+    assert np.array_equal(t["node_first"], want["node_first"])
+    assert np.array_equal(t["leaf_depth"], want["leaf_depth"])
+    assert t["merge_cost"] == want["merge_cost"]
