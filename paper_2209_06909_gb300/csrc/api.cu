@@ -88,7 +88,7 @@ struct Plan {
         auto take = [&](size_t bytes) { size_t at = o; o += align_up(bytes); return at; };
         o_ctr = take(kCtrWords * 8);
         o_lvloff = take(kMaxLevels * 4);
-        o_det_state = take(det_tiles * 8);
+        o_det_state = take(det_tiles * 24 + (ceil_div(std::max<uint64_t>(n, 1), 32) + 8) * 4);
         o_rs = take((rmax + 2 + 32) * 4);  // padded for 16-byte loads past r
         o_rdesc = take(rmax + 1);
         o_fused = take((size_t)fused_cap * 16);

@@ -30,7 +30,6 @@ enum : int {
     kCtrIntervals = 202,  // splitter intervals of the current level (packed into units)
     kCtrMaxRun = 203,   // longest run (elements)
     kCtrMaxLen = 204,   // longest array of a batch (elements)
-    kCtrDetTile = 205,  // next run-detection tile to take
     kCtrCand = 206,     // node-pass candidates listed by the mask pass
     kCtrMrGood = 207,   // minimum run length: good intervals (natural runs of >= m-1 interior flags)
     kCtrTailCount = 208,  // final-collapse variant: boundaries left on the run stack after the last run
@@ -61,7 +60,7 @@ static_assert(sizeof(LevelNode) == 96, "LevelNode layout");
 struct WsView {
     uint64_t n;                    // keys being sorted (all arrays of a batch)
     uint64_t* counters;
-    uint64_t* det_state;           // [tiles] run-detection tile words (look-back)
+    uint64_t* det_state;           // run detection: tile summaries, tile prefixes, comparison bits
     uint32_t* run_starts;
     uint8_t* run_desc;
     uint8_t* lv[kMinTreeLevels];   // lv[0] = powers[0..r] (+ padding)

@@ -333,7 +333,12 @@ __global__ void __launch_bounds__(kFusedThreads)
                 spins++;
             }
             if (__syncthreads_or(!done)) {
-                // the bulk copy did not complete: report it, one more bounded wait, stop
+                // The bulk copy did not complete: report it, one more bounded wait, stop.
+                // The copy is well formed by construction (16-byte aligned source and
+                // destination, a size that is a multiple of 16 inside the tile's buffer,
+                // the expected byte count set before it is issued), so it completes
+                // unless the memory system fails; this branch only keeps that case from
+                // hanging the GPU, and the status tells the host the output is invalid.
                 if (tid == 0) dev_fail(status, kDevSpin);
                 for (spins = 0; !mbar_try_wait(&s_bar, phase) && spins < kMbarSpinLimit; spins++) {
                 }
@@ -1038,8 +1043,12 @@ __global__ void __launch_bounds__(kLvlThreads)
                 spins++;
             }
             if (__syncthreads_or(!done)) {
-                // the bulk copies did not complete: report it, give them one more
-                // bounded wait, and stop (the whole block leaves together)
+                // The bulk copies did not complete: report it, give them one more
+                // bounded wait, and stop (the whole block leaves together).  Every copy
+                // is well formed by construction (16-byte aligned ends, sizes that are
+                // multiples of 16 inside the unit's buffer, the expected byte count set
+                // before they are issued), so they complete unless the memory system
+                // fails; this branch only keeps that case from hanging the GPU.
                 if (threadIdx.x == 0) dev_fail(status, kDevSpin);
                 for (spins = 0; !mbar_try_wait(&s_bar, phase) && spins < kMbarSpinLimit; spins++) {
                 }

@@ -11,9 +11,10 @@
 //     not lt : B->A, A->A, D->B          lt : B->D, A->B, D->D
 // and element 0 is always B.  A tile's effect is a map {B,A,D} -> {B,A,D}
 // plus, per entry state, the number of B states produced; maps compose
-// associatively, so the greedy scan becomes one pass: each tile scans its own
-// elements and takes its entry state and run offset from the tiles before it
-// (decoupled look-back).  Run i is descending iff key[s_i + 1] < key[s_i].
+// associatively, so the greedy scan becomes a scan over tiles: each tile
+// summarises its elements, one block composes the summaries into every tile's
+// entry state and run offset, and each tile then writes its runs.  Run i is
+// descending iff key[s_i + 1] < key[s_i].
 //
 // Powers.  With run i-1 = [s_{i-1}, s_i) and run i = [s_i, s_{i+1}), Def. 3.1's
 // midpoints are a = (s_{i-1} + s_i) / 2n and b = (s_i + s_{i+1}) / 2n.  For a
@@ -168,145 +169,151 @@ __device__ __forceinline__ ThreadRuns thread_runs(uint64_t lt, uint64_t n, uint6
     return R;
 }
 
-// ---- single-pass tile scan with decoupled look-back
-// Each tile publishes a 64-bit word: flag (bits 62-63) and either its own
-// summary (flag 1: map in bits 0-5, B-counts per entry state in 14-bit fields
-// at 6, 20, 34) or its inclusive prefix (flag 2: state after the tile in bits
-// 0-1, runs up to and including the tile in bits 2-33).  Tile 0 starts in
-// state B, so a prefix needs only the one state and count.
-constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr uint64_t kFlagPre = 2ull << 62;
-constexpr uint64_t kFlagMask = 3ull << 62;
-constexpr uint32_t kSpinLimit = 1u << 22;
-
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
-}
-static_assert(kDetTile < (1 << 14), "tile counts fit 14 bits");
-__device__ __forceinline__ uint64_t pack_agg(uint4 a) {
-    return kFlagAgg | (uint64_t)a.x | ((uint64_t)a.y << 6) | ((uint64_t)a.z << 20) | ((uint64_t)a.w << 34);
-}
-__device__ __forceinline__ uint4 unpack_agg(uint64_t w) {
-    return make_uint4((uint32_t)(w & 63u), (uint32_t)((w >> 6) & 0x3FFFu), (uint32_t)((w >> 20) & 0x3FFFu),
-                      (uint32_t)((w >> 34) & 0x3FFFu));
-}
 __device__ __forceinline__ uint32_t runsum_count(uint4 a, uint32_t st) { return st == 0 ? a.y : (st == 1 ? a.z : a.w); }
 
-// Run detection in one pass over the keys.  Tiles take their index from a
-// counter in launch order, so every tile a block waits for is already
-// running; the block scans its tile, publishes the tile summary, walks back
-// over earlier tiles until it meets a published prefix (bounded waits; a wait
-// that runs out sets the status word), publishes its own prefix, and writes
-// its run starts and directions, staged in shared memory, as one contiguous
-// coalesced range.
-template <typename K>
-__global__ void __launch_bounds__(kDetThreads, 4) k_detect(const K* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
-                                                        uint32_t m, uint64_t* __restrict__ tile_state,
-                                                        uint64_t* __restrict__ counters, uint32_t* __restrict__ run_starts,
-                                                        uint8_t* __restrict__ run_desc) {
-    __shared__ uint4 tmp[kDetThreads / 32 + 1];
-    __shared__ uint32_t s_tile, s_state, s_base, s_count;
-    __shared__ uint32_t s_rs[kDetTile];
-    __shared__ uint8_t s_rd[kDetTile];
-    __shared__ uint16_t s_lut[3 * 256];
-    if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(counters + kCtrDetTile), 1ull);
-    for (uint32_t e = threadIdx.x; e < 3 * 256; e += kDetThreads) {
+// ---- run detection in three passes over tiles of kDetTile elements
+// 1. every tile: the comparison bits of its elements (one 32-bit word per
+//    thread, bit j = key[i0+j] < key[i0+j-1]) and the tile's summary (exit
+//    state per entry state, starts per entry state);
+// 2. one block: the exclusive composition of the tile summaries, i.e. each
+//    tile's entry state and first run index (element 0 enters in state B);
+// 3. every tile: the run starts and directions from its comparison bits and
+//    entry state, staged in shared memory and written as one coalesced range.
+// The keys are read once; passes 2 and 3 read n/8 bytes of comparison bits.
+
+// lut[state * 256 + comparison bits of 8 elements] = start mask | exit state << 8,
+// generated at compile time and copied to shared memory by every block.
+struct DetLut {
+    uint16_t v[3 * 256];
+};
+constexpr DetLut make_det_lut() {
+    DetLut t{};
+    for (uint32_t e = 0; e < 3 * 256; e++) {
         uint32_t st = e >> 8, msk = 0;
         for (uint32_t j = 0; j < 8; j++) {
-            st = step_state(st, ((e >> j) & 1u) != 0);
+            const bool lt = ((e >> j) & 1u) != 0;
+            st = lt ? (st == 1u ? 0u : 2u) : (st == 2u ? 0u : 1u);  // the automaton above
             msk |= (st == 0 ? 1u : 0u) << j;
         }
-        s_lut[e] = (uint16_t)(msk | (st << 8));
+        t.v[e] = (uint16_t)(msk | (st << 8));
     }
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint32_t tiles = (uint32_t)ceil_div(n, kDetTile);
+    return t;
+}
+__device__ const DetLut kDetLut = make_det_lut();
+static_assert(sizeof(DetLut) == 3 * 256 * 2 && sizeof(DetLut) % 16 == 0, "16-byte copies of the table");
+
+__device__ __forceinline__ void build_lut(uint16_t* lut) {
+    const uint4* src = reinterpret_cast<const uint4*>(kDetLut.v);
+    for (uint32_t q = threadIdx.x; q < sizeof(DetLut) / 16; q += blockDim.x) reinterpret_cast<uint4*>(lut)[q] = src[q];
+}
+
+// One block per tile.
+template <typename K>
+__global__ void __launch_bounds__(kDetThreads) k_detect_sum(const K* __restrict__ keys, uint64_t n,
+                                                            const uint64_t* __restrict__ off, uint32_t m,
+                                                            uint32_t* __restrict__ lt_words, uint4* __restrict__ tile_sum) {
+    __shared__ uint4 tmp[kDetThreads / 32 + 1];
+    __shared__ __align__(16) uint16_t s_lut[3 * 256];
+    const uint32_t tile = blockIdx.x;
     const uint64_t i0 = (uint64_t)tile * kDetTile + (uint64_t)threadIdx.x * kDetItems;
     uint64_t lt;
     {
+        // the keys are requested first; the table copy overlaps their latency
         K v[kDetItems + 2];
         load_window(keys, n, i0, v);
+        build_lut(s_lut);
         lt = lt_mask(v);
     }
+    if (i0 < n) lt_words[(size_t)tile * kDetThreads + threadIdx.x] = (uint32_t)lt;
+    __syncthreads();
+    const ThreadRuns tr = thread_runs(lt, n, i0, off, m, s_lut);
+    uint4 tot;
+    block_scan_excl<kDetThreads, false>(tr.sum, OpRunSum(), runsum_identity(), tmp, &tot);
+    if (threadIdx.x == 0) tile_sum[tile] = tot;
+}
+
+// One block of 1024 threads over all tiles: tile_pre[t] = (entry state, runs
+// before tile t); writes r and the end sentinel run_starts[r] = n.  Warp w
+// owns a contiguous range of tiles and walks it 32 tiles at a time (coalesced
+// 16-byte loads, an in-warp scan, a carry); one block scan joins the warps.
+__device__ __forceinline__ uint4 warp_scan_incl(uint4 x) {
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint4 y = shfl_up(x, o);
+        if (lane >= (uint32_t)o) x = OpRunSum()(y, x);
+    }
+    return x;
+}
+__device__ __forceinline__ uint4 shfl_idx(uint4 v, int src) {
+    v.x = __shfl_sync(0xffffffffu, v.x, src); v.y = __shfl_sync(0xffffffffu, v.y, src);
+    v.z = __shfl_sync(0xffffffffu, v.z, src); v.w = __shfl_sync(0xffffffffu, v.w, src);
+    return v;
+}
+
+__global__ void __launch_bounds__(1024) k_detect_scan(uint64_t n, const uint4* __restrict__ tile_sum, uint2* __restrict__ tile_pre,
+                                                      uint64_t* __restrict__ counters, uint32_t* __restrict__ run_starts) {
+    __shared__ uint4 s_warp[32];
+    __shared__ uint4 tmp[1024 / 32 + 1];
+    const uint32_t tiles = (uint32_t)ceil_div(n, kDetTile);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t per = (tiles + 31) / 32;  // tiles per warp
+    const uint32_t t0 = min(tiles, warp * per), t1 = min(tiles, t0 + per);
+    // pass 1: the warp's aggregate
+    uint4 carry = runsum_identity();
+    for (uint32_t b = t0; b < t1; b += 32) {
+        const uint32_t t = b + lane;
+        uint4 x = warp_scan_incl(t < t1 ? tile_sum[t] : runsum_identity());
+        carry = OpRunSum()(carry, shfl_idx(x, 31));
+    }
+    uint4 tot;
+    const uint4 wpre = block_scan_excl<1024, false>(lane == 0 ? carry : runsum_identity(), OpRunSum(), runsum_identity(), tmp,
+                                                    &tot);
+    if (lane == 0) s_warp[warp] = wpre;
+    __syncthreads();
+    // pass 2: every tile's exclusive prefix, entered in state B
+    carry = s_warp[warp];
+    for (uint32_t b = t0; b < t1; b += 32) {
+        const uint32_t t = b + lane;
+        const uint4 x = t < t1 ? tile_sum[t] : runsum_identity();
+        const uint4 incl = warp_scan_incl(x);
+        uint4 excl = shfl_up(incl, 1);
+        if (lane == 0) excl = runsum_identity();
+        const uint4 pre = OpRunSum()(carry, excl);
+        if (t < t1) tile_pre[t] = make_uint2(map_get(pre.x, 0), pre.y);
+        carry = OpRunSum()(carry, shfl_idx(incl, 31));
+    }
+    if (threadIdx.x == 0) {
+        counters[kCtrR] = tot.y;
+        run_starts[tot.y] = (uint32_t)n;
+    }
+}
+
+// One block per tile.
+__global__ void __launch_bounds__(kDetThreads) k_detect_write(uint64_t n, const uint64_t* __restrict__ off, uint32_t m,
+                                                              const uint32_t* __restrict__ lt_words, const uint2* __restrict__ tile_pre,
+                                                              uint32_t* __restrict__ run_starts, uint8_t* __restrict__ run_desc) {
+    __shared__ uint4 tmp[kDetThreads / 32 + 1];
+    __shared__ uint32_t s_rs[kDetTile];
+    __shared__ uint8_t s_rd[kDetTile];
+    __shared__ __align__(16) uint16_t s_lut[3 * 256];
+    build_lut(s_lut);
+    const uint32_t tile = blockIdx.x;
+    const uint64_t i0 = (uint64_t)tile * kDetTile + (uint64_t)threadIdx.x * kDetItems;
+    const uint64_t words = ceil_div(n, kDetItems);
+    const uint64_t gi = (uint64_t)tile * kDetThreads + threadIdx.x;
+    uint64_t lt = 0;
+    if (gi < words) {
+        lt = lt_words[gi];
+        // bit 32 (the comparison after the chunk) is bit 0 of the next chunk's word
+        if (gi + 1 < words) lt |= (uint64_t)(lt_words[gi + 1] & 1u) << 32;
+    }
+    __syncthreads();
     const ThreadRuns tr = thread_runs(lt, n, i0, off, m, s_lut);
     uint4 tot;
     const uint4 pre = block_scan_excl<kDetThreads, false>(tr.sum, OpRunSum(), runsum_identity(), tmp, &tot);
-    if (threadIdx.x < 32) {
-        // Look-back by warp 0: lane i reads the word of tile (window end - i).
-        // The nearest published prefix ends the walk; the summaries of the
-        // tiles after it compose (earlier tile first) into `comp`.
-        const uint32_t lane = threadIdx.x;
-        // element 0 always starts a run, so tile 0's entry state is irrelevant (B)
-        uint32_t st_in = 0, base = 0;
-        if (tile > 0) {
-            if (lane == 0) st_release(tile_state + tile, pack_agg(tot));
-            uint4 comp = runsum_identity();
-            int64_t win_end = (int64_t)tile - 1;
-            bool failed = false;
-            while (true) {
-                const int64_t t = win_end - (int64_t)lane;
-                uint64_t w = 0;
-                uint32_t pmask = 0;
-                int jp = 32;
-                for (uint32_t spins = 0;; spins++) {
-                    w = t >= 0 ? ld_acquire(tile_state + t) : kFlagPre;  // tile 0 always holds a prefix
-                    pmask = __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagPre);
-                    jp = pmask ? __ffs(pmask) - 1 : 32;
-                    const uint32_t before = jp == 32 ? 0xffffffffu : ((1u << jp) - 1u);
-                    const uint32_t waiting = __ballot_sync(0xffffffffu, (w & kFlagMask) == 0) & before;
-                    if (!waiting) break;
-                    if (spins >= kSpinLimit) {
-                        failed = true;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-                if (failed) {
-                    if (lane == 0) dev_fail(reinterpret_cast<uint32_t*>(counters + kCtrStatus), kDevSpin);
-                    break;
-                }
-                // compose the summaries of lanes 0 .. jp-1 (lane jp-1 is the earliest tile)
-                uint4 x = (int)lane < jp ? unpack_agg(w) : runsum_identity();
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint4 y = shfl_down(x, o);
-                    if (lane + o < 32) x = OpRunSum()(y, x);
-                }
-                x.x = __shfl_sync(0xffffffffu, x.x, 0);
-                x.y = __shfl_sync(0xffffffffu, x.y, 0);
-                x.z = __shfl_sync(0xffffffffu, x.z, 0);
-                x.w = __shfl_sync(0xffffffffu, x.w, 0);
-                comp = OpRunSum()(x, comp);
-                if (jp < 32) {
-                    const uint64_t wp = __shfl_sync(0xffffffffu, w, jp);
-                    const uint32_t sp = (uint32_t)(wp & 3u), cp = (uint32_t)((wp >> 2) & 0xFFFFFFFFu);
-                    st_in = map_get(comp.x, sp);
-                    base = cp + runsum_count(comp, sp);
-                    break;
-                }
-                win_end -= 32;
-            }
-        }
-        if (lane == 0) {
-            const uint32_t cnt = runsum_count(tot, st_in);
-            const uint32_t st_out = map_get(tot.x, st_in);
-            st_release(tile_state + tile, kFlagPre | ((uint64_t)(base + cnt) << 2) | st_out);
-            s_state = st_in;
-            s_base = base;
-            s_count = cnt;
-            if (tile == tiles - 1) {
-                counters[kCtrR] = base + cnt;
-                run_starts[base + cnt] = (uint32_t)n;
-            }
-        }
-    }
-    __syncthreads();
-    const uint32_t st_in = s_state;
+    const uint2 tp = tile_pre[tile];
+    const uint32_t st_in = tp.x, base = tp.y;
     const uint32_t st = map_get(pre.x, st_in);  // state entering this thread's chunk
     uint32_t msk = st == 0 ? tr.ms[0] : (st == 1 ? tr.ms[1] : tr.ms[2]);
     uint32_t idx = runsum_count(pre, st_in);
@@ -318,7 +325,7 @@ __global__ void __launch_bounds__(kDetThreads, 4) k_detect(const K* __restrict__
         idx++;
     }
     __syncthreads();
-    const uint32_t base = s_base, cnt = s_count;
+    const uint32_t cnt = runsum_count(tot, st_in);
     for (uint32_t q = threadIdx.x; q < cnt; q += kDetThreads) {
         run_starts[base + q] = s_rs[q];
         run_desc[base + q] = s_rd[q];
@@ -450,11 +457,16 @@ __global__ void k_array_params(const uint64_t* __restrict__ off, uint32_t m, uin
 
 template <typename K>
 void launch_detect(const K* keys, uint64_t n, const WsView& ws, cudaStream_t st) {
-    uint32_t tiles = (uint32_t)ceil_div(n, kDetTile);
-    cudaMemsetAsync(ws.det_state, 0, (size_t)tiles * 8, st);
-    k_detect<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.batch_off, ws.batch_m, ws.det_state, ws.counters, ws.run_starts,
-                                               ws.run_desc);
-    g_launches += 1;
+    const uint32_t tiles = (uint32_t)ceil_div(n, kDetTile);
+    if (tiles == 0) return;
+    // detection scratch: tile summaries (16 B), tile prefixes (8 B), comparison words (4 B per 32 keys)
+    uint4* tile_sum = reinterpret_cast<uint4*>(ws.det_state);
+    uint2* tile_pre = reinterpret_cast<uint2*>(tile_sum + tiles);
+    uint32_t* lt_words = reinterpret_cast<uint32_t*>(tile_pre + tiles);
+    k_detect_sum<K><<<tiles, kDetThreads, 0, st>>>(keys, n, ws.batch_off, ws.batch_m, lt_words, tile_sum);
+    k_detect_scan<<<1, 1024, 0, st>>>(n, tile_sum, tile_pre, ws.counters, ws.run_starts);
+    k_detect_write<<<tiles, kDetThreads, 0, st>>>(n, ws.batch_off, ws.batch_m, lt_words, tile_pre, ws.run_starts, ws.run_desc);
+    g_launches += 3;
 }
 
 template void launch_detect<uint32_t>(const uint32_t*, uint64_t, const WsView&, cudaStream_t);
