@@ -34,6 +34,7 @@ enum : int {
     kCtrMrGood = 207,   // minimum run length: good intervals (natural runs of >= m-1 interior flags)
     kCtrTailCount = 208,  // final-collapse variant: boundaries left on the run stack after the last run
     kCtrTailShift = 209,  // final-collapse variant: number of final-collapse nodes (added to every other power)
+    kCtrFusedNext = 210,  // next fused tile to take (dynamic scheduling of k_fused)
     kCtrWords = 256
 };
 

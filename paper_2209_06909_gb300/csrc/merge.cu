@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(kFusedThreads)
     k_fused(const uint4* __restrict__ flist, const uint64_t* __restrict__ ctr, const K* __restrict__ leaf,
             const uint32_t* __restrict__ vleaf, K* __restrict__ out0, K* __restrict__ out1, uint32_t* __restrict__ vout0,
             uint32_t* __restrict__ vout1, const uint32_t* __restrict__ rs, const uint8_t* __restrict__ rdesc,
-            const uint8_t* __restrict__ P, uint32_t C, int k, uint64_t n_total, uint32_t* __restrict__ status) {
+            const uint8_t* __restrict__ P, uint32_t C, int k, uint64_t n_total, uint32_t* __restrict__ status,
+            unsigned long long* __restrict__ next_tile) {
     extern __shared__ uint4 smem_raw[];
     const uint32_t BMAX = C / 2 + 8;
     const uint32_t CP = C + kFusedPad;
@@ -272,7 +273,15 @@ __global__ void __launch_bounds__(kFusedThreads)
     if (tid == 0) mbar_init(&s_bar, 1);
     __syncthreads();
 
-    for (uint32_t f = blockIdx.x; f < F; f += gridDim.x) {
+    // tiles are taken one at a time from a counter (their sizes differ, so a
+    // fixed assignment would leave some blocks working long after the others)
+    __shared__ uint32_t s_f;
+    for (;;) {
+        __syncthreads();  // every thread has read the previous tile index
+        if (tid == 0) s_f = (uint32_t)atomicAdd(next_tile, 1ull);
+        __syncthreads();
+        const uint32_t f = s_f;
+        if (f >= F) break;
         const uint4 fr = flist[f];
         const uint32_t L = fr.x, R = fr.y;
         const bool odd = fr.z & 1u;
@@ -1194,7 +1203,8 @@ void launch_fused(const K* leaf_keys, const uint32_t* leaf_vals, K* out, uint32_
     K* tmp = reinterpret_cast<K*>(ws.keys_tmp);
     k_fused<K, V><<<grid, kFusedThreads, smem, st>>>(ws.fused_list, ws.counters, leaf_keys, leaf_vals, out, tmp, vout,
                                                      ws.vals_tmp, ws.run_starts, ws.run_desc, ws.powers, g.c_fused, g.k,
-                                                     ws.n, reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus));
+                                                     ws.n, reinterpret_cast<uint32_t*>(ws.counters + kCtrStatus),
+                                                     reinterpret_cast<unsigned long long*>(ws.counters + kCtrFusedNext));
     g_launches += 1;
 }
 
