@@ -123,3 +123,44 @@ def test_binding_argument_counts_match_the_header():
         assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
         checked += 1
     assert checked >= 20
+
+
+def test_fan_in_sixteen_and_tail_policy_checks(lib):
+    """k = 16 is accepted (and sizes a larger workspace than k = 8); the
+    final-collapse entry point rejects a policy outside 0..2 and a bad fan-in
+    before any device work."""
+    from paper_2209_06909_gb300 import mps
+    w8 = mps.workspace_size(1 << 20, 4, False, 8)
+    w16 = mps.workspace_size(1 << 20, 4, False, 16)
+    assert w16 > w8 > 0
+    with pytest.raises(mps.MpsError) as e:
+        mps.workspace_size(1 << 20, 4, False, 32)
+    assert e.value.code == 2
+    L = mps.lib()
+    assert L.mps_sort_keys_tail(None, None, 10, 0, 4, 3, None, 0, None, None) == 1
+    assert L.mps_sort_keys_tail(None, None, 10, 0, 4, -1, None, 0, None, None) == 1
+    assert L.mps_sort_keys_tail(None, None, 10, 0, 5, 1, None, 0, None, None) == 2
+
+
+def test_batch_configuration_host_logic(lib):
+    """The configuration that k = 0 selects: default (k = 4, the largest
+    tiles) until set; per key type, payload flag and mean-size bucket; bad
+    fan-in or tile rejected; the workspace for k = 0 covers every tile."""
+    from paper_2209_06909_gb300 import mps
+    n, m = 3_000_000, 700  # a mean size no other test of this process tunes
+    cfg = mps.batch_tuned_config(4, False, n, m)
+    assert cfg == {"k": 4, "c_fused": 6144, "c_level": 9216, "items_per_thread": 24}
+    mps.batch_set_config(4, False, n, m, 8, 2)
+    assert mps.batch_tuned_config(4, False, n, m) == {"k": 8, "c_fused": 2048, "c_level": 4096, "items_per_thread": 8}
+    assert mps.batch_tuned_config(4, True, n, m)["k"] == 4      # the payload flag has its own entry
+    assert mps.batch_tuned_config(4, False, n, m * 64)["k"] == 4  # so does another mean size
+    mps.batch_set_config(8, True, n, m, 16, 1)
+    assert mps.batch_tuned_config(8, True, n, m) == {"k": 16, "c_fused": 2048, "c_level": 3072, "items_per_thread": 8}
+    for bad_k, bad_tile, code in ((3, 0, 2), (4, 3, 1), (4, -1, 1)):
+        with pytest.raises(mps.MpsError) as e:
+            mps.batch_set_config(4, False, n, m, bad_k, bad_tile)
+        assert e.value.code == code
+    # k = 0 sizes the workspace for every configuration it may select
+    w0 = mps.batch_workspace(n, m, 4, False, 0, "meta").numel()
+    for k in (2, 4, 8, 16):
+        assert mps.batch_workspace(n, m, 4, False, k, "meta").numel() <= w0
