@@ -324,8 +324,8 @@ constexpr int kNet32Len = 191;
 
 // The network on 32 items held in registers: the loop is unrolled, so every
 // index is a compile-time constant.
-template <typename T>
-__device__ __forceinline__ void sort_net32(T (&x)[32], uint32_t (&v)[32]) {
+template <typename F>
+__device__ __forceinline__ void for_net32(F&& cas) {
     constexpr uint8_t net[kNet32Len][2] = {
     {0, 1}, {2, 3}, {4, 5}, {6, 7}, {8, 9}, {10, 11}, {12, 13}, {14, 15}, {16, 17}, {18, 19}, {20, 21}, {22, 23},
     {24, 25}, {26, 27}, {28, 29}, {30, 31}, {0, 2}, {1, 3}, {4, 6}, {5, 7}, {8, 10}, {9, 11}, {12, 14}, {13, 15},
@@ -345,43 +345,129 @@ __device__ __forceinline__ void sort_net32(T (&x)[32], uint32_t (&v)[32]) {
     {9, 10}, {11, 12}, {13, 14}, {15, 16}, {17, 18}, {19, 20}, {21, 22}, {23, 24}, {25, 26}, {27, 28}, {29, 30},
     };
 #pragma unroll
-    for (int c = 0; c < kNet32Len; c++) cswap(x[net[c][0]], x[net[c][1]], v[net[c][0]], v[net[c][1]]);
+    for (int c = 0; c < kNet32Len; c++) cas(net[c][0], net[c][1]);
 }
 
-// One thread per run of at most m <= 32 elements: the run is loaded into
-// registers (padded with items that sort last), sorted stably by (key,
-// position), and rewritten in place in the copy.
+template <typename T>
+__device__ __forceinline__ void sort_net32(T (&x)[32], uint32_t (&v)[32]) {
+    for_net32([&](int i, int j) { cswap(x[i], x[j], v[i], v[j]); });
+}
+
+// Keys alone: equal keys cannot be told apart, so the plain network (min and
+// max per pair) gives the stable sort's output.
+template <typename K>
+__device__ __forceinline__ void sort_net32_keys(K (&x)[32]) {
+    for_net32([&](int i, int j) {
+        const K a = x[i], b = x[j];
+        x[i] = a < b ? a : b;
+        x[j] = a < b ? b : a;
+    });
+}
+
+// Elements of the runs of one warp staged in shared memory: at most 32 runs of
+// at most 32 elements, with one pad slot after every 32 (so that lanes whose
+// runs start a multiple of 8 apart still read different banks).
+constexpr uint32_t kMrWarpSpan = 32 * 32;
+constexpr uint32_t kMrWarpSlots = kMrWarpSpan + kMrWarpSpan / 32;
+__device__ __forceinline__ uint32_t mr_slot(uint32_t j) { return j + (j >> 5); }
+
 template <typename K, bool V>
-__global__ void __launch_bounds__(kMrThreads) k_mr_sort_short(const uint64_t* __restrict__ ctr, const uint32_t* __restrict__ rs,
+struct MrSortSmem {
+    static constexpr size_t bytes() { return (size_t)(kMrThreads / 32) * kMrWarpSlots * (sizeof(K) + (V ? 4 : 0)); }
+};
+
+// One thread per run of at most m <= 32 elements: the run is loaded into
+// registers (padded with items that sort last), sorted (with payloads: stably
+// by (key, position); keys alone by key), and rewritten in place in the copy.
+// A warp takes 32 consecutive
+// runs; when they span at most kMrWarpSpan elements (every run short, as in a
+// permutation) the warp stages the span in shared memory with coalesced loads
+// and stores it back the same way, else each thread reads and writes its run
+// in global memory directly.
+template <typename K, bool V>
+__global__ void __launch_bounds__(kMrThreads, V ? 1 : 2) k_mr_sort_short(const uint64_t* __restrict__ ctr, const uint32_t* __restrict__ rs,
                                                              uint32_t m, K* __restrict__ copy, uint32_t* __restrict__ vcopy,
                                                              uint32_t r_cap) {
     using T = typename std::conditional<sizeof(K) == 4, ShortItem32, ShortItem64>::type;
+    extern __shared__ uint4 mr_smem[];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    K* wk = reinterpret_cast<K*>(mr_smem) + (size_t)warp * kMrWarpSlots;
+    uint32_t* wv = V ? reinterpret_cast<uint32_t*>(reinterpret_cast<K*>(mr_smem) + (size_t)(kMrThreads / 32) * kMrWarpSlots) +
+                           (size_t)warp * kMrWarpSlots
+                     : nullptr;
     const uint32_t r = min((uint32_t)ctr[kCtrR], r_cap);
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < r; q += gridDim.x * blockDim.x) {
-        const uint32_t s = rs[q], len = rs[q + 1] - s;
-        if (len > m || len < 2) continue;
-        T x[32];
-        uint32_t v[32];
-#pragma unroll
-        for (uint32_t i = 0; i < 32; i++) {
-            const bool in = i < len;
-            const K key = in ? copy[s + i] : ~K(0);
-            if constexpr (sizeof(K) == 4) {
-                x[i].kp = ((unsigned long long)key << 32) | (in ? i : 32u + i);
-            } else {
-                x[i].key = key;
-                x[i].pos = in ? i : 32u + i;
+    const uint32_t warps = gridDim.x * (kMrThreads / 32);
+    for (uint32_t g0 = (blockIdx.x * (kMrThreads / 32) + warp) * 32u; g0 < r; g0 += warps * 32u) {
+        const uint32_t q = g0 + lane;
+        const uint32_t s = q < r ? rs[q] : 0u;
+        const uint32_t e = q < r ? rs[q + 1] : 0u;
+        const uint32_t len = e - s;
+        const bool mine = q < r && len >= 2 && len <= m;
+        const uint32_t S = __shfl_sync(0xffffffffu, s, 0);
+        const uint32_t last = min(32u, r - g0) - 1u;
+        const uint32_t E = __shfl_sync(0xffffffffu, e, last);
+        const bool staged = E - S <= kMrWarpSpan;  // the same for the whole warp
+        if (staged) {
+            for (uint32_t i = lane; i < E - S; i += 32) {
+                wk[mr_slot(i)] = copy[S + i];
+                if (V) wv[mr_slot(i)] = vcopy[S + i];
             }
-            v[i] = (V && in) ? vcopy[s + i] : 0u;
+            __syncwarp();
         }
-        sort_net32(x, v);
+        if (!V && mine) {
+            const uint32_t b = s - S;
+            K xk[32];
 #pragma unroll
-        for (uint32_t i = 0; i < 32; i++) {
-            if (i < len) {
-                if constexpr (sizeof(K) == 4) copy[s + i] = (K)(x[i].kp >> 32);
-                else copy[s + i] = x[i].key;
-                if (V) vcopy[s + i] = v[i];
+            for (uint32_t i = 0; i < 32; i++) xk[i] = i < len ? (staged ? wk[mr_slot(b + i)] : copy[s + i]) : ~K(0);
+            sort_net32_keys(xk);
+#pragma unroll
+            for (uint32_t i = 0; i < 32; i++) {
+                if (i < len) {
+                    if (staged) wk[mr_slot(b + i)] = xk[i];
+                    else copy[s + i] = xk[i];
+                }
             }
+        }
+        if (V && mine) {
+            const uint32_t b = s - S;
+            T x[32];
+            uint32_t v[32];
+#pragma unroll
+            for (uint32_t i = 0; i < 32; i++) {
+                const bool in = i < len;
+                const K key = in ? (staged ? wk[mr_slot(b + i)] : copy[s + i]) : ~K(0);
+                if constexpr (sizeof(K) == 4) {
+                    x[i].kp = ((unsigned long long)key << 32) | (in ? i : 32u + i);
+                } else {
+                    x[i].key = key;
+                    x[i].pos = in ? i : 32u + i;
+                }
+                v[i] = (V && in) ? (staged ? wv[mr_slot(b + i)] : vcopy[s + i]) : 0u;
+            }
+            sort_net32(x, v);
+#pragma unroll
+            for (uint32_t i = 0; i < 32; i++) {
+                if (i < len) {
+                    K key;
+                    if constexpr (sizeof(K) == 4) key = (K)(x[i].kp >> 32);
+                    else key = x[i].key;
+                    if (staged) {
+                        wk[mr_slot(b + i)] = key;
+                        if (V) wv[mr_slot(b + i)] = v[i];
+                    } else {
+                        copy[s + i] = key;
+                        if (V) vcopy[s + i] = v[i];
+                    }
+                }
+            }
+        }
+        if (staged) {
+            __syncwarp();
+            for (uint32_t i = lane; i < E - S; i += 32) {
+                copy[S + i] = wk[mr_slot(i)];
+                if (V) vcopy[S + i] = wv[mr_slot(i)];
+            }
+            __syncwarp();
         }
     }
 }
@@ -422,8 +508,10 @@ void launch_min_run(const K* keys, K* copy, uint32_t* vcopy, uint64_t n, const M
     const uint32_t run_grid = (uint32_t)std::min<uint64_t>(ceil_div(r_bound, kMrThreads), 152 * 16);
     k_mr_write_runs<K><<<run_grid, kMrThreads, 0, st>>>(ws.counters, keys, n, mr, ws.run_starts, ws.run_desc, r_bound);
     // the copy: every run of at most m elements sorted in place
-    k_mr_sort_short<K, V><<<(uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r_bound, kMrThreads), 152 * 16), kMrThreads, 0,
-                            st>>>(ws.counters, ws.run_starts, mr.m, copy, vcopy, r_bound);
+    const size_t sort_smem = MrSortSmem<K, V>::bytes();
+    cudaFuncSetAttribute(k_mr_sort_short<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
+    k_mr_sort_short<K, V><<<(uint32_t)std::min<uint64_t>(ceil_div((uint64_t)r_bound, kMrThreads), 152 * 16), kMrThreads,
+                            sort_smem, st>>>(ws.counters, ws.run_starts, mr.m, copy, vcopy, r_bound);
     g_launches += 9 + rounds;
 }
 
