@@ -259,11 +259,14 @@ __global__ void __launch_bounds__(1024) k_detect_scan(uint64_t n, const uint4* _
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t per = (tiles + 31) / 32;  // tiles per warp
     const uint32_t t0 = min(tiles, warp * per), t1 = min(tiles, t0 + per);
-    // pass 1: the warp's aggregate
+    // pass 1: the warp's aggregate (the next 32 summaries are loaded while
+    // the current ones are scanned)
     uint4 carry = runsum_identity();
+    uint4 nx = t0 + lane < t1 ? tile_sum[t0 + lane] : runsum_identity();
     for (uint32_t b = t0; b < t1; b += 32) {
-        const uint32_t t = b + lane;
-        uint4 x = warp_scan_incl(t < t1 ? tile_sum[t] : runsum_identity());
+        const uint4 cur = nx;
+        nx = b + 32 + lane < t1 ? tile_sum[b + 32 + lane] : runsum_identity();
+        const uint4 x = warp_scan_incl(cur);
         carry = OpRunSum()(carry, shfl_idx(x, 31));
     }
     uint4 tot;
@@ -273,9 +276,11 @@ __global__ void __launch_bounds__(1024) k_detect_scan(uint64_t n, const uint4* _
     __syncthreads();
     // pass 2: every tile's exclusive prefix, entered in state B
     carry = s_warp[warp];
+    nx = t0 + lane < t1 ? tile_sum[t0 + lane] : runsum_identity();
     for (uint32_t b = t0; b < t1; b += 32) {
         const uint32_t t = b + lane;
-        const uint4 x = t < t1 ? tile_sum[t] : runsum_identity();
+        const uint4 x = nx;
+        nx = b + 32 + lane < t1 ? tile_sum[b + 32 + lane] : runsum_identity();
         const uint4 incl = warp_scan_incl(x);
         uint4 excl = shfl_up(incl, 1);
         if (lane == 0) excl = runsum_identity();
