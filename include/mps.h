@@ -26,7 +26,8 @@
  *     unsigned integers; every value, including the type's maximum, is a
  *     legal key (no sentinel is reserved; cf. Sec. 4 "Sentinel values").
  *   - Fan-in k must be 2, 4, 8 or 16 (Sec. 3's k-way powers for k a power of
- *     two; Sec. 6 leaves k > 4 open).  n must be below 2^31.
+ *     two; Sec. 6 leaves k > 4 open).  n must be below 2^32 (below 2^31 with a
+ *     minimum run length, and for a queued request).
  *   - For a single array, d_keys_out may equal (or overlap) d_keys_in, and
  *     d_vals_out d_vals_in: the sort then reads a copy of the input that it
  *     makes in the workspace (mps_workspace_size includes room for it).  Keys
@@ -49,7 +50,7 @@ extern "C" {
 typedef enum {
     MPS_OK = 0,
     MPS_ERR_INVALID_ARG = 1,  /* null pointer, overlap, bad key type           */
-    MPS_ERR_UNSUPPORTED = 2,  /* k not in {2,4,8}, n >= 2^31                   */
+    MPS_ERR_UNSUPPORTED = 2,  /* k not in {2,4,8,16}, n >= 2^32 (see above)     */
     MPS_ERR_WORKSPACE = 3,    /* workspace smaller than mps_workspace_size      */
     MPS_ERR_CUDA = 4,         /* a CUDA runtime call failed                     */
     MPS_ERR_TIMEOUT = 5,      /* a bounded wait ran out (queue / device spin)   */
@@ -156,7 +157,8 @@ mps_status mps_sort_pairs_minrun(const void* d_keys_in, const uint32_t* d_vals_i
  * labels the tree was built from: each final-collapse node is numbered from
  * the root (1, 2, ...) and every other power is raised by the number of
  * final-collapse nodes.  Workspace: mps_workspace_size(n, kt, 0, k).  Device
- * status 20 if the relabelled powers would exceed 32 (n near 2^31 at k = 4).
+ * status 20 if the relabelled powers would exceed 32 (possible above n = 2^30
+ * at k = 4).
  * tail_policy outside 0..2: MPS_ERR_INVALID_ARG. */
 mps_status mps_sort_keys_tail(const void* d_keys_in, void* d_keys_out, uint64_t n, mps_key_type kt, int k, int tail_policy,
                               void* d_ws, size_t ws_bytes, const mps_tree* opt_tree, cudaStream_t stream);
@@ -201,7 +203,7 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
  *             (fan-in and tile sizes) chosen by mps_batch_autotune or set by
  *             mps_batch_set_config for this key type and mean array size
  *             (k = 4, default tiles until then).
- * n must be below 2^31.  Workspace: mps_batch_workspace_size(n, m, kt,
+ * n must be below 2^32.  Workspace: mps_batch_workspace_size(n, m, kt,
  * has_payload, k); k = 0 asks for the largest over every configuration.
  *   d_merge_costs : NULL, or device memory for m uint64 values that receives
  *             each array's merge cost M = sum_i depth(run i) * L_i (Sec. 2.2)

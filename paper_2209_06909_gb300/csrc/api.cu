@@ -413,7 +413,9 @@ mps_status sort_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, uin
     if (tail < 0 || tail > 2) return MPS_ERR_INVALID_ARG;
     // for k = 2 every final-collapse node has one boundary: all policies build the same tree
     const bool relabel = tail != 0 && k > 2;
-    if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    // run starts are 32-bit positions; a minimum run length steps positions by
+    // m, which is kept clear of wrapping by the lower limit
+    if (n >= (1ull << 32) || (min_run > 1 && n >= (1ull << 31))) return MPS_ERR_UNSUPPORTED;
     const double b = (double)sizeof(K) + (V ? 4.0 : 0.0);
     g_launches = 0;
     if (n == 0) {
@@ -538,7 +540,7 @@ mps_status batch_impl(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
                       uint64_t* d_costs, bool sync_at_end, cudaStream_t st, int tile) {
     if (!fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
     if (tile < 0 || tile >= kTileChoices) return MPS_ERR_INVALID_ARG;
-    if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    if (n >= (1ull << 32)) return MPS_ERR_UNSUPPORTED;
     struct Range {  // NVTX range around the whole batch
         Range() { nvtxRangePushA("sort_batch"); }
         ~Range() { nvtxRangePop(); }
@@ -601,7 +603,7 @@ mps_status mps_workspace_size(uint64_t n, mps_key_type kt, int has_payload, int 
     if (!bytes) return MPS_ERR_INVALID_ARG;
     if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
     if (!fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
-    if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    if (n >= (1ull << 32)) return MPS_ERR_UNSUPPORTED;
     Plan p(n, kt == MPS_U32 ? 4 : 8, has_payload != 0, k);
     *bytes = p.total;
     return MPS_OK;
@@ -776,7 +778,7 @@ mps_status mps_batch_workspace_size(uint64_t n, uint32_t m, mps_key_type kt, int
     if (!bytes) return MPS_ERR_INVALID_ARG;
     if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
     if (k != 0 && !fan_in_ok(k)) return MPS_ERR_UNSUPPORTED;
-    if (n >= (1ull << 31)) return MPS_ERR_UNSUPPORTED;
+    if (n >= (1ull << 32)) return MPS_ERR_UNSUPPORTED;
     // k = 0 (the tuned configuration): the largest over fan-ins 2, 4, 8 (and 16
     // if set by mps_batch_set_config) and every tile choice
     size_t best = 0;

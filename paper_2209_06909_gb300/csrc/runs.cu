@@ -354,10 +354,9 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
     const uint32_t pad_end = (r + 1 + 31) / 32 * 32;
     unsigned long long bits = 0;
     uint32_t longest = 0;  // longest run seen by this thread
-    // a single array: 2n and its shift are the same for every boundary
-    const uint64_t d1 = 2 * n;
-    const bool pow2_1 = (d1 & (d1 - 1)) == 0;
-    const int sh1 = (int)w - ((int)__ffsll((long long)d1) - 1);
+    // a single array: n and its shift are the same for every boundary
+    const bool pow2_1 = (n & (n - 1)) == 0;
+    const int sh1 = (int)w - (int)__ffsll((long long)n);  // w - log2(2n) when n is a power of two
     for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < groups; gi += gridDim.x * blockDim.x) {
         const uint32_t i0 = gi * 16;
         uint32_t rv[20];
@@ -403,18 +402,23 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
                     mg = ((uint64_t)prm.y << 32) | arr_param[m + arr].x;
                 }
                 if (i >= 1 && i < r && !arr_start) {
-                    const uint64_t d = BATCH ? 2 * nn : d1;
-                    const uint32_t a2 = (sp - base) + (si - base);         // 2n * a  (< 2n <= 2^32)
-                    const uint32_t b2 = (si - base) + (rv[q + 1] - base);  // 2n * b
+                    const uint64_t d = BATCH ? nn : n;
+                    const uint64_t a2 = (uint64_t)(sp - base) + (si - base);         // 2n * a  (< 2n < 2^33)
+                    const uint64_t b2 = (uint64_t)(si - base) + (rv[q + 1] - base);  // 2n * b
                     uint32_t h;
                     if (BATCH ? (d & (d - 1)) == 0 : pow2_1) {
-                        // 2n a power of two: x = a2 * 2^w / 2n is a shift, and x, y < 2^w <= 2^31
-                        const int sh = BATCH ? (int)ww - ((int)__ffsll((long long)d) - 1) : sh1;
-                        const uint32_t x = sh >= 0 ? a2 << sh : a2 >> -sh;
-                        const uint32_t y = sh >= 0 ? b2 << sh : b2 >> -sh;
+                        // n a power of two (so n <= 2^31 and a2, b2 < 2^32): x = a2 * 2^w / 2n
+                        // is a shift, and x, y < 2^w <= 2^31
+                        const int sh = BATCH ? (int)ww - (int)__ffsll((long long)d) : sh1;
+                        const uint32_t a32 = (uint32_t)a2, b32 = (uint32_t)b2;
+                        const uint32_t x = sh >= 0 ? a32 << sh : a32 >> -sh;
+                        const uint32_t y = sh >= 0 ? b32 << sh : b32 >> -sh;
                         h = 31u - (uint32_t)__clz((int)(x ^ y));
                     } else {
-                        const uint64_t X = (uint64_t)a2 << ww, Y = (uint64_t)b2 << ww;
+                        // x = a2 * 2^(w-1) / n, the same quotient as a2 * 2^w / 2n, with the
+                        // product below 2^64 for n < 2^32 (a2 < 2^33, 2^(w-1) <= 2^31);
+                        // mg = floor((2^64 - 1) / n) gives it to within two, then corrected
+                        const uint64_t X = a2 << (ww - 1), Y = b2 << (ww - 1);
                         uint64_t x = __umul64hi(X, mg), y = __umul64hi(Y, mg);
                         uint64_t rx = X - x * d, ry = Y - y * d;
                         while (rx >= d) { x++; rx -= d; }
@@ -439,7 +443,7 @@ __global__ void __launch_bounds__(256) k_powers(const uint32_t* __restrict__ run
 }
 
 // Per-array power parameters of a batch: w = ceil(log2 n_a) and the 64-bit
-// reciprocal floor((2^64 - 1) / (2 n_a)), stored as prm[a] = (w, magic_hi),
+// reciprocal floor((2^64 - 1) / n_a), stored as prm[a] = (w, magic_hi),
 // prm[m + a].x = magic_lo.  Also the longest array, checked against the
 // caller's bound max_len (0: no bound given).
 __global__ void k_array_params(const uint64_t* __restrict__ off, uint32_t m, uint64_t max_len, uint2* __restrict__ prm,
@@ -450,7 +454,7 @@ __global__ void k_array_params(const uint64_t* __restrict__ off, uint32_t m, uin
         atomicMax(reinterpret_cast<unsigned long long*>(counters + kCtrMaxLen), (unsigned long long)na);
         uint32_t w = 0;
         while ((1ull << w) < na) w++;
-        const uint64_t mg = na ? ~0ull / (2 * na) : 0ull;
+        const uint64_t mg = na ? ~0ull / na : 0ull;
         prm[a] = make_uint2(w, (uint32_t)(mg >> 32));
         prm[m + a] = make_uint2((uint32_t)mg, 0u);
     }
@@ -480,7 +484,7 @@ template void launch_detect<uint64_t>(const uint64_t*, uint64_t, const WsView&, 
 void launch_powers(uint64_t n, uint32_t r, int k, const WsView& ws, cudaStream_t st) {
     uint32_t w = 0;
     while ((1ull << w) < n) w++;
-    uint64_t magic = ~0ull / (2 * n);
+    uint64_t magic = ~0ull / std::max<uint64_t>(n, 1);
     const uint32_t log2k = (uint32_t)__builtin_ctz((unsigned)k);
     uint32_t threads = 256;
     uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div(ceil_div((uint64_t)r + 1, 16), threads), 152 * 16);

@@ -44,16 +44,25 @@ def test_workspace_size_host_checks(lib):
         mps.workspace_size(1000, 4, False, 3)
     assert e.value.code == 2
     with pytest.raises(mps.MpsError):
-        mps.workspace_size(1 << 31, 4, False, 4)
+        mps.workspace_size(1 << 32, 4, False, 4)
 
 
 def test_sort_rejects_bad_fan_in_before_any_device_work(lib):
     P = ctypes.c_void_p
     lib.mps_sort_keys.argtypes = [P, P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P, P]
     assert lib.mps_sort_keys(None, None, 10, 0, 3, None, 0, None, None) == 2
-    assert lib.mps_sort_keys(None, None, 1 << 31, 0, 4, None, 0, None, None) == 2
+    assert lib.mps_sort_keys(None, None, 1 << 32, 0, 4, None, 0, None, None) == 2
+    # n >= 2^31 with a minimum run length
+    assert mps_minrun_code(lib, 1 << 31) == 2 and mps_minrun_code(lib, (1 << 31) - 1) == 1
     lib.mps_status_string.restype = ctypes.c_char_p
     assert lib.mps_status_string(3) == b"workspace too small"
+
+
+def mps_minrun_code(lib, n):
+    P = ctypes.c_void_p
+    lib.mps_sort_keys_minrun.argtypes = [P, P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, P,
+                                         ctypes.c_size_t, P, P]
+    return lib.mps_sort_keys_minrun(None, None, n, 0, 4, 24, None, 0, None, None)
 
 
 # C structs shared with the binding: (C type, ctypes class or numpy dtype name)

@@ -8,7 +8,8 @@ tree is still checked through its merge cost:
     exactly 0..n-1; runs, powers, node table, leaf depths and merge cost equal
     the oracle's run scan and tree from run lengths;
   * geometric random runs (n = 2^28, mean 2^14, k = 4 and 2): keys and tree
-    equal the oracle's;
+    equal the oracle's; and at n = 2^31 + 4099 (k = 4) the tree, with the
+    output checked for order, sum and xor;
   * pairs (n = 2^27, uint64 keys with 2^16 distinct values, payload = index):
     keys and payload order equal the oracle's;
   * records (n = 2^26, uint64 keys and uint64 payloads, runs of geometric
@@ -76,6 +77,28 @@ def test_geometric_runs_2e28(k):
     check_tree(tb.to_numpy(), a, k)
     want = oracle.sort(a, k=k, want_tree=False)
     assert np.array_equal(got, want["keys"])
+
+
+def test_geometric_runs_above_2e31():
+    """n = 2^31 + 4099 uint32 keys, past the size where 2n needs 33 bits (the
+    power kernel's quotient), geometric runs of mean 2^14, k = 4: the output is
+    non-decreasing with the input's sum and xor, and runs, powers, node table,
+    leaf depths and merge cost equal the oracle's run scan and tree from run
+    lengths."""
+    n = (1 << 31) + 4099
+    a = inputs.random_runs_geometric(n, 3100, mean=float(1 << 14))
+    tb = mps.TreeBuffers.alloc(n, DEV)
+    d = mps.to_device(a, DEV)
+    out = mps.sort_keys(d, k=4, tree=tb)
+    torch.cuda.synchronize()
+    del d
+    got = mps.to_numpy(out, np.uint32)
+    del out
+    assert np.all(got[1:] >= got[:-1])
+    assert int(got.sum(dtype=np.uint64)) == int(a.sum(dtype=np.uint64))
+    assert np.bitwise_xor.reduce(got) == np.bitwise_xor.reduce(a)
+    del got
+    check_tree(tb.to_numpy(), a, 4)
 
 
 def test_pairs_2e27():
