@@ -230,8 +230,9 @@ mps_status mps_sort_batch_pairs(const void* d_keys_in, const uint32_t* d_vals_in
  * k = 0 use it.  *best_k receives the fan-in; mps_batch_tuned_config reports
  * the tile sizes.  A tile choice sets the fused-subtree tile (elements merged
  * in one block's shared memory; items per thread = tile / 256) and the
- * level-merge work unit: choice 0 is the default (6144 and 9216 elements for
- * uint32 keys), 1 and 2 are smaller tiles with more blocks per SM.  The
+ * level-merge work unit: choice 0 is the default (4096 and 9216 elements for
+ * uint32 keys); 1 and 2 are other sizes (for uint32 keys a larger fused tile
+ * with fewer blocks per SM, and smaller tiles).  The
  * workspace must be sized with k = 0. */
 mps_status mps_batch_autotune(const void* d_keys_in, void* d_keys_out, const uint64_t* d_offsets, uint32_t m,
                               uint64_t n, uint64_t max_len, mps_key_type kt, void* d_ws, size_t ws_bytes,
@@ -243,7 +244,7 @@ mps_status mps_batch_autotune(const void* d_keys_in, void* d_keys_out, const uin
 mps_status mps_batch_tuned_config(mps_key_type kt, int has_payload, uint64_t n, uint32_t m, int* k, uint32_t* c_fused,
                                   uint32_t* c_level);
 /* Sets that configuration by hand: k in {2, 4, 8, 16}, tile in 0..2 (0: the
- * default tiles; 1, 2: smaller). */
+ * default tiles; 1, 2: the other choices of mps_batch_autotune). */
 mps_status mps_batch_set_config(mps_key_type kt, int has_payload, uint64_t n, uint32_t m, int k, int tile);
 
 /* A batch sort captured once into a CUDA graph for the given buffers (the

@@ -137,8 +137,8 @@ struct MergeGeom {
 };
 
 // Tile choices for the merge stages of one key/payload type: 0 is the
-// default (largest tiles); 1 and 2 halve and third the fused tile, so that
-// more blocks share an SM (items per thread = c_fused / 256).
+// default; 1 and 2 trade the fused tile's size against the blocks that share
+// an SM (items per thread = c_fused / 256).
 constexpr int kTileChoices = 3;
 MergeGeom merge_geom(int key_bytes, bool vals, int k, int tile = 0);
 

@@ -1174,7 +1174,7 @@ __global__ void k_copy_lone_runs(const K* __restrict__ in, const uint32_t* __res
 
 MergeGeom merge_geom(int key_bytes, bool vals, int k, int tile) {
     // {fused tile, level unit} elements per choice
-    static const uint32_t kKeys4[kTileChoices][2] = {{6144, 9216}, {3072, 6144}, {2048, 4096}};
+    static const uint32_t kKeys4[kTileChoices][2] = {{4096, 9216}, {6144, 9216}, {2048, 4096}};
     static const uint32_t kMid[kTileChoices][2] = {{4096, 4096}, {2048, 3072}, {1536, 2048}};
     static const uint32_t kKeys8Vals[kTileChoices][2] = {{3072, 4096}, {2048, 3072}, {1024, 2048}};
     const uint32_t(*t)[2] = (key_bytes == 4 && !vals) ? kKeys4 : ((key_bytes == 8 && vals) ? kKeys8Vals : kMid);

@@ -152,13 +152,13 @@ def test_fan_in_sixteen_and_tail_policy_checks(lib):
 
 
 def test_batch_configuration_host_logic(lib):
-    """The configuration that k = 0 selects: default (k = 4, the largest
+    """The configuration that k = 0 selects: default (k = 4, the default
     tiles) until set; per key type, payload flag and mean-size bucket; bad
     fan-in or tile rejected; the workspace for k = 0 covers every tile."""
     from paper_2209_06909_gb300 import mps
     n, m = 3_000_000, 700  # a mean size no other test of this process tunes
     cfg = mps.batch_tuned_config(4, False, n, m)
-    assert cfg == {"k": 4, "c_fused": 6144, "c_level": 9216, "items_per_thread": 24}
+    assert cfg == {"k": 4, "c_fused": 4096, "c_level": 9216, "items_per_thread": 16}
     mps.batch_set_config(4, False, n, m, 8, 2)
     assert mps.batch_tuned_config(4, False, n, m) == {"k": 8, "c_fused": 2048, "c_level": 4096, "items_per_thread": 8}
     assert mps.batch_tuned_config(4, True, n, m)["k"] == 4      # the payload flag has its own entry
