@@ -220,6 +220,13 @@ __device__ __forceinline__ uint32_t odd_chunk(uint32_t m) {
     return per | 1u;
 }
 
+// (count in bits 0..31, summed; bit set in bits 32..63, OR-ed)
+struct OpSumOr {
+    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const {
+        return (((a & 0xFFFFFFFFull) + (b & 0xFFFFFFFFull)) & 0xFFFFFFFFull) | ((a | b) & 0xFFFFFFFF00000000ull);
+    }
+};
+
 struct OpMax2 {
     __device__ uint4 operator()(uint4 X, uint4 Y) const { return make_uint4(max(X.x, Y.x), max(X.y, Y.y), 0u, 0u); }
 };
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(kFusedThreads)
     uint32_t* vB = V ? vA + CP : nullptr;
     uint32_t* bl0 = V ? (vB + CP) : reinterpret_cast<uint32_t*>(kB + CP);
     uint32_t* bl1 = bl0 + BMAX;
-    __shared__ uint32_t stmp[kFusedThreads / 32 + 1];
+    __shared__ unsigned long long stmp8[kFusedThreads / 32 + 1];
     __shared__ uint4 stmp4[kFusedThreads / 32 + 1];
     __shared__ __align__(8) uint64_t s_bar;
     // strictly descending runs longer than kShortRun, reversed by the whole block
@@ -434,7 +441,6 @@ __global__ void __launch_bounds__(kFusedThreads)
         uint32_t* bln = bl1;
         uint32_t T = 0;  // tournament rounds per node: log2 k
         while ((1u << T) < (uint32_t)k) T++;
-        __shared__ uint32_t s_rmask;
 
         for (uint32_t p = pmax; p >= pmin && p >= 1 && p > floor_p; p--) {
             per = odd_chunk(na);
@@ -459,13 +465,14 @@ __global__ void __launch_bounds__(kFusedThreads)
                     nk++;
                 }
             }
-            if (tid == 0) s_rmask = 0;
-            uint32_t nkeep;
-            const uint32_t kpos = block_sum_excl<kFusedThreads>(nk, stmp, &nkeep);
+            // one scan gives each thread's place in the next list, that list's
+            // length, and the rounds this level plays
+            unsigned long long tot;
+            const unsigned long long pre = block_scan_excl<kFusedThreads, false>(
+                (unsigned long long)nk | ((unsigned long long)rmask << 32), OpSumOr(), 0ull, stmp8, &tot);
+            const uint32_t kpos = (uint32_t)pre, nkeep = (uint32_t)tot;
             if (nkeep == na) continue;  // no boundary of power p in this subtree
-            if (rmask) atomicOr(&s_rmask, rmask);
-            __syncthreads();
-            const uint32_t rounds = s_rmask;
+            const uint32_t rounds = (uint32_t)(tot >> 32);
             const int first = round_entry(len, blc, (int)na);
             // tournament rounds
             for (uint32_t t = 0; t < T; t++) {
