@@ -130,7 +130,7 @@ struct MergeGeom {
     uint32_t c_fused;   // elements of shared memory per fused tile
     uint32_t tmax;      // largest fused subtree (== c_fused)
     uint32_t c_level;   // elements per level-merge unit
-    uint32_t ts;        // splitter spacing per child (c_level / 2k)
+    uint32_t ts;        // splitter spacing per child (c_level / k)
     int k;              // fan-in
     uint32_t level_grid;  // blocks of the persistent level merge
     uint32_t fused_grid;  // blocks of the persistent fused-subtree kernel
