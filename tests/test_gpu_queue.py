@@ -43,21 +43,22 @@ def make_requests(seed, count):
     return reqs
 
 
-def alone(kind, a, v):
+def alone(kind, a, v, k=4):
     """The request's sort and merge cost through the single-array calls."""
     if a.size == 0:
         return a, v, 0
     if kind == "keys":
-        ok = mps.to_numpy(mps.sort_keys(mps.to_device(a, DEV), k=4), a.dtype)
+        ok = mps.to_numpy(mps.sort_keys(mps.to_device(a, DEV), k=k), a.dtype)
         return ok, None, mps.last_stats()["merge_cost"]
-    ok, ov = mps.sort_pairs(mps.to_device(a, DEV), mps.to_device(v, DEV), k=4)
+    ok, ov = mps.sort_pairs(mps.to_device(a, DEV), mps.to_device(v, DEV), k=k)
     return mps.to_numpy(ok, a.dtype), mps.to_numpy(ov, np.uint32), mps.last_stats()["merge_cost"]
 
 
-def test_mixed_requests_match_alone():
-    reqs = make_requests(1, 80)
+@pytest.mark.parametrize("k", [4, 2, 16])
+def test_mixed_requests_match_alone(k):
+    reqs = make_requests(1 + k, 80 if k == 4 else 40)
     pool = torch.empty(256 << 20, dtype=torch.uint8, device=DEV)
-    q = mps.Queue(pool, max_inflight=3, max_batch=16, k=4)
+    q = mps.Queue(pool, max_inflight=3, max_batch=16, k=k)
     bufs, tickets = [], []
     lock = threading.Lock()
 
@@ -95,7 +96,7 @@ def test_mixed_requests_match_alone():
     assert len(results) == len(reqs)
     for i, d_out, dvo in bufs:
         kind, a, v = reqs[i]
-        wk, wv, wcost = alone(kind, a, v)
+        wk, wv, wcost = alone(kind, a, v, k)
         assert np.array_equal(mps.to_numpy(d_out, a.dtype), wk), i
         assert results[i]["merge_cost"] == wcost, i
         if kind == "pairs":
