@@ -1192,7 +1192,7 @@ MergeGeom merge_geom(int key_bytes, bool vals, int k, int tile) {
     g.c_fused = t[c][0];
     g.c_level = t[c][1];
     g.tmax = g.c_fused;
-    g.ts = 2u * g.c_level / (3u * (uint32_t)k);
+    g.ts = g.c_level / (uint32_t)k;
     g.k = k;
     // persistent level merge: two buffers of c_level elements per block
     size_t lvl_smem = (size_t)2 * (g.c_level + kLvlPad) * ((size_t)key_bytes + (vals ? 4 : 0)) + 256;
