@@ -7,7 +7,8 @@ keys resident in HBM before the timed region (1 GiB of input, larger than the
 129 MB L2, so no flush is needed between steps).  Also reported on the same
 line: the geometric random-runs input (mean run length 2^14) and k = 2 for
 both inputs (fewer steps each), the end-to-end time from pinned host memory
-through mps_sort_keys_host, the roofline of the dominant kernel, and the CPU
+(mps_sort_keys_host_async calls queued in turn on three streams, and the
+blocking mps_sort_keys_host), the roofline of the dominant kernel, and the CPU
 oracle timed on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mps|reference]
@@ -559,20 +560,47 @@ def run_mps(args):
                      "fused_subtrees": stats["frontier_nodes"], "level_nodes": stats["hbm_nodes"]}}
 
     if rank == 0:
-        # end to end through the C ABI from pinned host memory
+        # end to end through the C ABI from pinned host memory.  Headline form: a
+        # sequence of sorts, each a mps_sort_keys_host_async call (input copy, sort,
+        # output copy) queued in turn on three streams with their own device buffers
+        # and workspaces, so one sort's copies overlap another's kernels; every
+        # step's 1 GiB in and 1 GiB out is inside the timed region.  Also timed: the
+        # blocking mps_sort_keys_host, one call after another.
         h_in = torch.from_numpy(a.view(np.int32)).pin_memory()
-        h_out = torch.empty_like(h_in).pin_memory()
-        d_tmp = torch.empty_like(d_in)
-        mps.sort_keys_host(h_in, h_out, d_tmp, d_out, ws, k=k, stream=stream)
-        e2e_steps = 4
+        nst = 3
+        h_out = [torch.empty_like(h_in).pin_memory() for _ in range(nst)]
+        streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(nst - 1)]
+        d_ins = [torch.empty_like(d_in) for _ in range(nst)]
+        d_outs = [d_out] + [torch.empty_like(d_out) for _ in range(nst - 1)]
+        wss = [ws] + [torch.empty_like(ws) for _ in range(nst - 1)]
+        torch.cuda.synchronize()
+        mps.sort_keys_host(h_in, h_out[0], d_ins[0], d_outs[0], wss[0], k=k, stream=stream)
+        blocking_steps = 4
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            mps.sort_keys_host(h_in, h_out, d_tmp, d_out, ws, k=k, stream=stream)
+        for _ in range(blocking_steps):
+            mps.sort_keys_host(h_in, h_out[0], d_ins[0], d_outs[0], wss[0], k=k, stream=stream)
+        blocking_s = (time.perf_counter() - t0) / blocking_steps
+        for i in range(nst):  # warm-up of every stream's buffers
+            mps.sort_keys_host_async(h_in, h_out[i], d_ins[i], d_outs[i], wss[i], k=k, stream=streams[i])
+        torch.cuda.synchronize()
+        e2e_steps = 12
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            j = i % nst
+            mps.sort_keys_host_async(h_in, h_out[j], d_ins[j], d_outs[j], wss[j], k=k, stream=streams[j])
+        for s_ in streams:
+            s_.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
-        assert np.array_equal(h_out.numpy()[:1024].view(np.uint32), np.arange(1024, dtype=np.uint32))
+        want = np.arange(n, dtype=np.uint32)
+        for h in h_out:
+            assert np.array_equal(h.numpy().view(np.uint32), want)
         line["e2e"] = {"value": n / e2e_s / 1e9, "unit": "GKeys/s", "h2d_bytes_per_step": n * 4,
-                       "d2h_bytes_per_step": n * 4, "ms_per_step": e2e_s * 1e3}
-        del h_in, h_out
+                       "d2h_bytes_per_step": n * 4, "ms_per_step": e2e_s * 1e3,
+                       "form": f"{e2e_steps} sorts through mps_sort_keys_host_async on {nst} streams in turn "
+                               "(pinned host buffers)",
+                       "blocking": {"value": n / blocking_s / 1e9, "ms_per_step": blocking_s * 1e3,
+                                    "form": f"{blocking_steps} mps_sort_keys_host calls, one after another"}}
+        del h_in, h_out, d_ins, d_outs, wss
 
         if not args.no_variants:
             variants = []
@@ -632,7 +660,6 @@ def run_mps(args):
                                      "sort_roofline": sort_frac(b, n, st["merge_cost"], vms, peaks)})
             line["variants"] = variants
             del d_runs, ws_k
-        del d_tmp
         for name, fn, flag in (("pairs", lambda: bench_pairs(mps, torch, dev, stream, peaks), args.no_variants),
                                ("records", lambda: bench_records(mps, torch, dev, stream, peaks), args.no_variants),
                                ("batch", lambda: bench_batch(mps, torch, dev, stream, peaks), args.no_batch),

@@ -188,6 +188,20 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
                               void* d_keys_in, void* d_keys_out, void* d_ws, size_t ws_bytes,
                               cudaStream_t stream);
 
+/* The same three steps queued on `stream` without waiting: the call returns
+ * once the input copy, the sort's kernels and the output copy are enqueued,
+ * and h_keys_out holds the result when `stream` reaches that point.  With
+ * pinned host buffers the copies run on the copy engines, so a caller that
+ * sorts a sequence of arrays on two or more streams (each with its own device
+ * buffers and workspace) overlaps one array's copies with another's sort.
+ * The host buffers, device buffers and workspace must stay untouched until
+ * the stream has passed the call.  Returns MPS_ERR_CUDA if a copy cannot be
+ * queued; other errors as mps_sort_keys (device-side failures are read with
+ * mps_sync_status). */
+mps_status mps_sort_keys_host_async(const void* h_keys_in, void* h_keys_out, uint64_t n, mps_key_type kt, int k,
+                                    void* d_keys_in, void* d_keys_out, void* d_ws, size_t ws_bytes,
+                                    cudaStream_t stream);
+
 /* ---------------------------------------------------------------- batches
  * A batch is m independent arrays laid end to end in one key buffer:
  * array a occupies [d_offsets[a], d_offsets[a+1]) with d_offsets[0] = 0 and

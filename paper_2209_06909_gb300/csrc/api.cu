@@ -696,14 +696,22 @@ mps_status mps_sort_pairs_minrun(const void* d_keys_in, const uint32_t* d_vals_i
     return MPS_ERR_INVALID_ARG;
 }
 
-mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t n, mps_key_type kt, int k, void* d_keys_in,
-                              void* d_keys_out, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+mps_status mps_sort_keys_host_async(const void* h_keys_in, void* h_keys_out, uint64_t n, mps_key_type kt, int k,
+                                    void* d_keys_in, void* d_keys_out, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
     if (n && (!h_keys_in || !h_keys_out || !d_keys_in || !d_keys_out)) return MPS_ERR_INVALID_ARG;
-    size_t bytes = n * (kt == MPS_U32 ? 4 : 8);
+    if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
+    const size_t bytes = n * (kt == MPS_U32 ? 4 : 8);
     if (n && cudaMemcpyAsync(d_keys_in, h_keys_in, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) return MPS_ERR_CUDA;
     mps_status s = mps_sort_keys(d_keys_in, d_keys_out, n, kt, k, d_ws, ws_bytes, nullptr, stream);
     if (s != MPS_OK) return s;
     if (n && cudaMemcpyAsync(h_keys_out, d_keys_out, bytes, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return MPS_ERR_CUDA;
+    return MPS_OK;
+}
+
+mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t n, mps_key_type kt, int k, void* d_keys_in,
+                              void* d_keys_out, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    mps_status s = mps_sort_keys_host_async(h_keys_in, h_keys_out, n, kt, k, d_keys_in, d_keys_out, d_ws, ws_bytes, stream);
+    if (s != MPS_OK) return s;
     if (cudaStreamSynchronize(stream) != cudaSuccess) return MPS_ERR_CUDA;
     return MPS_OK;
 }

@@ -76,7 +76,7 @@ EXPORTS = ["mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_t
            "mps_queue_create", "mps_queue_submit", "mps_queue_poll", "mps_queue_wait", "mps_queue_pause",
            "mps_queue_destroy", "mps_records_workspace_size", "mps_sort_records", "mps_sync_status",
            "mps_workspace_size_minrun", "mps_sort_keys_minrun", "mps_sort_pairs_minrun", "mps_sort_keys_tail",
-           "mps_batch_tuned_config", "mps_batch_set_config"]
+           "mps_batch_tuned_config", "mps_batch_set_config", "mps_sort_keys_host_async"]
 
 # Largest n accepted by mps_sort_keys_noalloc (its scratch is compiled into the library).
 NOALLOC_MAX_N = 1 << 20
@@ -98,6 +98,7 @@ def lib():
     L.mps_sort_pairs.argtypes = [P, P, P, P, U64, I, I, P, ctypes.c_size_t, P, P]
     L.mps_merge_tree.argtypes = [P, U64, I, I, P, P, ctypes.c_size_t, P]
     L.mps_sort_keys_host.argtypes = [P, P, U64, I, I, P, P, P, ctypes.c_size_t, P]
+    L.mps_sort_keys_host_async.argtypes = [P, P, U64, I, I, P, P, P, ctypes.c_size_t, P]
     L.mps_profile_enable.argtypes = [I]
     L.mps_profile_enable.restype = None
     L.mps_profile_read.argtypes = [P, I]
@@ -145,7 +146,7 @@ def lib():
     L.mps_status_string.argtypes = [I]
     L.mps_status_string.restype = ctypes.c_char_p
     for fn in ("mps_workspace_size", "mps_sort_keys", "mps_sort_pairs", "mps_merge_tree", "mps_sort_keys_host",
-               "mps_last_stats"):
+               "mps_sort_keys_host_async", "mps_last_stats"):
         getattr(L, fn).restype = I
     _lib = L
     return L
@@ -308,6 +309,18 @@ def sort_keys_host(h_in: torch.Tensor, h_out: torch.Tensor, d_in: torch.Tensor, 
     _check("mps_sort_keys_host", lib().mps_sort_keys_host(h_in.data_ptr(), h_out.data_ptr(), n, _key_type(h_in), k,
                                                           d_in.data_ptr(), d_out.data_ptr(), ws.data_ptr(),
                                                           ws.numel(), _stream(stream)))
+
+
+def sort_keys_host_async(h_in: torch.Tensor, h_out: torch.Tensor, d_in: torch.Tensor, d_out: torch.Tensor,
+                         ws: torch.Tensor, k: int = 4, stream=None) -> None:
+    """The same, queued on `stream` without waiting (mps_sort_keys_host_async):
+    h_out holds the result once the stream has passed the call.  The caller
+    keeps every buffer alive and untouched until then."""
+    n = h_in.numel()
+    _check("mps_sort_keys_host_async", lib().mps_sort_keys_host_async(h_in.data_ptr(), h_out.data_ptr(), n,
+                                                                      _key_type(h_in), k, d_in.data_ptr(),
+                                                                      d_out.data_ptr(), ws.data_ptr(), ws.numel(),
+                                                                      _stream(stream)))
 
 
 def sort_keys_noalloc(keys: torch.Tensor, out: torch.Tensor, k: int = 4, stream=None) -> torch.Tensor:

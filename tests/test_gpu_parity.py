@@ -161,6 +161,28 @@ def test_host_entry_point():
     assert np.array_equal(h_out.numpy().view(np.uint32), np.sort(a))
 
 
+def test_host_async_pipeline():
+    """Six arrays through mps_sort_keys_host_async on two streams, each stream
+    with its own device buffers and workspace, queued without waiting: every
+    host result must be that array's sort."""
+    n = 300000
+    arrays = [inputs.random_runs_geometric(n, seed=40 + i, mean=50.0) if i % 2 else inputs.random_permutation(n, seed=40 + i)
+              for i in range(6)]
+    h_in = [torch.from_numpy(a.view(np.int32)).pin_memory() for a in arrays]
+    h_out = [torch.empty_like(h).pin_memory() for h in h_in]
+    streams = [torch.cuda.Stream(device=DEV) for _ in range(2)]
+    d_in = [torch.empty(n, dtype=torch.int32, device=DEV) for _ in range(2)]
+    d_out = [torch.empty_like(d) for d in d_in]
+    ws = [mps.workspace(n, 4, False, 4, DEV) for _ in range(2)]
+    torch.cuda.synchronize()
+    for i in range(6):
+        s = i % 2
+        mps.sort_keys_host_async(h_in[i], h_out[i], d_in[s], d_out[s], ws[s], k=4, stream=streams[s])
+    torch.cuda.synchronize()
+    for i, a in enumerate(arrays):
+        assert np.array_equal(h_out[i].numpy().view(np.uint32), np.sort(a)), i
+
+
 def test_argument_errors():
     a = mps.to_device(np.arange(1000, dtype=np.uint32), DEV)
     with pytest.raises(mps.MpsError) as e:
