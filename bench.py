@@ -569,7 +569,8 @@ def run_mps(args):
         h_in = torch.from_numpy(a.view(np.int32)).pin_memory()
         nst = 3
         h_out = [torch.empty_like(h_in).pin_memory() for _ in range(nst)]
-        streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(nst - 1)]
+        # streams of their own: work on the legacy default stream would wait for the others
+        streams = [torch.cuda.Stream(device=dev) for _ in range(nst)]
         d_ins = [torch.empty_like(d_in) for _ in range(nst)]
         d_outs = [d_out] + [torch.empty_like(d_out) for _ in range(nst - 1)]
         wss = [ws] + [torch.empty_like(ws) for _ in range(nst - 1)]
