@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", choices=["mps", "reference"], default="mps")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--k", type=int, default=4)
+    ap.add_argument("--input", choices=["perm", "runs"], default="perm",
+                    help="main workload: random permutation (default) or geometric runs of mean 2^14")
     ap.add_argument("--no-variants", action="store_true", help="skip the secondary inputs and fan-ins")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-arrays section")
@@ -437,7 +439,8 @@ def run_reference(args):
     import oracle
     oracle.build()
     n_sample = 1 << args.ref_sample_log2
-    a = gen_input("perm", n_sample, 1234)
+    a = gen_input(args.input, n_sample, 1234)
+    in_name = "uniform random permutation" if args.input == "perm" else "geometric runs of mean 2^14"
     for _ in range(args.warmup):
         oracle.sort(a, k=args.k, want_tree=False)
     times = []
@@ -450,12 +453,12 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "sorted_keys_per_second", "value": value, "unit": "GKeys/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "single-array sort, uint32 keys, uniform random permutation, k=%d "
-                                   "(oracle steps sort a 2^%d-key sample)" % (args.k, args.ref_sample_log2),
-                       "n": n_sample, "k": args.k, "input": "random permutation"},
+            "config": {"workload": "single-array sort, uint32 keys, %s, k=%d "
+                                   "(oracle steps sort a 2^%d-key sample)" % (in_name, args.k, args.ref_sample_log2),
+                       "n": n_sample, "k": args.k, "input": in_name},
             "cpu_baseline": {"value": value, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
-                             "sample": "random permutation of 2^%d uint32 keys per step, one host core"
-                                       % args.ref_sample_log2},
+                             "sample": "%s, 2^%d uint32 keys per step, one host core"
+                                       % (in_name, args.ref_sample_log2)},
             "e2e": {"value": value, "unit": "GKeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -483,7 +486,8 @@ def run_mps(args):
     n, k = args.n, args.k
     stream = torch.cuda.current_stream(dev)
 
-    a = gen_input("perm", n, rank_seed(rank))
+    a = gen_input(args.input, n, rank_seed(rank))
+    want = np.arange(n, dtype=np.uint32) if args.input == "perm" else np.sort(a)
     d_in = mps.to_device(a, dev)
     d_out = torch.empty_like(d_in)
     ws = mps.workspace(n, 4, False, max(k, 2), dev)
@@ -492,7 +496,7 @@ def run_mps(args):
     # correctness spot check of this exact configuration (outside the timed region)
     mps.sort_keys(d_in, k=k, out=d_out, ws=ws, stream=stream)
     torch.cuda.synchronize()
-    assert torch.equal(d_out, torch.arange(n, dtype=torch.int32, device=dev)), "sorted output is not 0..n-1"
+    assert np.array_equal(mps.to_numpy(d_out, np.uint32), want), "sorted output differs from numpy's sort"
     stats = mps.last_stats()
 
     props = torch.cuda.get_device_properties(dev)
@@ -531,7 +535,8 @@ def run_mps(args):
                                                                              "merge.cu")],
                                  capture_output=True, text=True).stdout.strip()
         ent = tj.get(dom["name"])
-        if ent and ent.get("merge_cu_sha") == src_sha and ent.get("n") == n and ent.get("k") == k:
+        if (ent and ent.get("merge_cu_sha") == src_sha and ent.get("n") == n and ent.get("k") == k
+                and args.input == "perm"):
             traffic = ent["bytes_per_launch"]
     roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -542,12 +547,13 @@ def run_mps(args):
                 "ms_per_step": e["total_ms"] / args.steps,
                 "share": e["total_ms"] / sum(x["total_ms"] for x in prof)} for e in prof]
 
+    in_name = "uniform random permutation" if args.input == "perm" else "geometric runs of mean 2^14"
     line = {"metric": "sorted_keys_per_second", "value": value, "unit": "GKeys/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "single-array sort, n=2^%d uint32 keys, uniform random permutation, k=%d"
-                                   % (int(round(math.log2(n))), k),
-                       "n": n, "k": k, "input": "random permutation", "per_gpu_arrays": 1,
+            "config": {"workload": "single-array sort, n=2^%d uint32 keys, %s, k=%d"
+                                   % (int(round(math.log2(n))), in_name, k),
+                       "n": n, "k": k, "input": in_name, "per_gpu_arrays": 1,
                        "l2": "input 1 GiB > 129 MB L2 (no flush needed)"},
             "clocks": clocks, "gpu_launches": int(stats["launches"]) * args.steps,
             "roofline": roofline,
@@ -592,7 +598,6 @@ def run_mps(args):
         for s_ in streams:
             s_.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
-        want = np.arange(n, dtype=np.uint32)
         for h in h_out:
             assert np.array_equal(h.numpy().view(np.uint32), want)
         line["e2e"] = {"value": n / e2e_s / 1e9, "unit": "GKeys/s", "h2d_bytes_per_step": n * 4,
