@@ -635,10 +635,23 @@ __global__ void __launch_bounds__(256) k_level_split(const LevelNode* __restrict
     uint32_t split = 0, v = 0, c = 0, unit_base = 0, nsp = 0;
     int d = 0;
     if (active) {
-        uint32_t lo = 0, hi = nn;  // last node with split_off <= g
+        // the node holding splitter g: the last node with split_off <= g.  With
+        // s_lo = split_off[lo] <= g < s_hi = split_off[hi] (split_off[nn] read as
+        // the total), each step probes where interpolation between s_lo and s_hi
+        // puts g, and adds a bisection probe when that did not at least halve
+        // [lo, hi]; split_off grows with v almost linearly, so a few probes do
+        uint32_t lo = 0, hi = nn, s_lo = 0, s_hi = total;
         while (hi - lo > 1) {
-            uint32_t m = (lo + hi) >> 1;
-            if (nodes[m].split_off <= g) lo = m; else hi = m;
+            const uint32_t span = hi - lo;
+            uint32_t m = lo + (uint32_t)(((uint64_t)(g - s_lo) * span) / (uint64_t)(s_hi - s_lo));
+            m = min(max(m, lo + 1u), hi - 1u);
+            uint32_t sm = nodes[m].split_off;
+            if (sm <= g) { lo = m; s_lo = sm; } else { hi = m; s_hi = sm; }
+            if (2u * (hi - lo) > span && hi - lo > 1) {
+                m = lo + ((hi - lo) >> 1);
+                sm = nodes[m].split_off;
+                if (sm <= g) { lo = m; s_lo = sm; } else { hi = m; s_hi = sm; }
+            }
         }
         v = lo;
         const LevelNode nd = nodes[v];
