@@ -33,6 +33,11 @@
  *     makes in the workspace (mps_workspace_size includes room for it).  Keys
  *     and payloads must not overlap each other.  Batch outputs must not
  *     overlap their inputs.
+ *   - A workspace serves one call at a time.  Two calls whose kernels may run
+ *     at the same time (queued on different streams with no event or
+ *     synchronisation between them) need different workspaces: sharing one
+ *     mixes the two sorts' counters and tables, and kernels that index with
+ *     them can then read or write out of range.
  *   - Errors are returned as mps_status; a device-side invariant violation
  *     (which would indicate a library bug) is reported as MPS_ERR_DEVICE_CHECK.
  */
