@@ -590,20 +590,26 @@ def run_mps(args):
         for i in range(nst):  # warm-up of every stream's buffers
             mps.sort_keys_host_async(h_in, h_out[i], d_ins[i], d_outs[i], wss[i], k=k, stream=streams[i])
         torch.cuda.synchronize()
-        e2e_steps = 12
-        t0 = time.perf_counter()
-        for i in range(e2e_steps):
-            j = i % nst
-            mps.sort_keys_host_async(h_in, h_out[j], d_ins[j], d_outs[j], wss[j], k=k, stream=streams[j])
-        for s_ in streams:
-            s_.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        # three repetitions of the 12-step loop, median reported: host copy rates
+        # vary between runs when other processes share the host's memory and links
+        e2e_steps, e2e_reps = 12, 3
+        rep_s = []
+        for _ in range(e2e_reps):
+            t0 = time.perf_counter()
+            for i in range(e2e_steps):
+                j = i % nst
+                mps.sort_keys_host_async(h_in, h_out[j], d_ins[j], d_outs[j], wss[j], k=k, stream=streams[j])
+            for s_ in streams:
+                s_.synchronize()
+            rep_s.append((time.perf_counter() - t0) / e2e_steps)
+        e2e_s = float(np.median(rep_s))
         for h in h_out:
             assert np.array_equal(h.numpy().view(np.uint32), want)
         line["e2e"] = {"value": n / e2e_s / 1e9, "unit": "GKeys/s", "h2d_bytes_per_step": n * 4,
                        "d2h_bytes_per_step": n * 4, "ms_per_step": e2e_s * 1e3,
-                       "form": f"{e2e_steps} sorts through mps_sort_keys_host_async on {nst} streams in turn "
-                               "(pinned host buffers)",
+                       "form": f"median of {e2e_reps} runs of {e2e_steps} sorts through mps_sort_keys_host_async "
+                               f"on {nst} streams in turn (pinned host buffers)",
+                       "ms_per_step_runs": [x * 1e3 for x in rep_s],
                        "blocking": {"value": n / blocking_s / 1e9, "ms_per_step": blocking_s * 1e3,
                                     "form": f"{blocking_steps} mps_sort_keys_host calls, one after another"}}
         del h_in, h_out, d_ins, d_outs, wss
