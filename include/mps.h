@@ -200,9 +200,10 @@ mps_status mps_sort_keys_host(const void* h_keys_in, void* h_keys_out, uint64_t 
  * sorts a sequence of arrays on two or more streams (each with its own device
  * buffers and workspace) overlaps one array's copies with another's sort.
  * The host buffers, device buffers and workspace must stay untouched until
- * the stream has passed the call.  Returns MPS_ERR_CUDA if a copy cannot be
- * queued; other errors as mps_sort_keys (device-side failures are read with
- * mps_sync_status). */
+ * the stream has passed the call.  The sort's argument checks (key type, k,
+ * n, workspace size and alignment) come first, so a rejected call queues
+ * nothing.  Returns MPS_ERR_CUDA if a copy cannot be queued; other errors as
+ * mps_sort_keys (device-side failures are read with mps_sync_status). */
 mps_status mps_sort_keys_host_async(const void* h_keys_in, void* h_keys_out, uint64_t n, mps_key_type kt, int k,
                                     void* d_keys_in, void* d_keys_out, void* d_ws, size_t ws_bytes,
                                     cudaStream_t stream);

@@ -699,7 +699,13 @@ mps_status mps_sort_pairs_minrun(const void* d_keys_in, const uint32_t* d_vals_i
 mps_status mps_sort_keys_host_async(const void* h_keys_in, void* h_keys_out, uint64_t n, mps_key_type kt, int k,
                                     void* d_keys_in, void* d_keys_out, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
     if (n && (!h_keys_in || !h_keys_out || !d_keys_in || !d_keys_out)) return MPS_ERR_INVALID_ARG;
-    if (kt != MPS_U32 && kt != MPS_U64) return MPS_ERR_INVALID_ARG;
+    // the sort's argument checks, made before the input copy is queued, so that
+    // a rejected call leaves nothing in flight
+    size_t need = 0;
+    const mps_status sz = mps_workspace_size(n, kt, 0, k, &need);
+    if (sz != MPS_OK) return sz;
+    if (n && (!d_ws || reinterpret_cast<uintptr_t>(d_ws) % 16)) return MPS_ERR_INVALID_ARG;
+    if (n && ws_bytes < need) return MPS_ERR_WORKSPACE;
     const size_t bytes = n * (kt == MPS_U32 ? 4 : 8);
     if (n && cudaMemcpyAsync(d_keys_in, h_keys_in, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) return MPS_ERR_CUDA;
     mps_status s = mps_sort_keys(d_keys_in, d_keys_out, n, kt, k, d_ws, ws_bytes, nullptr, stream);

@@ -198,6 +198,23 @@ def test_argument_errors():
     assert e.value.code == 1
 
 
+def test_host_async_rejects_before_copying():
+    """A rejected mps_sort_keys_host_async call queues nothing: the device
+    input buffer keeps its contents."""
+    n = 5000
+    h_in = torch.from_numpy(np.arange(n, dtype=np.int32)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in = torch.full((n,), 7, dtype=torch.int32, device=DEV)
+    d_out = torch.empty_like(d_in)
+    small = torch.empty(16, dtype=torch.uint8, device=DEV)
+    for k, ws, code in ((4, small, 3), (3, mps.workspace(n, 4, False, 4, DEV), 2)):
+        with pytest.raises(mps.MpsError) as e:
+            mps.sort_keys_host_async(h_in, h_out, d_in, d_out, ws, k=k)
+        assert e.value.code == code
+    torch.cuda.synchronize()
+    assert bool((d_in == 7).all())
+
+
 @pytest.mark.parametrize("k", [2, 4, 8, 16])
 def test_sort_in_place(k):
     """d_keys_out == d_keys_in (and payloads in place): the same result as the oracle."""
